@@ -146,3 +146,51 @@ def test_graph_without_non_singular_samples_is_rejected():
         g.sample_ids(1, np.arange(3, dtype=np.uint64))
     with pytest.raises(oracle.OracleError):
         oracle.OracleSketch(g, 1, 10)
+
+
+def _coin(seed, domain, retry, j, e):
+    """The coin word of edge e (reading R6), from the KAT-pinned Philox:
+    counter (q mod 2^32, (q >> 32) | retry << 4 | domain << 28, j lo, j hi),
+    q = e >> 2, key = (seed lo, seed hi), word e mod 4."""
+    q = e >> 2
+    ctr = [q & 0xFFFFFFFF, ((q >> 32) & 0xF) | ((retry & 0xFFFFFF) << 4) | (domain << 28),
+           j & 0xFFFFFFFF, j >> 32]
+    return int(oracle.philox4x32_10(ctr, [seed & 0xFFFFFFFF, seed >> 32])[e & 3])
+
+
+def test_first_step_coin_boundary_is_strict():
+    # single edge 1 -> 0 (CSR position 0): the round-0 FIRST coin x decides;
+    # tau = x is dead (x < tau fails), tau = x + 1 is live
+    seed = 0x5EED
+    for j in (0, 1, 7, 2**33 + 5):
+        x = _coin(seed, 2, 0, j, 0)
+        if x >= SENT - 1:
+            continue
+        dead = oracle.OracleGraph(2, [1], [0], weights=np.array([x], np.uint32), model=oracle.W_TAU)
+        live = oracle.OracleGraph(2, [1], [0], weights=np.array([x + 1], np.uint32), model=oracle.W_TAU)
+        a = dead.sample_ids(seed, np.array([j], np.uint64))
+        b = live.sample_ids(seed, np.array([j], np.uint64))
+        assert a["retries"][0] >= 1 and b["retries"][0] == 0
+
+
+def test_bfs_coin_boundary_is_strict():
+    # path 2 -> 1 -> 0 with 1 -> 0 always live. CSR: position 0 is (1 -> 0),
+    # position 1 is (2 -> 1). In a sample with source 0, vertex 2 joins R iff
+    # the BFS coin of edge 1 is below its threshold.
+    seed = 0xC0FFEE
+    checked = 0
+    for j in range(200):
+        x = _coin(seed, 3, 0, j, 1)
+        if x == 0 or x >= SENT - 1:
+            continue
+        res = []
+        for t in (x, x + 1):
+            g = oracle.OracleGraph(3, [1, 2], [0, 1], weights=np.array([SENT, t], np.uint32),
+                                   model=oracle.W_TAU)
+            o = g.sample_ids(seed, np.array([j], np.uint64))
+            res.append((int(o["src"][0]), set(o["members"].tolist())))
+        if res[0][0] != 0 or res[1][0] != 0:
+            continue
+        assert res[0][1] == {0, 1} and res[1][1] == {0, 1, 2}
+        checked += 1
+    assert checked >= 20
