@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark of the SKIS hot path on GB300.
+
+One step = one pass of the whole hot path over the Chung-Lu workload
+(n = 1M, m = 10M, exponent 2.1, trivalency probabilities, 10M IIS samples,
+greedy max-coverage k = 50): graph load (canonical in-CSR, thresholds,
+fixed-point gamma, alias table), IIS sampling, one batch of 64 influence
+queries (seed sets of 10 uniform vertices) and greedy max-coverage.
+
+`value` is RR sets/s with the edge arrays already in HBM; `e2e` is the same
+metric through the C ABI with host buffers (pinned), the host->device copy
+of the inputs and the device->host read of the results inside the timed
+region. `--impl reference` times the CPU oracle on the same workload.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, one rank per GPU, each rank an independent replica
+(its own sketch seed), value = all ranks' samples / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "RR sets/s and sampled edges/s (% HBM roofline); oracle queries/s with p50/p99"
+WORKLOAD = "chunglu-1e6-tri"
+QUERIES, QUERY_SIZE = 64, 10
+SKETCH_SEED = 0x5EED0002
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run exactly one step and exit (the command profiled with ncu)")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic_per_sample():
+    """Measured DRAM bytes per sample of the warp-tier sampler from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "iis_warp_dram.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    src = open(os.path.join(ROOT, "paper_1709_03565_gb300", "csrc", "sample.cu"), "rb").read()
+    if d.get("sample_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return float(d["dram_bytes_per_sample"])
+
+
+def algorithmic_bytes(T: int, entries: int, coins: int, per_edge_tau: bool) -> int:
+    """Algorithmic HBM bytes of one IIS sampling launch (random gathers at
+    32-byte sector granularity): per sample one alias-entry sector and a
+    32-byte header; per member one row-record sector and a 4-byte write; per
+    non-source member one source-id sector (the live edge that added it);
+    per coin a 4-byte threshold when thresholds are per edge."""
+    return 32 * T + 32 * T + 36 * entries + 32 * (entries - T) + (4 * coins if per_edge_tau else 0)
+
+
+# -------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    import synth
+
+    spec, src, dst, p = synth.workload(WORKLOAD)
+    oracle.build()
+    g = oracle.OracleGraph(spec["n"], src, dst, weights=p, model=oracle.W_P)
+    per_step = 200_000
+    nxt = 0
+
+    def step():
+        nonlocal nxt
+        ids = np.arange(nxt, nxt + per_step, dtype=np.uint64)
+        nxt += per_step
+        out = g.sample_ids(SKETCH_SEED, ids)
+        return int(out["coins"].sum())
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    coins = 0
+    for _ in range(args.steps):
+        coins += step()
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "RR sets/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": spec["n"], "m": spec["m"], "samples": spec["samples"],
+                   "k": spec["k"], "step": f"{per_step} consecutive sample ids of the workload"},
+        "sampled_edges_per_s": coins / dt,
+        "cpu_baseline": {"value": value, "unit": "RR sets/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} sample ids per step, single-threaded C oracle"},
+        "e2e": {"value": value, "unit": "RR sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------- ours
+def main():
+    args = _args()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    import paper_1709_03565_gb300 as skis
+    import synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    skis.lib()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    spec, src, dst, p = synth.workload(WORKLOAD)
+    n, m, T, k = spec["n"], spec["m"], spec["samples"], spec["k"]
+    q_off, q_seeds = synth.seed_sets(n, [QUERY_SIZE] * QUERIES, 11)
+    d_src, d_dst, d_p = (torch.from_numpy(x).to(dev) for x in (src, dst, p))
+    d_off, d_seeds = torch.from_numpy(q_off).to(dev), torch.from_numpy(q_seeds).to(dev)
+    d_cov = torch.empty(QUERIES, dtype=torch.int64, device=dev)
+    d_est = torch.empty(QUERIES, dtype=torch.float64, device=dev)
+    seed = SKETCH_SEED + rank
+    arena_hint = int(T * 5.5)
+    torch.cuda.synchronize()
+
+    def step():
+        g = skis.skis_load_graph(n, d_src, d_dst, d_p, skis.SKIS_W_EXPLICIT_P, stream=stream)
+        s = skis.skis_sketch_create(g, seed, arena_hint, stream=stream)
+        skis.skis_sample(s, T, stream=stream)
+        skis.skis_estimate(s, d_off, d_seeds, d_cov, d_est, stream=stream)
+        sd, sc, se = skis.skis_greedy_maxcover(s, k, stream=stream)
+        st = skis.skis_sketch_stats(s)
+        s.close()
+        g.close()
+        return st
+
+    if args.profile_step:
+        st = step()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_step": WORKLOAD, "samples": T, "entries": st["entries"],
+                          "coins": st["coins"], "deferred": st["deferred"],
+                          "launches": skis.skis_kernel_launches()}))
+        return
+    for _ in range(max(args.warmup, 3)):
+        step()
+    gpu_uuid = "0"
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_uuid = str(local)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-resident inputs
+    clocks = ClockSampler(gpu_uuid)
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = skis.skis_kernel_launches()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = skis.skis_kernel_launches() - launches0
+    elapsed_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * args.steps * T / (elapsed_ms / 1e3)
+    coins, entries = stats[-1]["coins"], stats[-1]["entries"]
+    warp_ms = statistics.mean(s["last_warp_ms"] for s in stats)
+    cta_ms = statistics.mean(s["last_cta_ms"] for s in stats)
+    sample_ms = statistics.mean(s["last_sample_ms"] for s in stats)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    h_src = torch.from_numpy(src).pin_memory()
+    h_dst = torch.from_numpy(dst).pin_memory()
+    h_p = torch.from_numpy(p).pin_memory()
+    h_off = torch.from_numpy(q_off).pin_memory()
+    h_seeds = torch.from_numpy(q_seeds).pin_memory()
+    h_cov = torch.empty(QUERIES, dtype=torch.int64).pin_memory()
+    h_est = torch.empty(QUERIES, dtype=torch.float64).pin_memory()
+
+    def step_e2e():
+        g = skis.skis_load_graph(n, h_src, h_dst, h_p, skis.SKIS_W_EXPLICIT_P, stream=stream)
+        s = skis.skis_sketch_create(g, seed, arena_hint, stream=stream)
+        skis.skis_sample(s, T, stream=stream)
+        skis.skis_estimate(s, h_off, h_seeds, h_cov, h_est, stream=stream)
+        out = skis.skis_greedy_maxcover(s, k, stream=stream)
+        s.close()
+        g.close()
+        return out
+
+    step_e2e()
+    barrier()
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e2.record(stream)
+    for _ in range(args.e2e_steps):
+        step_e2e()
+    e3.record(stream)
+    torch.cuda.synchronize()
+    wall_e2e = time.perf_counter() - t0
+    e2e_ms = max(e2.elapsed_time(e3), wall_e2e * 1e3)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * args.e2e_steps * T / (e2e_ms / 1e3)
+    h2d = m * (4 + 4 + 8) + q_off.nbytes + q_seeds.nbytes
+    d2h = k * (4 + 8 + 8) + QUERIES * (8 + 8)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (warp-tier IIS sampler)
+    peak, peak_kind = _peaks()
+    # both sampling launches of one skis_sample call together produce the
+    # whole sketch; the warp tier carries almost all of it
+    alg = algorithmic_bytes(T, entries, coins, per_edge_tau=True)
+    achieved = alg / (sample_ms / 1e3) / 1e9
+    tps = _traffic_per_sample()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tps * T if tps is not None else None), "kernel": "k_iis_warp + k_iis_cta",
+                "algorithmic_bytes": alg, "kernel_ms": sample_ms, "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
+
+    # ---- CPU baseline: the oracle, as it stands, on a bounded sample
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        og = oracle.OracleGraph(n, src, dst, weights=p, model=oracle.W_P)
+        done, t0 = 0, time.perf_counter()
+        while time.perf_counter() - t0 < args.cpu_seconds:
+            og.sample_ids(seed, np.arange(done, done + 50_000, dtype=np.uint64))
+            done += 50_000
+        dt = time.perf_counter() - t0
+        cpu = {"value": done / dt, "unit": "RR sets/s", "cores": 1, "kind": "oracle",
+               "sample": f"sample ids 0..{done - 1} of the same workload (single-threaded C oracle)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "RR sets/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": "Chung-Lu directed, exponent 2.1, TRI probabilities",
+                   "n": n, "m": m, "samples": T, "queries": QUERIES, "query_size": QUERY_SIZE, "k": k,
+                   "l2": "inputs larger than L2 (edge arrays 160 MB, arena ~170 MB, rebuilt every step)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "sampled_edges_per_s": world * args.steps * coins / (elapsed_ms / 1e3),
+        "sampling_only": {"rr_sets_per_s": T / (sample_ms / 1e3), "edges_per_s": coins / (sample_ms / 1e3),
+                          "warp_tier_ms": warp_ms, "cta_tier_ms": cta_ms, "deferred": stats[-1]["deferred"]},
+        "per_sample": {"members": entries / T, "coins": coins / T},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "RR sets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

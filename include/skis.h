@@ -1,0 +1,202 @@
+/*
+ * skis.h — C ABI of the SKIS GB300 library.
+ *
+ * The library implements the data-parallel hot path of the SKIS method of
+ * Nguyen, Dinh, Thai, "Importance Sketching of Influence Dynamics in
+ * Billion-scale Networks" (arXiv 1709.03565) on one NVIDIA GB300 (sm_103a):
+ * importance sampling of non-singular reverse-reachable sets under the
+ * Independent Cascade model (Sec. III, Alg. 1), the SKIS influence estimator
+ * (Sec. IV, Eq. 21, Alg. 2) and greedy max-coverage (Sec. V, Alg. 3).
+ *
+ * Conventions for every entry point:
+ *   - Return value: a skis_status code. No exceptions cross the ABI and the
+ *     library never aborts. skis_last_error() gives a message for the last
+ *     failing call of the calling thread.
+ *   - Ownership: the library allocates and owns all device memory behind its
+ *     handles (stream-ordered, on the stream of the call). Input arrays
+ *     belong to the caller and are copied; output buffers are allocated by
+ *     the caller. A graph must outlive every sketch made from it.
+ *   - Streams: cuda_stream is a cudaStream_t (NULL = legacy default stream).
+ *     Calls on one handle must be ordered: issue them on one stream, or
+ *     synchronise between streams. Entry points that return values to the
+ *     host (statuses, counts, host outputs) synchronise that stream.
+ *     skis_graph_free / skis_sketch_free release memory on the stream of the
+ *     handle's last call, which must still exist.
+ *   - Memory spaces: where a call takes SKIS_MEM_HOST or SKIS_MEM_DEVICE,
+ *     the pointers it names are host or device pointers accordingly.
+ *   - Determinism: sample j of a sketch is a pure function of (graph, seed,
+ *     j). The same graph in any input edge order, the same seed and the same
+ *     ids give identical samples, coverage counts and greedy seed sets,
+ *     whatever the launch configuration.
+ *   - Exactness: thresholds, gamma, the source law, coverage counts and the
+ *     greedy keys are integers; only the final estimate is a binary64
+ *     quotient of two exact integers.
+ */
+#ifndef SKIS_H
+#define SKIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct skis_graph skis_graph;
+typedef struct skis_sketch skis_sketch;
+
+typedef enum skis_status {
+    SKIS_OK = 0,
+    SKIS_EINVAL = 1,           /* bad argument or bad input data */
+    SKIS_ENOMEM = 2,           /* device or host allocation failed */
+    SKIS_ERR_CUDA = 3,         /* a CUDA call failed (message has the CUDA error) */
+    SKIS_ERR_RETRY_LIMIT = 4,  /* a conditioned first step hit the retry cap */
+    SKIS_ERR_ARENA_FULL = 5,   /* the sketch arena could not be grown */
+    SKIS_ERR_ABORTED = 6       /* device-side work stopped on a bounded wait */
+} skis_status;
+
+/* Edge-probability models (Sec. II-A; Sec. VI "Weight Settings"). Every
+ * probability becomes an integer threshold tau = floor(p * 2^32); an edge is
+ * live iff its 32-bit Philox coin word x satisfies x < tau.
+ * tau = 0xFFFFFFFF is the sentinel "always live" (p >= 1 - 2^-32). */
+typedef enum skis_weight_model {
+    SKIS_W_EXPLICIT_P = 0,   /* weights = double p[m], each in [0, 1], no NaN */
+    SKIS_W_EXPLICIT_TAU = 1, /* weights = uint32 tau[m] */
+    SKIS_W_WC = 2,           /* weighted cascade: p = 1 / d_in(v), as
+                                tau = floor(2^32 / d_in(v)), sentinel if d_in = 1;
+                                weights = NULL */
+    SKIS_W_TRI = 3           /* trivalency: p uniform over {0.1, 0.01, 0.001},
+                                drawn per canonical edge position from Philox
+                                keyed by weight_seed; weights = NULL */
+} skis_weight_model;
+
+typedef enum skis_mem_space { SKIS_MEM_HOST = 0, SKIS_MEM_DEVICE = 1 } skis_mem_space;
+
+typedef struct skis_graph_info {
+    int64_t n, m;
+    uint64_t W;        /* Gamma in fixed point: Gamma~ = W / 2^f */
+    int32_t f;         /* fractional bits: gamma~_v = w_v / 2^f, f = 61 - ceil(log2 n) */
+    int32_t row_uniform_tau; /* 1 when every in-row has one threshold (WC) */
+    double Gamma;      /* W / 2^f as binary64 (informational) */
+} skis_graph_info;
+
+typedef struct skis_stats {
+    uint64_t T;              /* samples in the sketch (ids 0 .. T-1) */
+    uint64_t entries;        /* sum of |R_j| */
+    uint64_t coins;          /* sum over samples of in-edges examined (see skis_sample) */
+    uint64_t retries;        /* sum of rejected first-step rounds */
+    uint64_t arena_capacity; /* entries the arena can hold before it grows */
+    uint64_t arena_reserved; /* entries reserved so far (>= entries) */
+    uint64_t deferred;       /* samples of the last skis_sample call that ran on the CTA tier */
+    double last_warp_ms;     /* device time of the last warp-tier sampling launch */
+    double last_cta_ms;      /* device time of the last CTA-tier sampling launch */
+    double last_sample_ms;   /* device time of the whole last skis_sample call */
+} skis_stats;
+
+typedef enum skis_option {
+    SKIS_OPT_RETRY_CAP = 0,   /* cap on rejected first-step rounds (default 2^24) */
+    SKIS_OPT_CTA_SLOTS = 1,   /* CTAs of the large-sample tier (default 2 per SM) */
+    SKIS_OPT_WARP_BLOCKS = 2  /* CTAs of the warp tier (default: full occupancy) */
+} skis_option;
+
+/* Load G = (V, E, w) (Sec. II-A) and build the device structures every later
+ * step reads:
+ *   - the canonical in-CSR: rows by destination, each row sorted by
+ *     (source, input index); edge id = CSR position;
+ *   - thresholds tau (per edge, or per row for WC);
+ *   - gamma_v = 1 - prod over in-edges (1 - w(u,v)) (Eq. gamma_v, Sec. III-A)
+ *     in fixed point: Q = 2^62, Q <- floor(Q (2^32 - tau) / 2^32) along the
+ *     row (Q = 0 on a sentinel), w_v = (2^62 - Q) >> (ceil(log2 n) + 1);
+ *   - W = sum_v w_v (Gamma = sum gamma_v) and the alias table of the source
+ *     law Pr[src = v] = w_v / W (Eq. probu).
+ * src, dst: int32[m] vertex ids in [0, n); weights: see skis_weight_model;
+ * all three in mem_space. Rejected with SKIS_EINVAL: n < 1, n > 2^31,
+ * m < 0, m >= 2^32 - 8, an id outside [0, n), a self-loop, p outside [0, 1]
+ * or NaN. Parallel edges are kept as independent coins. */
+int skis_load_graph(skis_graph **out, int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                    const void *weights, int weight_model, uint64_t weight_seed, int mem_space,
+                    void *cuda_stream);
+
+int skis_graph_get_info(const skis_graph *g, skis_graph_info *info);
+
+/* Copy the graph's device structures to host arrays (any may be NULL):
+ * offsets int64[n+1], csr_src int32[m], tau uint32[m] (per-edge thresholds,
+ * expanded for WC), perm int64[m] (CSR position -> input index),
+ * w uint64[n], prob uint64[n], alias uint32[n]. Synchronises the stream. */
+int skis_graph_export(const skis_graph *g, int64_t *offsets, int32_t *csr_src, uint32_t *tau,
+                      int64_t *perm, uint64_t *w, uint64_t *prob, uint32_t *alias,
+                      void *cuda_stream);
+
+void skis_graph_free(skis_graph *g);
+
+/* Create an empty SKIS sketch R (Alg. 2, preprocessing) over g with the
+ * given Philox key. arena_entries is the initial capacity of the member
+ * arena (0 = a default); the arena grows on demand. */
+int skis_sketch_create(skis_sketch **out, const skis_graph *g, uint64_t seed,
+                       uint64_t arena_entries, void *cuda_stream);
+
+int skis_sketch_set_option(skis_sketch *s, int option, uint64_t value);
+
+/* Append IIS samples (Alg. 1) with ids [T, T + count) to the sketch. For
+ * sample j:
+ *   - source: Philox block (key seed, domain SRC, id j) gives col = floor(U1 n)
+ *     and y = floor(U2 W); src = col if y < prob[col] else alias[col];
+ *   - first step (Alg. 1 lines 2-6, Eq. probn) by rejection: round
+ *     r = 0, 1, ... flips every in-edge coin of src (domain FIRST, retry r)
+ *     until one is live; its live in-neighbours join R_j;
+ *   - reverse BFS (Alg. 1 lines 7-11): every in-edge e of every other member
+ *     gets the coin (domain BFS, sample j, edge e); live edges add their
+ *     source. R_j is the reverse-reachable set of src in that live-edge world.
+ * Counters per sample: retries r, coins = d_in(src)(r + 1) + sum of d_in
+ * over the other members. Returns SKIS_ERR_RETRY_LIMIT (the failing samples
+ * are left empty) if a first step reaches the retry cap, SKIS_EINVAL if
+ * W = 0 (no non-singular sample exists). Synchronises the stream.
+ * next_sample_id_out (nullable) receives the new T. */
+int skis_sample(skis_sketch *s, uint64_t count, uint64_t *next_sample_id_out, void *cuda_stream);
+
+/* Influence queries (Alg. 2 line 2, Eq. 21): for each seed set S_b, b <
+ * num_queries, given as CSR (seed_offsets int64[q+1], seeds int32[...]):
+ *   coverage_out[b] = Cov_R(S_b) = #{j : R_j meets S_b},
+ *   estimate_out[b] = N / D with N = Cov W + T sum_{v in S_b} (2^f - w_v) and
+ *   D = T 2^f, i.e. Cov/T Gamma~ + sum (1 - gamma~_v).
+ * Pointers in mem_space; coverage_out may be NULL. Rejected with
+ * SKIS_EINVAL: T = 0, an empty seed set, a seed outside [0, n), a seed
+ * repeated within a set. Synchronises the stream. */
+int skis_estimate(skis_sketch *s, int32_t num_queries, const int64_t *seed_offsets,
+                  const int32_t *seeds, int64_t *coverage_out, double *estimate_out, int mem_space,
+                  void *cuda_stream);
+
+/* Greedy max-coverage on the sketch (Alg. 3): k rounds, each adds the vertex
+ * v outside S maximising Eq. margin, compared exactly as the integer key
+ * Delta_R(v, S) W + T (2^f - w_v); ties go to the lowest vertex id.
+ * seeds_out int32[k], coverage_out int64[k] (cumulative Cov_R, nullable) and
+ * estimate_out double[k] (I_R of each prefix, nullable) are host arrays.
+ * Rejected with SKIS_EINVAL: k < 0, k > n, T = 0. Synchronises the stream. */
+int skis_greedy_maxcover(skis_sketch *s, int32_t k, int32_t *seeds_out, int64_t *coverage_out,
+                         double *estimate_out, void *cuda_stream);
+
+int skis_sketch_stats(const skis_sketch *s, skis_stats *out);
+
+/* Copy samples [first_id, first_id + count) to host arrays (any may be
+ * NULL): src int32[count], retries uint32[count], len uint32[count],
+ * coins uint64[count], member_offsets int64[count+1] and members (the
+ * members of each sample, in device order, which is unspecified) with
+ * capacity members_cap. Returns SKIS_EINVAL if the range is outside the
+ * sketch or members_cap is too small. Synchronises the stream. */
+int skis_sketch_export(const skis_sketch *s, uint64_t first_id, uint64_t count, int32_t *src,
+                       uint32_t *retries, uint32_t *len, uint64_t *coins, int64_t *member_offsets,
+                       int32_t *members, uint64_t members_cap, void *cuda_stream);
+
+void skis_sketch_free(skis_sketch *s);
+
+/* Number of CUDA kernel launches the library has made in this process
+ * (diagnostic; counts every launch of every entry point). */
+uint64_t skis_kernel_launches(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *skis_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKIS_H */

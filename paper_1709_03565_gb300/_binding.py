@@ -1,0 +1,276 @@
+"""Thin ctypes binding of ``include/skis.h``: the same entry points, with
+argument marshalling only (pointers from numpy arrays or torch tensors,
+memory space inferred from them, stream from torch). Every step of the path
+runs in ``libskis.so``; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libskis.so")
+
+SKIS_OK, SKIS_EINVAL, SKIS_ENOMEM, SKIS_ERR_CUDA = 0, 1, 2, 3
+SKIS_ERR_RETRY_LIMIT, SKIS_ERR_ARENA_FULL, SKIS_ERR_ABORTED = 4, 5, 6
+SKIS_W_EXPLICIT_P, SKIS_W_EXPLICIT_TAU, SKIS_W_WC, SKIS_W_TRI = 0, 1, 2, 3
+SKIS_MEM_HOST, SKIS_MEM_DEVICE = 0, 1
+SKIS_OPT_RETRY_CAP, SKIS_OPT_CTA_SLOTS, SKIS_OPT_WARP_BLOCKS = 0, 1, 2
+
+
+class SkisError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[skis status {code}] {msg}")
+        self.code = code
+
+
+class skis_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("W", ctypes.c_uint64), ("f", ctypes.c_int32),
+                ("row_uniform_tau", ctypes.c_int32), ("Gamma", ctypes.c_double)]
+
+
+class skis_stats(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_uint64), ("entries", ctypes.c_uint64), ("coins", ctypes.c_uint64),
+                ("retries", ctypes.c_uint64), ("arena_capacity", ctypes.c_uint64),
+                ("arena_reserved", ctypes.c_uint64), ("deferred", ctypes.c_uint64),
+                ("last_warp_ms", ctypes.c_double), ("last_cta_ms", ctypes.c_double),
+                ("last_sample_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/skis.h
+_P, _I64, _U64, _I32, _INT = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int
+_SIGNATURES = [
+    ("skis_load_graph", _INT, [_P, _I64, _I64, _P, _P, _P, _INT, _U64, _INT, _P]),
+    ("skis_graph_get_info", _INT, [_P, _P]),
+    ("skis_graph_export", _INT, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    ("skis_graph_free", None, [_P]),
+    ("skis_sketch_create", _INT, [_P, _P, _U64, _U64, _P]),
+    ("skis_sketch_set_option", _INT, [_P, _INT, _U64]),
+    ("skis_sample", _INT, [_P, _U64, _P, _P]),
+    ("skis_estimate", _INT, [_P, _I32, _P, _P, _P, _P, _INT, _P]),
+    ("skis_greedy_maxcover", _INT, [_P, _I32, _P, _P, _P, _P]),
+    ("skis_sketch_stats", _INT, [_P, _P]),
+    ("skis_sketch_export", _INT, [_P, _U64, _U64, _P, _P, _P, _P, _P, _P, _U64, _P]),
+    ("skis_sketch_free", None, [_P]),
+    ("skis_kernel_launches", ctypes.c_uint64, []),
+    ("skis_last_error", ctypes.c_char_p, []),
+]
+
+
+def lib():
+    """The loaded ``libskis.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1709_03565_gb300.build()")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = h
+    return _lib
+
+
+def _check(rc: int):
+    if rc != SKIS_OK:
+        raise SkisError(rc, lib().skis_last_error().decode())
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """Pointer and memory space of a contiguous array of the given numpy dtype."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+
+        want = {np.int32: torch.int32, np.int64: torch.int64, np.uint32: torch.uint32,
+                np.uint64: torch.uint64, np.float64: torch.float64}[dtype]
+        if x.dtype != want:
+            raise TypeError(f"expected {want}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), (SKIS_MEM_DEVICE if x.is_cuda else SKIS_MEM_HOST)
+    if not isinstance(x, np.ndarray) or x.dtype != np.dtype(dtype) or not x.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    return ctypes.c_void_p(x.ctypes.data), SKIS_MEM_HOST
+
+
+def _space(*spaces):
+    s = {x for x in spaces if x is not None}
+    if len(s) > 1:
+        raise ValueError("all arrays of one call must be on the host or all on the device")
+    return s.pop() if s else SKIS_MEM_HOST
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, ptr, keep=None):
+        self.ptr = ptr
+        self._keep = keep
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            getattr(lib(), self._free)(self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Graph(_Handle):
+    _free = "skis_graph_free"
+
+
+class Sketch(_Handle):
+    _free = "skis_sketch_free"
+
+
+# ------------------------------------------------------------ entry points
+def skis_load_graph(n, src, dst, weights=None, weight_model=SKIS_W_WC, weight_seed=0, stream=None) -> Graph:
+    ps, ss = _ptr(src, np.int32)
+    pd, sd = _ptr(dst, np.int32)
+    wdt = np.float64 if weight_model == SKIS_W_EXPLICIT_P else np.uint32
+    pw, sw = _ptr(weights, wdt) if weight_model in (SKIS_W_EXPLICIT_P, SKIS_W_EXPLICIT_TAU) else (None, None)
+    out = ctypes.c_void_p()
+    m = int(src.shape[0])
+    _check(lib().skis_load_graph(ctypes.byref(out), int(n), m, ps, pd, pw, int(weight_model), int(weight_seed),
+                                 _space(ss, sd, sw), _stream(stream)))
+    return Graph(out)
+
+
+def skis_graph_get_info(g: Graph) -> dict:
+    info = skis_graph_info()
+    _check(lib().skis_graph_get_info(g.ptr, ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def skis_graph_export(g: Graph, stream=None) -> dict:
+    info = skis_graph_get_info(g)
+    n, m = info["n"], info["m"]
+    a = dict(off=np.empty(n + 1, np.int64), src=np.empty(m, np.int32), tau=np.empty(m, np.uint32),
+             perm=np.empty(m, np.int64), w=np.empty(n, np.uint64), prob=np.empty(n, np.uint64),
+             alias=np.empty(n, np.uint32))
+    P = lambda k: ctypes.c_void_p(a[k].ctypes.data)  # noqa: E731
+    _check(lib().skis_graph_export(g.ptr, P("off"), P("src"), P("tau"), P("perm"), P("w"), P("prob"),
+                                   P("alias"), _stream(stream)))
+    return a
+
+
+def skis_graph_free(g: Graph):
+    g.close()
+
+
+def skis_sketch_create(g: Graph, seed: int, arena_entries: int = 0, stream=None) -> Sketch:
+    out = ctypes.c_void_p()
+    _check(lib().skis_sketch_create(ctypes.byref(out), g.ptr, int(seed), int(arena_entries), _stream(stream)))
+    return Sketch(out, keep=g)
+
+
+def skis_sketch_set_option(s: Sketch, option: int, value: int):
+    _check(lib().skis_sketch_set_option(s.ptr, int(option), int(value)))
+
+
+def skis_sample(s: Sketch, count: int, stream=None) -> int:
+    nxt = ctypes.c_uint64()
+    _check(lib().skis_sample(s.ptr, int(count), ctypes.byref(nxt), _stream(stream)))
+    return nxt.value
+
+
+def skis_estimate(s: Sketch, seed_offsets, seeds, coverage_out=None, estimate_out=None, stream=None):
+    """Eq. 21 for a batch of seed sets (CSR). Host arrays in -> numpy out;
+    device tensors in -> the caller's device output tensors are filled."""
+    po, so = _ptr(seed_offsets, np.int64)
+    pz, sz = _ptr(seeds, np.int32)
+    q = int(seed_offsets.shape[0]) - 1
+    space = _space(so, sz)
+    if estimate_out is None:
+        if space == SKIS_MEM_DEVICE:
+            raise ValueError("device queries need device output tensors")
+        estimate_out = np.empty(q, np.float64)
+        coverage_out = np.empty(q, np.int64) if coverage_out is None else coverage_out
+    pe, se = _ptr(estimate_out, np.float64)
+    pc, sc = _ptr(coverage_out, np.int64)
+    if _space(space, se, sc) != space:
+        raise ValueError("outputs must be in the memory space of the queries")
+    _check(lib().skis_estimate(s.ptr, q, po, pz, pc, pe, space, _stream(stream)))
+    return coverage_out, estimate_out
+
+
+def skis_greedy_maxcover(s: Sketch, k: int, stream=None):
+    seeds = np.empty(k, np.int32)
+    cov = np.empty(k, np.int64)
+    est = np.empty(k, np.float64)
+    _check(lib().skis_greedy_maxcover(s.ptr, int(k), ctypes.c_void_p(seeds.ctypes.data),
+                                      ctypes.c_void_p(cov.ctypes.data), ctypes.c_void_p(est.ctypes.data),
+                                      _stream(stream)))
+    return seeds, cov, est
+
+
+def skis_sketch_stats(s: Sketch) -> dict:
+    st = skis_stats()
+    _check(lib().skis_sketch_stats(s.ptr, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def skis_sketch_export(s: Sketch, first_id: int, count: int, stream=None) -> dict:
+    a = dict(src=np.empty(count, np.int32), retries=np.empty(count, np.uint32), len=np.empty(count, np.uint32),
+             coins=np.empty(count, np.uint64), member_off=np.empty(count + 1, np.int64))
+    P = lambda k: ctypes.c_void_p(a[k].ctypes.data)  # noqa: E731
+    st = _stream(stream)
+    _check(lib().skis_sketch_export(s.ptr, int(first_id), int(count), P("src"), P("retries"), P("len"),
+                                    P("coins"), P("member_off"), None, 0, st))
+    total = int(a["member_off"][-1])
+    a["members"] = np.empty(max(total, 1), np.int32)
+    _check(lib().skis_sketch_export(s.ptr, int(first_id), int(count), None, None, None, None, None,
+                                    ctypes.c_void_p(a["members"].ctypes.data), total, st))
+    a["members"] = a["members"][:total]
+    return a
+
+
+def skis_sketch_free(s: Sketch):
+    s.close()
+
+
+def skis_kernel_launches() -> int:
+    return int(lib().skis_kernel_launches())
+
+
+def skis_last_error() -> str:
+    return lib().skis_last_error().decode()

@@ -1,0 +1,458 @@
+// Coverage counting and the SKIS estimator (Sec. IV, Eq. 21, Alg. 2) and
+// greedy max-coverage (Sec. V-A, Alg. 3, Eq. margin) on the device sketch.
+//
+// Coverage: each query of a batch of up to 64 owns one bit of a per-vertex
+// mask. A warp takes 32 consecutive samples, spreads their members over its
+// lanes, ORs the members' masks per sample in shared memory and counts, per
+// query bit, the samples whose OR has it (ballot + popcount). Counts and the
+// estimator numerator are exact integers.
+//
+// Greedy: an inverted index vertex -> samples (counting sort), marginal
+// coverage Delta_v, then per round an exact argmax of the integer key
+// Delta_v W + T (2^f - w_v) (ties to the lowest id), and the samples of the
+// chosen vertex are marked covered and their members' Delta decremented.
+#include <algorithm>
+#include <string>
+
+#include "../../include/skis.h"
+#include "skis_internal.cuh"
+
+namespace skis {
+
+constexpr int kCovThreads = 256;
+
+// Calls f(owner_lane, member) for every member of the samples held by the
+// lanes (lane i: arena offset off, length len), spread over the warp.
+template <class F>
+__device__ __forceinline__ void warp_members(uint64_t off, uint32_t len, const int32_t* __restrict__ arena, F&& f) {
+    const int lane = threadIdx.x & 31;
+    uint64_t incl = len;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const uint64_t total = __shfl_sync(kFull, incl, 31);
+    const uint64_t excl = incl - len;
+    for (uint64_t base = 0; base < total; base += 32) {
+        const uint64_t p = base + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const uint64_t v = __shfl_sync(kFull, incl, owner + step - 1);
+            if (v <= p) owner += step;
+        }
+        const uint64_t o_off = __shfl_sync(kFull, off, owner);
+        const uint64_t o_excl = __shfl_sync(kFull, excl, owner);
+        if (p < total) f(owner, arena[o_off + (p - o_excl)]);
+    }
+}
+
+// ------------------------------------------------------------- coverage
+__global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
+                            int32_t qn, int64_t n, uint64_t* __restrict__ qmask, DevStatus* st) {
+    const int lane = threadIdx.x & 31;
+    const int32_t b = q0 + (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (b >= q0 + qn) return;
+    const int64_t lo = off[b], hi = off[b + 1];
+    const uint64_t bit = 1ull << (b - q0);
+    if (hi <= lo && lane == 0) {
+        atomicOr(&st->flags, kStInval);
+        atomicMin(&st->first_bad, (unsigned long long)b);
+    }
+    for (int64_t i = lo + lane; i < hi; i += 32) {
+        const int32_t v = seeds[i];
+        bool bad = v < 0 || v >= n;
+        if (!bad) bad = (atomicOr((unsigned long long*)&qmask[v], (unsigned long long)bit) & bit) != 0;
+        if (bad) {
+            atomicOr(&st->flags, kStInval);
+            atomicMin(&st->first_bad, (unsigned long long)b);
+        }
+    }
+}
+
+__global__ void k_qmask_clear(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
+                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask) {
+    const int lane = threadIdx.x & 31;
+    const int32_t b = q0 + (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (b >= q0 + qn) return;
+    for (int64_t i = off[b] + lane; i < off[b + 1]; i += 32) {
+        const int32_t v = seeds[i];
+        if (v >= 0 && v < n) qmask[v] = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kCovThreads) k_coverage(const uint64_t* __restrict__ h_off,
+                                                          const uint32_t* __restrict__ h_len, uint64_t T,
+                                                          const int32_t* __restrict__ arena,
+                                                          const uint64_t* __restrict__ qmask,
+                                                          unsigned long long* __restrict__ cov) {
+    __shared__ unsigned long long s_acc[kCovThreads / 32][32];
+    __shared__ unsigned long long s_cnt[64];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long c_lo = 0, c_hi = 0;  // counts of queries `lane` and `lane + 32`
+    const uint64_t nwarps = (uint64_t)gridDim.x * (kCovThreads / 32);
+    const uint64_t groups = (T + 31) / 32;
+    for (uint64_t gidx = (uint64_t)blockIdx.x * (kCovThreads / 32) + wib; gidx < groups; gidx += nwarps) {
+        const uint64_t j = gidx * 32 + lane;
+        const bool valid = j < T;
+        const uint64_t off = valid ? h_off[j] : 0;
+        const uint32_t len = valid ? h_len[j] : 0;
+        s_acc[wib][lane] = 0;
+        __syncwarp();
+        unsigned long long* acc_row = s_acc[wib];
+        warp_members(off, len, arena, [&](int owner, int32_t u) {
+            const uint64_t msk = qmask[u];
+            if (msk) atomicOr(&acc_row[owner], (unsigned long long)msk);
+        });
+        __syncwarp();
+        const uint64_t acc = s_acc[wib][lane];
+        uint64_t present = acc;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) present |= __shfl_xor_sync(kFull, present, d);
+        while (present) {
+            const int b = __ffsll((long long)present) - 1;
+            present &= present - 1;
+            const unsigned c = (unsigned)__popc(__ballot_sync(kFull, (acc >> b) & 1ull));
+            if (lane == (b & 31)) {
+                if (b < 32) c_lo += c;
+                else c_hi += c;
+            }
+        }
+    }
+    if (c_lo) atomicAdd(&s_cnt[lane], c_lo);
+    if (c_hi) atomicAdd(&s_cnt[lane + 32], c_hi);
+    __syncthreads();
+    if (threadIdx.x < 64 && s_cnt[threadIdx.x]) atomicAdd(&cov[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+// Eq. 21 with exact integers: N = Cov W + T sum_{v in S} (2^f - w_v),
+// D = T 2^f, estimate = N / D.
+__global__ void k_estimate(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
+                           int32_t qn, int64_t n, const uint64_t* __restrict__ w, int f, uint64_t W, uint64_t T,
+                           const unsigned long long* __restrict__ cov, int64_t* __restrict__ cov_out,
+                           double* __restrict__ est_out) {
+    const int lane = threadIdx.x & 31;
+    const int32_t b = q0 + (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (b >= q0 + qn) return;
+    const uint64_t one_f = 1ull << f;
+    uint64_t s = 0;  // <= |S| 2^f <= 2^61
+    for (int64_t i = off[b] + lane; i < off[b + 1]; i += 32) {
+        const int32_t v = seeds[i];
+        if (v >= 0 && v < n) s += one_f - w[v];
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(kFull, s, d);
+    if (lane == 0) {
+        const uint64_t c = cov[b - q0];
+        const u128 N = (u128)c * W + (u128)T * s;
+        const u128 D = (u128)T << f;
+        if (cov_out) cov_out[b] = (int64_t)c;
+        est_out[b] = u128_to_double(N) / u128_to_double(D);
+    }
+}
+
+#define CV_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t _e = (call);                                                   \
+        if (_e != cudaSuccess) {                                                   \
+            *err = std::string(where) + ": CUDA error: " + cudaGetErrorString(_e); \
+            return _e == cudaErrorMemoryAllocation ? SKIS_ENOMEM : SKIS_ERR_CUDA;  \
+        }                                                                          \
+    } while (0)
+
+static int coverage_blocks(uint64_t T) {
+    const uint64_t groups = (T + 31) / 32;
+    const uint64_t want = (groups + (kCovThreads / 32) - 1) / (kCovThreads / 32);
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sm_count() * 8));
+}
+
+int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds, int64_t* d_cov,
+                    double* d_est, cudaStream_t st, std::string* err) {
+    const char* where = "skis_estimate";
+    const skis_graph* g = s->g;
+    if (s->T == 0) {
+        *err = "skis_estimate: the sketch has no samples";
+        return SKIS_EINVAL;
+    }
+    if (!s->qmask) {
+        CV_CUDA(dev_alloc_t(&s->qmask, (size_t)g->n, st));
+        CV_CUDA(cudaMemsetAsync(s->qmask, 0, (size_t)g->n * sizeof(uint64_t), st));
+        CV_CUDA(dev_alloc_t(&s->qcov, 64, st));
+        CV_CUDA(dev_alloc_t(&s->qstatus, 1, st));
+    }
+    CV_CUDA(cudaMemsetAsync(s->qstatus, 0, sizeof(DevStatus), st));
+    CV_CUDA(cudaMemsetAsync(&s->qstatus->first_bad, 0xFF, sizeof(unsigned long long), st));
+    const int cblocks = coverage_blocks(s->T);
+    for (int32_t q0 = 0; q0 < q; q0 += 64) {
+        const int32_t qn = std::min<int32_t>(64, q - q0);
+        const int wb = div_up((int64_t)qn * 32, 256);
+        CV_CUDA(cudaMemsetAsync(s->qcov, 0, 64 * sizeof(unsigned long long), st));
+        k_qmask_set<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask, s->qstatus); note_launch();
+        CV_CUDA(cudaGetLastError());
+        k_coverage<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, s->qmask, s->qcov); note_launch();
+        CV_CUDA(cudaGetLastError());
+        k_estimate<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, g->w, g->f, g->W, s->T, s->qcov, d_cov, d_est); note_launch();
+        CV_CUDA(cudaGetLastError());
+        k_qmask_clear<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask); note_launch();
+        CV_CUDA(cudaGetLastError());
+    }
+    DevStatus h;
+    CV_CUDA(cudaMemcpyAsync(&h, s->qstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    CV_CUDA(cudaStreamSynchronize(st));
+    if (h.flags & kStInval) {
+        *err = "skis_estimate: query " + std::to_string(h.first_bad) +
+               " is empty, has a seed outside [0, n) or repeats a seed";
+        return SKIS_EINVAL;
+    }
+    return SKIS_OK;
+}
+
+// --------------------------------------------------------------- greedy
+__global__ void __launch_bounds__(kCovThreads) k_count_members(const uint64_t* __restrict__ h_off,
+                                                               const uint32_t* __restrict__ h_len, uint64_t T,
+                                                               const int32_t* __restrict__ arena,
+                                                               uint32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (kCovThreads / 32);
+    const uint64_t groups = (T + 31) / 32;
+    for (uint64_t gidx = (uint64_t)blockIdx.x * (kCovThreads / 32) + wib; gidx < groups; gidx += nwarps) {
+        const uint64_t j = gidx * 32 + lane;
+        const bool valid = j < T;
+        warp_members(valid ? h_off[j] : 0, valid ? h_len[j] : 0u, arena,
+                     [&](int, int32_t u) { atomicAdd(&cnt[u], 1u); });
+    }
+}
+
+__global__ void __launch_bounds__(kCovThreads) k_fill_inverted(const uint64_t* __restrict__ h_off,
+                                                               const uint32_t* __restrict__ h_len, uint64_t T,
+                                                               const int32_t* __restrict__ arena,
+                                                               const uint64_t* __restrict__ inv_off,
+                                                               uint32_t* __restrict__ fill,
+                                                               uint32_t* __restrict__ inv) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (kCovThreads / 32);
+    const uint64_t groups = (T + 31) / 32;
+    for (uint64_t gidx = (uint64_t)blockIdx.x * (kCovThreads / 32) + wib; gidx < groups; gidx += nwarps) {
+        const uint64_t j0 = gidx * 32;
+        const uint64_t j = j0 + lane;
+        const bool valid = j < T;
+        warp_members(valid ? h_off[j] : 0, valid ? h_len[j] : 0u, arena, [&](int owner, int32_t u) {
+            const uint32_t pos = atomicAdd(&fill[u], 1u);
+            inv[inv_off[u] + pos] = (uint32_t)(j0 + owner);
+        });
+    }
+}
+
+struct GreedyState {
+    unsigned long long done;     // blocks finished in the current argmax round
+    unsigned long long cov;      // Cov_R(S)
+    unsigned long long sum_c;    // sum_{v in S} (2^f - w_v), < 2^61 for |S| <= n
+    unsigned long long pad;
+};
+
+struct KeyId {
+    u128 key;
+    uint32_t id;
+    uint32_t valid;
+};
+
+__device__ __forceinline__ bool better(const KeyId& a, const KeyId& b) {
+    if (a.valid != b.valid) return a.valid > b.valid;
+    if (a.key != b.key) return a.key > b.key;
+    return a.id < b.id;
+}
+
+__device__ __forceinline__ KeyId shfl_down_keyid(const KeyId& x, int d) {
+    KeyId y;
+    y.key = shfl_down_u128(x.key, d);
+    y.id = __shfl_down_sync(kFull, x.id, d);
+    y.valid = __shfl_down_sync(kFull, x.valid, d);
+    return y;
+}
+
+__device__ KeyId block_best(KeyId b, KeyId* s_part) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const KeyId o = shfl_down_keyid(b, d);
+        if (better(o, b)) b = o;
+    }
+    if (lane == 0) s_part[wib] = b;
+    __syncthreads();
+    if (wib == 0) {
+        b = lane < (int)(blockDim.x / 32) ? s_part[lane] : KeyId{0, 0xFFFFFFFFu, 0};
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const KeyId o = shfl_down_keyid(b, d);
+            if (better(o, b)) b = o;
+        }
+    }
+    return b;  // valid in thread 0
+}
+
+// One argmax round of Alg. 3: exact key Delta_v W + T (2^f - w_v) over
+// v outside S; the last block to finish reduces the per-block winners and
+// commits round i.
+__global__ void __launch_bounds__(kCovThreads) k_argmax(const uint32_t* __restrict__ delta,
+                                                        const uint64_t* __restrict__ w,
+                                                        uint8_t* __restrict__ inS, int64_t n, uint64_t W,
+                                                        uint64_t T, int f, KeyId* __restrict__ partial,
+                                                        GreedyState* gs, int32_t round,
+                                                        int32_t* __restrict__ seeds,
+                                                        int64_t* __restrict__ cov_out,
+                                                        double* __restrict__ est_out) {
+    __shared__ KeyId s_part[kCovThreads / 32];
+    __shared__ bool s_last;
+    const uint64_t one_f = 1ull << f;
+    KeyId best{0, 0xFFFFFFFFu, 0};
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (inS[v]) continue;
+        const KeyId c{(u128)delta[v] * W + (u128)T * (one_f - w[v]), (uint32_t)v, 1u};
+        if (better(c, best)) best = c;
+    }
+    best = block_best(best, s_part);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = best;
+        __threadfence();
+        s_last = atomicAdd(&gs->done, 1ull) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    KeyId b{0, 0xFFFFFFFFu, 0};
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+        const KeyId c = partial[i];
+        if (better(c, b)) b = c;
+    }
+    __syncthreads();
+    b = block_best(b, s_part);
+    if (threadIdx.x == 0) {
+        const uint32_t v = b.id;
+        inS[v] = 1;
+        gs->cov += delta[v];
+        gs->sum_c += one_f - w[v];
+        gs->done = 0;
+        seeds[round] = (int32_t)v;
+        cov_out[round] = (int64_t)gs->cov;
+        const u128 N = (u128)gs->cov * W + (u128)T * gs->sum_c;
+        const u128 D = (u128)T << f;
+        est_out[round] = u128_to_double(N) / u128_to_double(D);
+    }
+}
+
+// Mark the still-uncovered samples of the chosen vertex covered and remove
+// their members' marginal coverage.
+__global__ void __launch_bounds__(kCovThreads) k_cover(const int32_t* __restrict__ seeds, int32_t round,
+                                                       const uint64_t* __restrict__ inv_off,
+                                                       const uint32_t* __restrict__ inv,
+                                                       const uint64_t* __restrict__ h_off,
+                                                       const uint32_t* __restrict__ h_len,
+                                                       const int32_t* __restrict__ arena,
+                                                       uint32_t* __restrict__ covered,
+                                                       uint32_t* __restrict__ delta) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int32_t v = seeds[round];
+    const uint64_t lo = inv_off[v], cnt = inv_off[v + 1] - lo;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (kCovThreads / 32);
+    for (uint64_t base = ((uint64_t)blockIdx.x * (kCovThreads / 32) + wib) * 32; base < cnt; base += nwarps * 32) {
+        const uint64_t x = base + lane;
+        uint64_t off = 0;
+        uint32_t len = 0;
+        if (x < cnt) {
+            const uint32_t j = inv[lo + x];
+            const uint32_t bit = 1u << (j & 31);
+            if ((atomicOr(&covered[j >> 5], bit) & bit) == 0) {
+                off = h_off[j];
+                len = h_len[j];
+            }
+        }
+        warp_members(off, len, arena, [&](int, int32_t u) { atomicSub(&delta[u], 1u); });
+    }
+}
+
+int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, double* h_est, cudaStream_t st,
+                  std::string* err) {
+    const char* where = "skis_greedy_maxcover";
+    const skis_graph* g = s->g;
+    const int64_t n = g->n;
+    const uint64_t T = s->T;
+    if (k < 0 || k > n) {
+        *err = "skis_greedy_maxcover: k must be in [0, n]";
+        return SKIS_EINVAL;
+    }
+    if (T == 0 || T >= (1ull << 32)) {
+        *err = "skis_greedy_maxcover: the sketch must hold between 1 and 2^32 - 1 samples";
+        return SKIS_EINVAL;
+    }
+    if (k == 0) return SKIS_OK;
+    uint32_t *cnt = nullptr, *fill = nullptr, *inv = nullptr, *covered = nullptr;
+    uint64_t* inv_off = nullptr;
+    uint8_t* inS = nullptr;
+    KeyId* partial = nullptr;
+    GreedyState* gs = nullptr;
+    int32_t* d_seeds = nullptr;
+    int64_t* d_cov = nullptr;
+    double* d_est = nullptr;
+    uint64_t E = 0;
+    int rc = SKIS_OK;
+    const int cblocks = coverage_blocks(T);
+    const int ablocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * 2, (n + 255) / 256));
+    auto body = [&]() -> int {
+        CV_CUDA(dev_alloc_t(&cnt, (size_t)n, st));
+        CV_CUDA(dev_alloc_t(&fill, (size_t)n, st));
+        CV_CUDA(dev_alloc_t(&inv_off, (size_t)n + 1, st));
+        CV_CUDA(dev_alloc_t(&inS, (size_t)n, st));
+        CV_CUDA(dev_alloc_t(&covered, (size_t)((T + 31) / 32), st));
+        CV_CUDA(dev_alloc_t(&partial, (size_t)ablocks, st));
+        CV_CUDA(dev_alloc_t(&gs, 1, st));
+        CV_CUDA(dev_alloc_t(&d_seeds, (size_t)k, st));
+        CV_CUDA(dev_alloc_t(&d_cov, (size_t)k, st));
+        CV_CUDA(dev_alloc_t(&d_est, (size_t)k, st));
+        CV_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), st));
+        CV_CUDA(cudaMemsetAsync(fill, 0, (size_t)n * sizeof(uint32_t), st));
+        CV_CUDA(cudaMemsetAsync(inS, 0, (size_t)n, st));
+        CV_CUDA(cudaMemsetAsync(covered, 0, (size_t)((T + 31) / 32) * sizeof(uint32_t), st));
+        CV_CUDA(cudaMemsetAsync(gs, 0, sizeof(GreedyState), st));
+        // Delta_R(v, {}) = number of samples containing v, and the inverted index
+        k_count_members<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, T, s->arena, cnt); note_launch();
+        CV_CUDA(cudaGetLastError());
+        CV_CUDA(scan_u32_to_u64(cnt, inv_off, n, st));
+        CV_CUDA(cudaMemcpyAsync(&E, inv_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        CV_CUDA(cudaStreamSynchronize(st));
+        CV_CUDA(dev_alloc_t(&inv, (size_t)std::max<uint64_t>(E, 1), st));
+        k_fill_inverted<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, T, s->arena, inv_off, fill, inv); note_launch();
+        CV_CUDA(cudaGetLastError());
+        const int cover_blocks = sm_count() * 4;
+        for (int32_t i = 0; i < k; ++i) {
+            k_argmax<<<ablocks, kCovThreads, 0, st>>>(cnt, g->w, inS, n, g->W, T, g->f, partial, gs, i, d_seeds,
+                                                      d_cov, d_est); note_launch();
+            CV_CUDA(cudaGetLastError());
+            k_cover<<<cover_blocks, kCovThreads, 0, st>>>(d_seeds, i, inv_off, inv, s->h_off, s->h_len, s->arena,
+                                                          covered, cnt); note_launch();
+            CV_CUDA(cudaGetLastError());
+        }
+        CV_CUDA(cudaMemcpyAsync(h_seeds, d_seeds, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if (h_cov) CV_CUDA(cudaMemcpyAsync(h_cov, d_cov, (size_t)k * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        if (h_est) CV_CUDA(cudaMemcpyAsync(h_est, d_est, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CV_CUDA(cudaStreamSynchronize(st));
+        return SKIS_OK;
+    };
+    rc = body();
+    dev_free(cnt, st);
+    dev_free(fill, st);
+    dev_free(inv, st);
+    dev_free(covered, st);
+    dev_free(inv_off, st);
+    dev_free(inS, st);
+    dev_free(partial, st);
+    dev_free(gs, st);
+    dev_free(d_seeds, st);
+    dev_free(d_cov, st);
+    dev_free(d_est, st);
+    return rc;
+}
+
+}  // namespace skis

@@ -1,0 +1,367 @@
+// Graph build on the device (Sec. II-A, Sec. III-A components 1 and 2):
+// input validation, the canonical in-CSR, integer thresholds, gamma_v in
+// fixed point (Eq. gamma_v) and the alias table of the source law
+// Pr[src = v] = gamma_v / Gamma (Eq. probu).
+#include <string>
+
+#include "../../include/skis.h"
+#include "skis_internal.cuh"
+
+namespace skis {
+
+#define GB_CUDA(call)                                                         \
+    do {                                                                      \
+        cudaError_t _e = (call);                                              \
+        if (_e != cudaSuccess) {                                              \
+            *err = std::string("CUDA error in graph build: ") + cudaGetErrorString(_e); \
+            rc = _e == cudaErrorMemoryAllocation ? SKIS_ENOMEM : SKIS_ERR_CUDA; \
+            goto cleanup;                                                     \
+        }                                                                     \
+    } while (0)
+
+// tau = floor(p * 2^32) (p * 2^32 is exact in binary64), clamped to the
+// always-live sentinel; p >= 1 is always live.
+__device__ __forceinline__ uint32_t tau_from_p(double p) {
+    if (p >= 1.0) return kSentinel;
+    const uint64_t t = (uint64_t)(p * 4294967296.0);
+    return t >= kSentinel ? kSentinel : (uint32_t)t;
+}
+
+__global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                           const double* __restrict__ p, int64_t m, int64_t n, DevStatus* st) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = src[e], v = dst[e];
+        bool bad = u < 0 || u >= n || v < 0 || v >= n || u == v;
+        if (p) {
+            const double x = p[e];
+            bad = bad || !(x >= 0.0 && x <= 1.0);
+        }
+        if (bad) {
+            atomicOr(&st->flags, kStInval);
+            atomicMin(&st->first_bad, (unsigned long long)e);
+        }
+    }
+}
+
+// Sort key (dst, src) packed as dst << src_bits | src; the value is the input
+// index, so the stable sort breaks ties by input order.
+__global__ void k_make_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
+                            int src_bits, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        keys[e] = ((uint64_t)(uint32_t)dst[e] << src_bits) | (uint64_t)(uint32_t)src[e];
+        vals[e] = (uint32_t)e;
+    }
+}
+
+__global__ void k_degree(const int32_t* __restrict__ dst, int64_t m, uint32_t* __restrict__ cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[dst[e]], 1u);
+}
+
+// CSR arrays from the sorted pairs; per-edge thresholds by model. Padding
+// positions (m .. m_pad) get source 0 and threshold 0 (never live).
+__global__ void k_gather_edges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t m,
+                               int64_t m_pad, int src_bits, int model, const void* __restrict__ weights,
+                               uint64_t weight_seed, int32_t* __restrict__ csr_src, uint32_t* __restrict__ csr_tau,
+                               uint32_t* __restrict__ perm) {
+    const uint64_t mask = (1ull << src_bits) - 1;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m_pad; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e >= m) {
+            csr_src[e] = 0;
+            if (csr_tau) csr_tau[e] = 0;
+            continue;
+        }
+        const uint32_t idx = vals[e];
+        csr_src[e] = (int32_t)(keys[e] & mask);
+        perm[e] = idx;
+        if (!csr_tau) continue;
+        uint32_t t;
+        if (model == SKIS_W_EXPLICIT_P) {
+            t = tau_from_p(((const double*)weights)[idx]);
+        } else if (model == SKIS_W_EXPLICIT_TAU) {
+            t = ((const uint32_t*)weights)[idx];
+        } else {  // SKIS_W_TRI: level floor(3 x / 2^32) of the WEIGHT coin of position e
+            const uint4 x = coin_block(weight_seed, (uint64_t)e >> 2, 0, kDomWeight, 0);
+            const uint32_t level = (uint32_t)(((uint64_t)word_of(x, (int)(e & 3)) * 3u) >> 32);
+            t = tau_from_p(level == 0 ? 0.1 : level == 1 ? 0.01 : 0.001);
+        }
+        csr_tau[e] = t;
+    }
+}
+
+__global__ void k_rows(const uint64_t* __restrict__ off, int64_t n, int wc, RowInfo* __restrict__ rows) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        RowInfo r;
+        r.off = off[v];
+        r.deg = (uint32_t)(off[v + 1] - off[v]);
+        r.tau = 0;
+        if (wc) r.tau = r.deg == 1 ? kSentinel : (r.deg ? (uint32_t)((1ull << 32) / r.deg) : 0u);
+        rows[v] = r;
+    }
+}
+
+// Eq. gamma_v in fixed point: Q = 2^62; Q <- floor(Q (2^32 - tau) / 2^32) for
+// each in-edge in CSR order (0 on a sentinel); w_v = (2^62 - Q) >> s.
+__global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __restrict__ csr_tau, int64_t n, int s,
+                        uint64_t* __restrict__ w) {
+    const uint64_t one62 = 1ull << 62;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const RowInfo r = rows[v];
+        uint64_t Q = one62;
+        for (uint32_t k = 0; k < r.deg && Q != 0; ++k) {
+            const uint32_t t = csr_tau ? csr_tau[r.off + k] : r.tau;
+            if (t == kSentinel) Q = 0;
+            else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t)) >> 32);
+        }
+        w[v] = (one62 - Q) >> s;
+    }
+}
+
+// ------------------------------------------------------------- alias table
+// Parallel form of the sweeping alias construction (Huebschle-Schneider and
+// Sanders, "Parallel Weighted Random Sampling", ESA 2019) in integers.
+// Columns hold W; item v has mass w_v n. Light items (mass < W) and heavy
+// items are taken in ascending vertex order; D = exclusive prefix sums of the
+// light deficits W - mass, E = inclusive prefix sums of the heavy excesses
+// mass - W. Light item i aliases the first heavy j with E_j >= D_i. Heavy j
+// closes its own column with r = W + E_j - D_c, c = #{i : D_i <= E_j}; if
+// r < W it aliases heavy j+1, else r = W and it aliases itself.
+__global__ void k_alias_classify(const uint64_t* __restrict__ w, int64_t n, const unsigned long long* __restrict__ dW,
+                                 uint32_t* __restrict__ is_light) {
+    const uint64_t W = *dW;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        is_light[v] = (w[v] * (uint64_t)n < W) ? 1u : 0u;
+}
+
+__global__ void k_alias_compact(const uint64_t* __restrict__ w, int64_t n, const unsigned long long* __restrict__ dW,
+                                const uint64_t* __restrict__ light_idx, uint32_t* __restrict__ light_ids,
+                                uint32_t* __restrict__ heavy_ids, u128* __restrict__ deficit,
+                                u128* __restrict__ excess) {
+    const uint64_t W = *dW;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t mass = w[v] * (uint64_t)n;
+        const uint64_t li = light_idx[v];
+        if (light_idx[v + 1] != li) {  // light
+            light_ids[li] = (uint32_t)v;
+            deficit[li] = (u128)(W - mass);
+        } else {
+            const uint64_t hi = (uint64_t)v - li;
+            heavy_ids[hi] = (uint32_t)v;
+            excess[hi] = (u128)(mass - W);
+        }
+    }
+}
+
+__global__ void k_alias_light(int64_t nl, const uint32_t* __restrict__ light_ids, const uint64_t* __restrict__ w,
+                              int64_t n, const u128* __restrict__ D, const u128* __restrict__ Ex, int64_t nh,
+                              const uint32_t* __restrict__ heavy_ids, AliasEntry* __restrict__ table) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nl; i += (int64_t)gridDim.x * blockDim.x) {
+        const u128 target = D[i];
+        // first j in [0, nh) with Ex[j+1] >= target (exists: Ex[nh] = D[nl] > D[i])
+        int64_t lo = 0, hi = nh - 1;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (Ex[mid + 1] >= target) hi = mid;
+            else lo = mid + 1;
+        }
+        const uint32_t v = light_ids[i];
+        AliasEntry a;
+        a.prob = w[v] * (uint64_t)n;
+        a.alias = heavy_ids[lo];
+        a.pad = 0;
+        table[v] = a;
+    }
+}
+
+__global__ void k_alias_heavy(int64_t nh, const uint32_t* __restrict__ heavy_ids, const u128* __restrict__ D,
+                              int64_t nl, const u128* __restrict__ Ex, const unsigned long long* __restrict__ dW,
+                              AliasEntry* __restrict__ table) {
+    const uint64_t W = *dW;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nh; j += (int64_t)gridDim.x * blockDim.x) {
+        const u128 E = Ex[j + 1];
+        // c = #{i < nl : D[i] <= E}
+        int64_t lo = 0, hi = nl;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (D[mid] <= E) lo = mid + 1;
+            else hi = mid;
+        }
+        const u128 r = (u128)W + E - D[lo];
+        const uint32_t v = heavy_ids[j];
+        AliasEntry a;
+        a.pad = 0;
+        if (r < (u128)W && j + 1 < nh) {  // j + 1 < nh always holds when sum(mass) = n W
+            a.prob = (uint64_t)r;
+            a.alias = heavy_ids[j + 1];
+        } else {
+            a.prob = W;
+            a.alias = v;
+        }
+        table[v] = a;
+    }
+}
+
+__global__ void k_alias_empty(int64_t n, AliasEntry* __restrict__ table) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        AliasEntry a;
+        a.prob = 0;
+        a.alias = (uint32_t)v;
+        a.pad = 0;
+        table[v] = a;
+    }
+}
+
+static int bits_for(int64_t n) {  // bits needed to hold values 0 .. n-1
+    int b = 0;
+    while (b < 63 && ((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+void graph_release(skis_graph* g) {
+    cudaStream_t st = g->stream;
+    dev_free(g->off, st);
+    dev_free(g->rows, st);
+    dev_free(g->src, st);
+    dev_free(g->tau, st);
+    dev_free(g->perm, st);
+    dev_free(g->w, st);
+    dev_free(g->alias, st);
+    g->off = nullptr; g->rows = nullptr; g->src = nullptr; g->tau = nullptr;
+    g->perm = nullptr; g->w = nullptr; g->alias = nullptr;
+}
+
+int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const void* d_weights, int model,
+                uint64_t weight_seed, cudaStream_t st, std::string* err) {
+    int rc = SKIS_OK;
+    const int64_t n = g->n, m = g->m;
+    const int grid = sm_count() * 8, block = 256;
+    const int src_bits = bits_for(n);
+    const int key_bits = 2 * src_bits;
+    // temporaries
+    DevStatus* d_status = nullptr;
+    unsigned long long* d_W = nullptr;
+    uint64_t *keys = nullptr, *keys_s = nullptr, *keys_alt = nullptr;
+    uint32_t *vals = nullptr, *vals_s = nullptr, *vals_alt = nullptr, *cnt = nullptr;
+    uint32_t *is_light = nullptr, *light_ids = nullptr, *heavy_ids = nullptr;
+    uint64_t* light_idx = nullptr;
+    u128 *deficit = nullptr, *excess = nullptr, *D = nullptr, *Ex = nullptr;
+    DevStatus h_status;
+    uint64_t nl = 0, nh = 0;
+
+    g->s = bits_for(n) + 1;  // ceil(log2 n) + 1
+    g->f = 62 - g->s;
+    g->row_uniform = (model == SKIS_W_WC);
+    g->m_pad = ((m + 3) / 4) * 4 + 4;
+
+    GB_CUDA(dev_alloc_t(&d_status, 1, st));
+    GB_CUDA(dev_alloc_t(&d_W, 1, st));
+    GB_CUDA(cudaMemsetAsync(d_status, 0, sizeof(DevStatus), st));
+    GB_CUDA(cudaMemsetAsync(&d_status->first_bad, 0xFF, sizeof(unsigned long long), st));
+
+    // validation first: nothing below may index with an unchecked id
+    if (m > 0) {
+        k_validate<<<grid, block, 0, st>>>(d_src, d_dst, model == SKIS_W_EXPLICIT_P ? (const double*)d_weights : nullptr,
+                                           m, n, d_status); note_launch();
+        GB_CUDA(cudaGetLastError());
+    }
+    GB_CUDA(cudaMemcpyAsync(&h_status, d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    if (h_status.flags & kStInval) {
+        *err = "skis_load_graph: invalid edge at input index " + std::to_string(h_status.first_bad) +
+               " (vertex id outside [0, n), self-loop, or p outside [0, 1] / NaN)";
+        rc = SKIS_EINVAL;
+        goto cleanup;
+    }
+
+    // canonical in-CSR
+    GB_CUDA(dev_alloc_t(&g->off, (size_t)n + 1, st));
+    GB_CUDA(dev_alloc_t(&g->rows, (size_t)n, st));
+    GB_CUDA(dev_alloc_t(&g->src, (size_t)g->m_pad, st));
+    GB_CUDA(dev_alloc_t(&g->perm, (size_t)(m > 0 ? m : 1), st));
+    if (!g->row_uniform) GB_CUDA(dev_alloc_t(&g->tau, (size_t)g->m_pad, st));
+    GB_CUDA(dev_alloc_t(&g->w, (size_t)n, st));
+    GB_CUDA(dev_alloc_t(&g->alias, (size_t)n, st));
+    GB_CUDA(dev_alloc_t(&cnt, (size_t)n, st));
+    GB_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), st));
+    if (m > 0) {
+        GB_CUDA(dev_alloc_t(&keys, (size_t)m, st));
+        GB_CUDA(dev_alloc_t(&keys_s, (size_t)m, st));
+        GB_CUDA(dev_alloc_t(&keys_alt, (size_t)m, st));
+        GB_CUDA(dev_alloc_t(&vals, (size_t)m, st));
+        GB_CUDA(dev_alloc_t(&vals_s, (size_t)m, st));
+        GB_CUDA(dev_alloc_t(&vals_alt, (size_t)m, st));
+        k_make_keys<<<grid, block, 0, st>>>(d_src, d_dst, m, src_bits, keys, vals); note_launch();
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(radix_sort_pairs(keys, vals, keys_s, vals_s, keys_alt, vals_alt, m, key_bits, st));
+        k_degree<<<grid, block, 0, st>>>(d_dst, m, cnt); note_launch();
+        GB_CUDA(cudaGetLastError());
+    }
+    GB_CUDA(scan_u32_to_u64(cnt, g->off, n, st));
+    k_gather_edges<<<grid, block, 0, st>>>(keys_s, vals_s, m, g->m_pad, src_bits, model, d_weights, weight_seed,
+                                           g->src, g->tau, g->perm); note_launch();
+    GB_CUDA(cudaGetLastError());
+    k_rows<<<grid, block, 0, st>>>(g->off, n, g->row_uniform, g->rows); note_launch();
+    GB_CUDA(cudaGetLastError());
+
+    // gamma in fixed point and W
+    k_gamma<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->s, g->w); note_launch();
+    GB_CUDA(cudaGetLastError());
+    GB_CUDA(sum_u64(g->w, n, d_W, st));
+
+    // alias table
+    GB_CUDA(dev_alloc_t(&is_light, (size_t)n, st));
+    GB_CUDA(dev_alloc_t(&light_idx, (size_t)n + 1, st));
+    k_alias_classify<<<grid, block, 0, st>>>(g->w, n, d_W, is_light); note_launch();
+    GB_CUDA(cudaGetLastError());
+    GB_CUDA(scan_u32_to_u64(is_light, light_idx, n, st));
+    GB_CUDA(cudaMemcpyAsync(&nl, light_idx + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(&g->W, d_W, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    nh = (uint64_t)n - nl;
+    if (g->W == 0) {
+        k_alias_empty<<<grid, block, 0, st>>>(n, g->alias); note_launch();
+        GB_CUDA(cudaGetLastError());
+    } else {
+        GB_CUDA(dev_alloc_t(&light_ids, (size_t)nl + 1, st));
+        GB_CUDA(dev_alloc_t(&heavy_ids, (size_t)nh + 1, st));
+        GB_CUDA(dev_alloc_t(&deficit, (size_t)nl + 1, st));
+        GB_CUDA(dev_alloc_t(&excess, (size_t)nh + 1, st));
+        GB_CUDA(dev_alloc_t(&D, (size_t)nl + 1, st));
+        GB_CUDA(dev_alloc_t(&Ex, (size_t)nh + 1, st));
+        k_alias_compact<<<grid, block, 0, st>>>(g->w, n, d_W, light_idx, light_ids, heavy_ids, deficit, excess); note_launch();
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(scan_u128(deficit, D, (int64_t)nl, st));
+        GB_CUDA(scan_u128(excess, Ex, (int64_t)nh, st));
+        if (nl > 0) {
+            k_alias_light<<<grid, block, 0, st>>>((int64_t)nl, light_ids, g->w, n, D, Ex, (int64_t)nh, heavy_ids,
+                                                  g->alias); note_launch();
+            GB_CUDA(cudaGetLastError());
+        }
+        k_alias_heavy<<<grid, block, 0, st>>>((int64_t)nh, heavy_ids, D, (int64_t)nl, Ex, d_W, g->alias); note_launch();
+        GB_CUDA(cudaGetLastError());
+    }
+    GB_CUDA(cudaStreamSynchronize(st));
+
+cleanup:
+    dev_free(d_status, st);
+    dev_free(d_W, st);
+    dev_free(keys, st);
+    dev_free(keys_s, st);
+    dev_free(keys_alt, st);
+    dev_free(vals, st);
+    dev_free(vals_s, st);
+    dev_free(vals_alt, st);
+    dev_free(cnt, st);
+    dev_free(is_light, st);
+    dev_free(light_idx, st);
+    dev_free(light_ids, st);
+    dev_free(heavy_ids, st);
+    dev_free(deficit, st);
+    dev_free(excess, st);
+    dev_free(D, st);
+    dev_free(Ex, st);
+    if (rc != SKIS_OK) graph_release(g);
+    return rc;
+}
+
+}  // namespace skis

@@ -1,0 +1,593 @@
+// Importance Influence Sampling (Sec. III, Alg. 1) on the device.
+//
+// Warp tier: one warp per sample. The member list doubles as the FIFO queue
+// (Alg. 1's Q is members[head .. len)) and lives in shared memory with an
+// open-addressing hash set as the visited set R_j. Edges of up to 32 queued
+// vertices are spread over the lanes one edge quad at a time, so one Philox
+// block serves the 4 coins of a quad and one 16-byte load brings their
+// thresholds and sources. A sample that outgrows the shared-memory queue is
+// handed, by id, to the CTA tier.
+//
+// CTA tier: one block per sample with a global n-bit visited bitmap and an
+// n-entry global queue per block slot.
+//
+// Both tiers compute the same R_j: every coin is a pure function of
+// (seed, sample id, domain, round, edge), so R_j is the reverse-reachable set
+// of the source in one live-edge world, whatever the order of expansion.
+#include <algorithm>
+#include <string>
+
+#include "../../include/skis.h"
+#include "skis_internal.cuh"
+
+namespace skis {
+
+constexpr int kWarpThreads = 256;  // 8 warps per block
+constexpr int kQCap = 256;         // warp-tier member capacity
+constexpr int kHCap = 512;         // warp-tier hash slots (load <= 1/2 + one insert round)
+constexpr int kHashBits = 9;
+constexpr int kIdBatch = 16;       // sample ids taken per work-cursor atomic
+constexpr uint32_t kArenaChunk = 4096;  // entries reserved per arena atomic (warp tier)
+constexpr int kCtaThreads = 512;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+struct SampleArgs {
+    const AliasEntry* __restrict__ alias;
+    const RowInfo* __restrict__ rows;
+    const int32_t* __restrict__ src;
+    const uint32_t* __restrict__ tau;  // nullptr: thresholds are per row
+    uint64_t n, W, seed;
+    const uint64_t* ids;  // nullptr: ids are first_id + t
+    uint64_t first_id, count;
+    uint32_t retry_cap;
+    uint64_t* h_off;
+    uint32_t* h_len;
+    uint32_t* h_src;
+    uint32_t* h_retries;
+    uint64_t* h_coins;
+    int32_t* arena;
+    uint64_t arena_cap;
+    SampleCounters* ctr;
+    uint64_t* defer_ids;
+    uint64_t* ovf_ids;
+    DevStatus* status;
+    uint32_t* bitmaps;
+    int32_t* queues;
+    uint64_t bitmap_words;
+};
+
+// Eq. probu through the alias table: column floor(U1 n), threshold draw
+// floor(U2 W) from the SRC-domain block of sample j.
+__device__ __forceinline__ uint32_t draw_source(const SampleArgs& a, uint64_t j) {
+    const uint4 x = coin_block(a.seed, 0, 0, kDomSrc, j);
+    const uint64_t u1 = (uint64_t)x.x | ((uint64_t)x.y << 32);
+    const uint64_t u2 = (uint64_t)x.z | ((uint64_t)x.w << 32);
+    const uint64_t col = __umul64hi(u1, a.n);
+    const uint64_t y = __umul64hi(u2, a.W);
+    const AliasEntry e = a.alias[col];
+    return y < e.prob ? (uint32_t)col : e.alias;
+}
+
+// ----------------------------------------------------------- inserters
+// Warp tier: shared-memory hash set + shared-memory member queue.
+struct WarpInserter {
+    uint32_t* hash;
+    int32_t* queue;
+    uint32_t qlen;
+    bool overflow;
+
+    __device__ __forceinline__ void insert(int32_t u) {
+        if (overflow) return;  // warp-uniform
+        bool fresh = false;
+        if (u >= 0) {
+            uint32_t h = ((uint32_t)u * 2654435761u) >> (32 - kHashBits);
+            for (;;) {
+                const uint32_t old = atomicCAS(&hash[h], kEmpty, (uint32_t)u);
+                if (old == kEmpty) { fresh = true; break; }
+                if (old == (uint32_t)u) break;
+                h = (h + 1) & (kHCap - 1);
+            }
+        }
+        const unsigned m = __ballot_sync(kFull, fresh);
+        if (m) {
+            const uint32_t pos = qlen + __popc(m & lanemask_lt());
+            if (fresh && pos < (uint32_t)kQCap) queue[pos] = u;
+            qlen += __popc(m);
+            if (qlen > (uint32_t)kQCap) overflow = true;
+        }
+        __syncwarp();
+    }
+};
+
+// CTA tier: global bitmap (test-and-set) + global queue with a shared counter.
+struct CtaInserter {
+    uint32_t* bitmap;
+    int32_t* queue;
+    uint32_t* qlen;  // shared
+    bool overflow;   // never set
+
+    __device__ __forceinline__ void insert(int32_t u) {
+        bool fresh = false;
+        if (u >= 0) {
+            const uint32_t bit = 1u << (u & 31);
+            fresh = (atomicOr(&bitmap[u >> 5], bit) & bit) == 0;
+        }
+        const unsigned m = __ballot_sync(kFull, fresh);
+        if (m) {
+            uint32_t base = 0;
+            if ((threadIdx.x & 31) == 0) base = atomicAdd(qlen, (uint32_t)__popc(m));
+            base = __shfl_sync(kFull, base, 0);
+            if (fresh) queue[base + __popc(m & lanemask_lt())] = u;
+        }
+    }
+};
+
+// Expand the in-rows held by the lanes (lane i: row off/deg/tau_row, deg = 0
+// for none): every in-edge e gets its coin (domain dom, round retry, sample
+// j); live edges offer their source to the inserter. Returns, warp-uniform,
+// whether any edge was live.
+template <class Ins>
+__device__ __forceinline__ bool expand_rows(const SampleArgs& a, uint64_t j, uint32_t dom, uint32_t retry,
+                                            uint64_t off, uint32_t deg, uint32_t tau_row, Ins& ins) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nq = deg ? (uint32_t)(((off + deg - 1) >> 2) - (off >> 2) + 1) : 0u;
+    uint32_t incl = nq;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - nq;
+    bool any = false;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t g = base + lane;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t v = __shfl_sync(kFull, incl, owner + step - 1);
+            if (v <= g) owner += step;
+        }
+        const uint64_t o_off = __shfl_sync(kFull, off, owner);
+        const uint32_t o_deg = __shfl_sync(kFull, deg, owner);
+        const uint32_t o_tau = __shfl_sync(kFull, tau_row, owner);
+        const uint32_t o_excl = __shfl_sync(kFull, excl, owner);
+        int32_t c0 = -1, c1 = -1, c2 = -1, c3 = -1;
+        if (g < total) {
+            const uint64_t q = (o_off >> 2) + (g - o_excl);
+            const uint4 x = coin_block(a.seed, q, retry, dom, j);
+            const uint4 t4 = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q)
+                                   : make_uint4(o_tau, o_tau, o_tau, o_tau);
+            const uint64_t e0 = q << 2, lo = o_off, hi = o_off + o_deg;
+            unsigned live = 0;
+            live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
+            live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
+            live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
+            live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
+            if (live) {
+                const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
+                any = true;
+                if (live & 1u) c0 = s4.x;
+                if (live & 2u) c1 = s4.y;
+                if (live & 4u) c2 = s4.z;
+                if (live & 8u) c3 = s4.w;
+            }
+        }
+        if (__any_sync(kFull, (c0 >= 0) | (c1 >= 0) | (c2 >= 0) | (c3 >= 0))) {
+            if (__any_sync(kFull, c0 >= 0)) ins.insert(c0);
+            if (__any_sync(kFull, c1 >= 0)) ins.insert(c1);
+            if (__any_sync(kFull, c2 >= 0)) ins.insert(c2);
+            if (__any_sync(kFull, c3 >= 0)) ins.insert(c3);
+            if (ins.overflow) break;
+        }
+    }
+    return __any_sync(kFull, any);
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(kFull, v, d);
+    return __shfl_sync(kFull, v, 0);
+}
+
+__device__ __forceinline__ void record_retry_failure(const SampleArgs& a, uint64_t j, uint32_t v, uint32_t r,
+                                                     uint32_t deg) {
+    a.h_off[j] = 0;
+    a.h_len[j] = 0;
+    a.h_src[j] = v;
+    a.h_retries[j] = r;
+    a.h_coins[j] = (uint64_t)deg * r;
+    atomicOr(&a.status->flags, kStRetry);
+    atomicMin(&a.status->first_bad, (unsigned long long)j);
+}
+
+// ------------------------------------------------------------- warp tier
+__global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
+    __shared__ __align__(16) uint32_t s_hash[kWarpThreads / 32][kHCap];
+    __shared__ __align__(16) int32_t s_queue[kWarpThreads / 32][kQCap];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t* hash = s_hash[wib];
+    int32_t* queue = s_queue[wib];
+    uint64_t chunk_pos = 0, chunk_end = 0;  // this warp's arena reservation
+
+    for (;;) {
+        unsigned long long t0 = 0;
+        if (lane == 0) t0 = atomicAdd(&a.ctr->work, (unsigned long long)kIdBatch);
+        t0 = __shfl_sync(kFull, t0, 0);
+        if (t0 >= a.count) break;
+        const uint64_t t1 = min((uint64_t)t0 + kIdBatch, a.count);
+        for (uint64_t t = t0; t < t1; ++t) {
+            const uint64_t j = a.ids ? a.ids[t] : a.first_id + t;
+            // clear the visited set
+#pragma unroll
+            for (int i = lane; i < kHCap / 4; i += 32)
+                reinterpret_cast<uint4*>(hash)[i] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+            __syncwarp();
+
+            // Alg. 1 line 1: the source
+            const uint32_t v = draw_source(a, j);
+            const RowInfo rv = a.rows[v];
+            WarpInserter ins{hash, queue, 0u, false};
+            ins.insert(lane == 0 ? (int32_t)v : -1);
+
+            // lines 2-6 by rejection: all in-edge coins of v, round r
+            uint32_t r = 0;
+            bool failed = false;
+            for (;;) {
+                const bool any = expand_rows(a, j, kDomFirst, r, rv.off, lane == 0 ? rv.deg : 0u, rv.tau, ins);
+                if (any) break;
+                if (++r >= a.retry_cap) { failed = true; break; }
+            }
+            if (failed) {
+                if (lane == 0) record_retry_failure(a, j, v, r, rv.deg);
+                continue;
+            }
+
+            // lines 7-11: reverse BFS over the queue, up to 32 vertices at a time
+            uint64_t coins = lane == 0 ? (uint64_t)rv.deg * (r + 1) : 0;
+            uint32_t head = 1;
+            while (head < ins.qlen && !ins.overflow) {
+                const uint32_t cnt = min(ins.qlen - head, 32u);
+                RowInfo rw;
+                rw.off = 0; rw.deg = 0; rw.tau = 0;
+                if ((uint32_t)lane < cnt) rw = a.rows[queue[head + lane]];
+                coins += rw.deg;
+                expand_rows(a, j, kDomBfs, 0, rw.off, rw.deg, rw.tau, ins);
+                head += cnt;
+            }
+            if (ins.overflow) {  // too large for shared memory: CTA tier
+                if (lane == 0) {
+                    const unsigned long long k = atomicAdd(&a.ctr->ndefer, 1ull);
+                    a.defer_ids[k] = j;
+                }
+                continue;
+            }
+            coins = warp_sum_u64(coins);
+
+            // arena append from this warp's chunk
+            const uint32_t len = ins.qlen;
+            if (chunk_end - chunk_pos < len) {
+                const uint64_t size = max((uint64_t)kArenaChunk, (uint64_t)len);
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&a.ctr->arena, (unsigned long long)size);
+                base = __shfl_sync(kFull, base, 0);
+                if (base + size > a.arena_cap) {
+                    chunk_pos = chunk_end = 0;
+                    if (lane == 0) {
+                        const unsigned long long k = atomicAdd(&a.ctr->novf, 1ull);
+                        a.ovf_ids[k] = j;
+                        atomicOr(&a.status->flags, kStArena);
+                    }
+                    continue;
+                }
+                chunk_pos = base;
+                chunk_end = base + size;
+            }
+            for (uint32_t i = lane; i < len; i += 32) a.arena[chunk_pos + i] = queue[i];
+            if (lane == 0) {
+                a.h_off[j] = chunk_pos;
+                a.h_len[j] = len;
+                a.h_src[j] = v;
+                a.h_retries[j] = r;
+                a.h_coins[j] = coins;
+            }
+            chunk_pos += len;
+            __syncwarp();
+        }
+    }
+}
+
+// -------------------------------------------------------------- CTA tier
+__global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
+    __shared__ unsigned long long s_j;
+    __shared__ uint32_t s_qlen;
+    __shared__ unsigned long long s_coins;
+    __shared__ unsigned long long s_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int kWarps = kCtaThreads / 32;
+    uint32_t* bitmap = a.bitmaps + (uint64_t)blockIdx.x * a.bitmap_words;
+    int32_t* queue = a.queues + (uint64_t)blockIdx.x * a.n;
+    const unsigned long long ndefer = a.ctr->ndefer;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long t = atomicAdd(&a.ctr->cta_work, 1ull);
+            s_j = t < ndefer ? a.defer_ids[t] : ~0ull;
+        }
+        __syncthreads();
+        const uint64_t j = s_j;
+        if (j == ~0ull) break;
+
+        const uint32_t v = draw_source(a, j);
+        const RowInfo rv = a.rows[v];
+        if (threadIdx.x == 0) {
+            bitmap[v >> 5] |= 1u << (v & 31);
+            queue[0] = (int32_t)v;
+            s_qlen = 1;
+            s_coins = 0;
+        }
+        __syncthreads();
+        CtaInserter ins{bitmap, queue, &s_qlen, false};
+
+        // first step: the source row split over the warps in whole quads
+        uint32_t r = 0;
+        bool failed = false;
+        {
+            const uint64_t q_lo = rv.off >> 2;
+            const uint64_t nq = rv.deg ? ((rv.off + rv.deg - 1) >> 2) - q_lo + 1 : 0;
+            const uint64_t per = (nq + kWarps - 1) / kWarps;
+            const uint64_t a_lo = max(rv.off, (q_lo + (uint64_t)wid * per) << 2);
+            const uint64_t a_hi = min(rv.off + rv.deg, (q_lo + (uint64_t)(wid + 1) * per) << 2);
+            const uint32_t sub_deg = a_hi > a_lo ? (uint32_t)(a_hi - a_lo) : 0u;
+            for (;;) {
+                const bool any_w = expand_rows(a, j, kDomFirst, r, a_lo, lane == 0 ? sub_deg : 0u, rv.tau, ins);
+                const int any = __syncthreads_or(any_w ? 1 : 0);
+                if (any) break;
+                if (++r >= a.retry_cap) { failed = true; break; }
+            }
+        }
+        if (failed) {
+            if (threadIdx.x == 0) {
+                record_retry_failure(a, j, v, r, rv.deg);
+                bitmap[v >> 5] = 0;
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // reverse BFS, level by level: the window [head, tail) is split over
+        // the warps, 32 vertices per warp step
+        uint64_t coins = 0;
+        uint32_t head = 1;
+        for (;;) {
+            __syncthreads();
+            const uint32_t tail = s_qlen;
+            __syncthreads();
+            if (head >= tail) break;
+            for (uint32_t base = head + 32u * wid; base < tail; base += 32u * kWarps) {
+                const uint32_t idx = base + lane;
+                RowInfo rw;
+                rw.off = 0; rw.deg = 0; rw.tau = 0;
+                if (idx < tail) rw = a.rows[queue[idx]];
+                coins += rw.deg;
+                expand_rows(a, j, kDomBfs, 0, rw.off, rw.deg, rw.tau, ins);
+            }
+            head = tail;
+        }
+        coins = warp_sum_u64(coins);
+        if (lane == 0 && coins) atomicAdd(&s_coins, (unsigned long long)coins);
+        __syncthreads();
+        const uint32_t len = s_qlen;
+        if (threadIdx.x == 0) {
+            const unsigned long long base = atomicAdd(&a.ctr->arena, (unsigned long long)len);
+            if (base + len > a.arena_cap) {
+                const unsigned long long k = atomicAdd(&a.ctr->novf, 1ull);
+                a.ovf_ids[k] = j;
+                atomicOr(&a.status->flags, kStArena);
+                s_base = ~0ull;
+            } else {
+                s_base = base;
+                a.h_off[j] = base;
+                a.h_len[j] = len;
+                a.h_src[j] = v;
+                a.h_retries[j] = r;
+                a.h_coins[j] = (uint64_t)rv.deg * (r + 1) + s_coins;
+            }
+        }
+        __syncthreads();
+        const unsigned long long base = s_base;
+        for (uint32_t i = threadIdx.x; i < len; i += kCtaThreads) {
+            const int32_t u = queue[i];
+            if (base != ~0ull) a.arena[base + i] = u;
+            bitmap[(uint32_t)u >> 5] = 0;  // restore the all-zero bitmap
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ host
+#define SK_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t _e = (call);                                                        \
+        if (_e != cudaSuccess) {                                                        \
+            *err = std::string("CUDA error in skis_sample: ") + cudaGetErrorString(_e); \
+            return _e == cudaErrorMemoryAllocation ? SKIS_ENOMEM : SKIS_ERR_CUDA;       \
+        }                                                                               \
+    } while (0)
+
+template <typename T>
+static cudaError_t grow_copy(T** p, uint64_t old_n, uint64_t new_n, cudaStream_t st) {
+    T* q = nullptr;
+    cudaError_t e = dev_alloc_t(&q, (size_t)new_n, st);
+    if (e != cudaSuccess) return e;
+    if (*p && old_n) {
+        e = cudaMemcpyAsync(q, *p, old_n * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { dev_free(q, st); return e; }
+    }
+    dev_free(*p, st);
+    *p = q;
+    return cudaSuccess;
+}
+
+static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* err) {
+    const skis_graph* g = s->g;
+    if (!s->ctr) {
+        SK_CUDA(dev_alloc_t(&s->ctr, 1, st));
+        SK_CUDA(cudaMemsetAsync(s->ctr, 0, sizeof(SampleCounters), st));
+        SK_CUDA(dev_alloc_t(&s->status, 1, st));
+        for (int i = 0; i < 4; ++i) SK_CUDA(cudaEventCreate(&s->ev[i]));
+    }
+    const uint64_t need = s->T + count;
+    if (need > s->hcap) {
+        const uint64_t nc = std::max<uint64_t>(need, s->hcap * 2);
+        SK_CUDA(grow_copy(&s->h_off, s->T, nc, st));
+        SK_CUDA(grow_copy(&s->h_len, s->T, nc, st));
+        SK_CUDA(grow_copy(&s->h_src, s->T, nc, st));
+        SK_CUDA(grow_copy(&s->h_retries, s->T, nc, st));
+        SK_CUDA(grow_copy(&s->h_coins, s->T, nc, st));
+        s->hcap = nc;
+    }
+    if (count > s->list_cap) {
+        dev_free(s->defer_ids, st);
+        dev_free(s->ovf_ids[0], st);
+        dev_free(s->ovf_ids[1], st);
+        s->defer_ids = s->ovf_ids[0] = s->ovf_ids[1] = nullptr;
+        SK_CUDA(dev_alloc_t(&s->defer_ids, (size_t)count, st));
+        SK_CUDA(dev_alloc_t(&s->ovf_ids[0], (size_t)count, st));
+        SK_CUDA(dev_alloc_t(&s->ovf_ids[1], (size_t)count, st));
+        s->list_cap = count;
+    }
+    if (!s->arena) {
+        uint64_t cap = s->arena_hint ? s->arena_hint : std::max<uint64_t>(count * 8, 1u << 20);
+        SK_CUDA(dev_alloc_t(&s->arena, (size_t)cap, st));
+        s->arena_cap = cap;
+    }
+    int slots = s->cta_slots;
+    if (slots <= 0) {
+        // two blocks per SM, within ~8 GB of per-slot bitmaps and queues
+        const uint64_t per_slot = (uint64_t)g->n * 4 + ((uint64_t)g->n + 31) / 32 * 4;
+        const uint64_t budget = 8ull << 30;
+        slots = (int)std::min<uint64_t>((uint64_t)sm_count() * 2, std::max<uint64_t>(1, budget / per_slot));
+    }
+    if (slots != s->cta_slots_alloc) {
+        dev_free(s->bitmaps, st);
+        dev_free(s->queues, st);
+        s->bitmaps = nullptr;
+        s->queues = nullptr;
+        s->bitmap_words = ((uint64_t)g->n + 31) / 32;
+        SK_CUDA(dev_alloc_t(&s->bitmaps, (size_t)(s->bitmap_words * slots), st));
+        SK_CUDA(cudaMemsetAsync(s->bitmaps, 0, s->bitmap_words * slots * sizeof(uint32_t), st));
+        SK_CUDA(dev_alloc_t(&s->queues, (size_t)((uint64_t)g->n * slots), st));
+        s->cta_slots_alloc = slots;
+    }
+    return SKIS_OK;
+}
+
+int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* err) {
+    const skis_graph* g = s->g;
+    if (g->W == 0) {
+        *err = "skis_sample: Gamma = 0, the graph has no non-singular sample";
+        return SKIS_EINVAL;
+    }
+    if (count == 0) return SKIS_OK;
+    int rc = ensure_sample_buffers(s, count, st, err);
+    if (rc != SKIS_OK) return rc;
+
+    int warp_blocks = s->warp_blocks;
+    if (warp_blocks <= 0) {
+        int per_sm = 0;
+        SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iis_warp, kWarpThreads, 0));
+        warp_blocks = sm_count() * std::max(per_sm, 1);
+    }
+    const uint64_t need_blocks = (count + kIdBatch - 1) / kIdBatch;  // at most one batch per warp... per block
+    warp_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)warp_blocks, need_blocks));
+
+    SampleArgs a;
+    a.alias = g->alias;
+    a.rows = g->rows;
+    a.src = g->src;
+    a.tau = g->row_uniform ? nullptr : g->tau;
+    a.n = (uint64_t)g->n;
+    a.W = g->W;
+    a.seed = s->seed;
+    a.ids = nullptr;
+    a.first_id = s->T;
+    a.count = count;
+    a.retry_cap = s->retry_cap;
+    a.h_off = s->h_off;
+    a.h_len = s->h_len;
+    a.h_src = s->h_src;
+    a.h_retries = s->h_retries;
+    a.h_coins = s->h_coins;
+    a.arena = s->arena;
+    a.arena_cap = s->arena_cap;
+    a.ctr = s->ctr;
+    a.defer_ids = s->defer_ids;
+    a.status = s->status;
+    a.bitmaps = s->bitmaps;
+    a.queues = s->queues;
+    a.bitmap_words = s->bitmap_words;
+
+    DevStatus hst;
+    SampleCounters hc;
+    int pass = 0;
+    s->last_warp_ms = s->last_cta_ms = s->last_sample_ms = 0;
+    s->last_deferred = 0;
+    SK_CUDA(cudaMemsetAsync(s->status, 0, sizeof(DevStatus), st));
+    SK_CUDA(cudaMemsetAsync(&s->status->first_bad, 0xFF, sizeof(unsigned long long), st));
+    for (;;) {
+        a.ovf_ids = s->ovf_ids[pass & 1];
+        // reset the per-pass cursors, keep the arena cursor
+        SK_CUDA(cudaMemsetAsync(&s->ctr->work, 0, sizeof(unsigned long long) * 2, st));
+        SK_CUDA(cudaMemsetAsync(&s->ctr->ndefer, 0, sizeof(unsigned long long) * 2, st));
+        SK_CUDA(cudaEventRecord(s->ev[0], st));
+        k_iis_warp<<<warp_blocks, kWarpThreads, 0, st>>>(a); note_launch();
+        SK_CUDA(cudaGetLastError());
+        SK_CUDA(cudaEventRecord(s->ev[1], st));
+        k_iis_cta<<<s->cta_slots_alloc, kCtaThreads, 0, st>>>(a); note_launch();
+        SK_CUDA(cudaGetLastError());
+        SK_CUDA(cudaEventRecord(s->ev[2], st));
+        SK_CUDA(cudaMemcpyAsync(&hc, s->ctr, sizeof(SampleCounters), cudaMemcpyDeviceToHost, st));
+        SK_CUDA(cudaMemcpyAsync(&hst, s->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+        SK_CUDA(cudaStreamSynchronize(st));
+        float ms_w = 0, ms_c = 0;
+        cudaEventElapsedTime(&ms_w, s->ev[0], s->ev[1]);
+        cudaEventElapsedTime(&ms_c, s->ev[1], s->ev[2]);
+        s->last_warp_ms += ms_w;
+        s->last_cta_ms += ms_c;
+        s->last_sample_ms += ms_w + ms_c;
+        s->last_deferred += hc.ndefer;
+        if (hc.novf == 0) break;
+        // some reservations did not fit: grow the arena (keeping every
+        // completed sample, all of which lie below the old capacity) and
+        // rerun exactly the samples that failed
+        const uint64_t old_cap = s->arena_cap;
+        const uint64_t new_cap = old_cap * 2 + (uint64_t)kArenaChunk * (uint64_t)warp_blocks * 8;
+        rc = [&]() -> int {
+            SK_CUDA(grow_copy(&s->arena, old_cap, new_cap, st));
+            return SKIS_OK;
+        }();
+        if (rc != SKIS_OK) {
+            *err = "skis_sample: the member arena could not grow to " + std::to_string(new_cap) + " entries";
+            return SKIS_ERR_ARENA_FULL;
+        }
+        s->arena_cap = new_cap;
+        unsigned long long cur = old_cap;
+        SK_CUDA(cudaMemcpyAsync(&s->ctr->arena, &cur, sizeof(cur), cudaMemcpyHostToDevice, st));
+        a.arena = s->arena;
+        a.arena_cap = s->arena_cap;
+        a.ids = s->ovf_ids[pass & 1];
+        a.first_id = 0;
+        a.count = hc.novf;
+        ++pass;
+    }
+    s->T += count;
+    if (hst.flags & kStRetry) {
+        *err = "skis_sample: a conditioned first step reached the retry cap (" + std::to_string(s->retry_cap) +
+               " rounds) at sample id " + std::to_string(hst.first_bad) + "; failed samples are empty";
+        return SKIS_ERR_RETRY_LIMIT;
+    }
+    return SKIS_OK;
+}
+
+}  // namespace skis

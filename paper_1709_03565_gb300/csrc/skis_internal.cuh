@@ -1,0 +1,237 @@
+// Internal declarations of the SKIS GB300 library: device data layouts,
+// the counter-based Philox coin generator, warp helpers and the launch
+// entry points shared between translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace skis {
+
+typedef unsigned __int128 u128;
+
+constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // threshold meaning "always live"
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Philox counter domains: one independent stream per use of randomness.
+enum : uint32_t { kDomSrc = 1, kDomFirst = 2, kDomBfs = 3, kDomWeight = 4 };
+
+// Per-vertex in-row record, one 16-byte load on the hot path: CSR offset of
+// the row, its length d_in(v) and, for row-uniform models (WC), the row's
+// threshold.
+struct __align__(16) RowInfo {
+    uint64_t off;
+    uint32_t deg;
+    uint32_t tau;
+};
+
+// Alias column (Eq. probu): threshold in [0, W] and the alias vertex.
+struct __align__(16) AliasEntry {
+    uint64_t prob;
+    uint32_t alias;
+    uint32_t pad;
+};
+
+// Device status word shared by kernels that can fail on the data.
+struct DevStatus {
+    unsigned int flags;
+    unsigned int pad;
+    unsigned long long first_bad;  // smallest failing index / sample id
+};
+enum : unsigned int {
+    kStRetry = 1u,      // a first step hit the retry cap
+    kStInval = 2u,      // invalid input data (ids, self-loop, p, query)
+    kStArena = 4u,      // an arena reservation did not fit
+    kStListFull = 8u,   // a deferral list overflowed (cannot happen by sizing)
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): per round,
+// the products of words 0 and 2 with the two multipliers are split into
+// high/low halves and recombined with words 1, 3 and the round key; the key
+// then advances by the two Weyl increments.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t hi_a = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo_a = 0xD2511F53u * c.x;
+        const uint32_t hi_b = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo_b = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The Philox block holding the coins of edge quad q (edges 4q .. 4q+3) of
+// sample j in domain dom and first-step round `retry`. Counter words:
+// (q mod 2^32, (q >> 32) & 0xF | retry << 4 | dom << 28, j mod 2^32, j >> 32);
+// key = (seed mod 2^32, seed >> 32). Edge e's coin is word e mod 4.
+__device__ __forceinline__ uint4 coin_block(uint64_t seed, uint64_t q, uint32_t retry, uint32_t dom,
+                                            uint64_t j) {
+    uint4 c;
+    c.x = (uint32_t)q;
+    c.y = ((uint32_t)(q >> 32) & 0xFu) | ((retry & 0xFFFFFFu) << 4) | (dom << 28);
+    c.z = (uint32_t)j;
+    c.w = (uint32_t)(j >> 32);
+    return philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ uint32_t word_of(const uint4& x, int k) {
+    return k == 0 ? x.x : k == 1 ? x.y : k == 2 ? x.z : x.w;
+}
+
+__device__ __forceinline__ bool coin_live(uint32_t x, uint32_t tau) {
+    return tau == kSentinel || x < tau;
+}
+
+// --------------------------------------------------------------- helpers
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ u128 shfl_u128(u128 v, int src) {
+    uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+    lo = __shfl_sync(kFull, lo, src);
+    hi = __shfl_sync(kFull, hi, src);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int d) {
+    uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+    lo = __shfl_down_sync(kFull, lo, d);
+    hi = __shfl_down_sync(kFull, hi, d);
+    return ((u128)hi << 64) | lo;
+}
+
+// binary64 value of an unsigned 128-bit integer (two correctly rounded
+// conversions and one rounded addition: relative error below 2^-52).
+__host__ __device__ __forceinline__ double u128_to_double(u128 v) {
+    const uint64_t hi = (uint64_t)(v >> 64), lo = (uint64_t)v;
+    return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// -------------------------------------------------------- device memory
+// Stream-ordered allocation helpers (cudaMallocAsync / cudaFreeAsync).
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+
+template <typename T>
+cudaError_t dev_alloc_t(T** p, size_t count, cudaStream_t st) {
+    return dev_alloc((void**)p, count * sizeof(T) + (count == 0 ? 16 : 0), st);
+}
+
+// ------------------------------------------------------------ primitives
+// Exclusive prefix sums with the total appended: out[0] = 0,
+// out[i] = in[0] + ... + in[i-1], out[n] = total. Temporary memory is taken
+// stream-ordered from the pool.
+cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, cudaStream_t st);
+cudaError_t scan_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t st);
+cudaError_t scan_u128(const u128* in, u128* out, int64_t n, cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+// Results land in keys_out / vals_out; the *_alt buffers are scratch of the
+// same sizes.
+cudaError_t radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                             uint32_t* vals_out, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                             int bits, cudaStream_t st);
+
+// Sum of a uint64 array (integers: order-independent), result in *out (device).
+cudaError_t sum_u64(const uint64_t* in, int64_t n, unsigned long long* out, cudaStream_t st);
+
+int sm_count();
+
+// Process-wide count of kernel launches made by the library.
+void note_launch();
+uint64_t launches();
+
+}  // namespace skis
+
+// Device-resident probabilistic graph G = (V, E, w) (C handle).
+struct skis_graph {
+    int64_t n = 0, m = 0;
+    int64_t m_pad = 0;          // edge arrays padded to a multiple of 4 (+4)
+    int32_t s = 0, f = 0;       // gamma~ = w / 2^f, s = 62 - f
+    uint64_t W = 0;             // sum of w
+    int row_uniform = 0;        // thresholds live in RowInfo.tau (WC)
+    uint64_t* off = nullptr;    // n+1 CSR offsets
+    skis::RowInfo* rows = nullptr;     // n
+    int32_t* src = nullptr;     // m_pad, CSR order, padding = 0
+    uint32_t* tau = nullptr;    // m_pad per-edge thresholds (nullptr if row_uniform)
+    uint32_t* perm = nullptr;   // m: CSR position -> input index
+    uint64_t* w = nullptr;      // n fixed-point gamma numerators
+    skis::AliasEntry* alias = nullptr;  // n
+    cudaStream_t stream = nullptr;      // stream of the last call (for release)
+};
+
+namespace skis {
+// Device cursors and counters of one skis_sample call.
+struct SampleCounters {
+    unsigned long long work;      // warp-tier id cursor
+    unsigned long long cta_work;  // CTA-tier list cursor
+    unsigned long long arena;     // arena reservation cursor (persists across calls)
+    unsigned long long ndefer;    // samples handed to the CTA tier
+    unsigned long long novf;      // samples whose arena reservation did not fit
+    unsigned long long pad[3];
+};
+}  // namespace skis
+
+// Device-resident SKIS sketch R = {R_0 .. R_{T-1}} (C handle).
+struct skis_sketch {
+    const skis_graph* g = nullptr;
+    uint64_t seed = 0;
+    uint64_t T = 0;
+    uint64_t hcap = 0;                   // header capacity
+    uint64_t* h_off = nullptr;           // arena offset of R_j
+    uint32_t* h_len = nullptr;           // |R_j| (0 for a failed sample)
+    uint32_t* h_src = nullptr;           // src(R_j)
+    uint32_t* h_retries = nullptr;       // rejected first-step rounds
+    uint64_t* h_coins = nullptr;         // in-edges examined
+    int32_t* arena = nullptr;            // members, sample after sample (with gaps)
+    uint64_t arena_cap = 0;
+    uint64_t arena_hint = 0;
+    skis::SampleCounters* ctr = nullptr;
+    skis::DevStatus* status = nullptr;
+    uint64_t* defer_ids = nullptr;
+    uint64_t* ovf_ids[2] = {nullptr, nullptr};
+    uint64_t list_cap = 0;
+    uint32_t* bitmaps = nullptr;         // CTA tier: one n-bit visited bitmap per slot
+    int32_t* queues = nullptr;           // CTA tier: one n-entry queue per slot
+    int cta_slots_alloc = 0;
+    uint64_t bitmap_words = 0;
+    // options
+    uint32_t retry_cap = 1u << 24;
+    int cta_slots = 0;                   // 0 = automatic
+    int warp_blocks = 0;                 // 0 = automatic
+    // last-call statistics
+    uint64_t last_deferred = 0;
+    double last_warp_ms = 0, last_cta_ms = 0, last_sample_ms = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // query / greedy scratch (allocated on first use)
+    uint64_t* qmask = nullptr;           // n per-vertex query bits
+    unsigned long long* qcov = nullptr;  // 64 coverage counters
+    skis::DevStatus* qstatus = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
+namespace skis {
+int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* err);
+int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds, int64_t* d_cov,
+                    double* d_est, cudaStream_t st, std::string* err);
+int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, double* h_est, cudaStream_t st,
+                  std::string* err);
+void sketch_release(skis_sketch* s);
+
+// Builds every device structure of g from device edge arrays. Returns a
+// skis_status code; *err receives a message on failure.
+int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const void* d_weights,
+                int model, uint64_t weight_seed, cudaStream_t st, std::string* err);
+void graph_release(skis_graph* g);
+}  // namespace skis

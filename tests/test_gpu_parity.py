@@ -1,0 +1,295 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, element by
+element on the same seeded inputs: graph structures, every sample's
+(src, retries, |R|, coins, member set), coverage counts, estimates (relative
+1e-12) and greedy seed sets. Bit-exact for all integers."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1709_03565_gb300 as skis
+import synth
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12  # FP64 estimate tolerance (numerator and denominator are exact integers)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    skis.build()
+    yield
+
+
+def _canon(member_off, members):
+    """Members sorted within each sample (the member order is unspecified)."""
+    lens = np.diff(member_off)
+    seg = np.repeat(np.arange(len(lens)), lens)
+    order = np.lexsort((members, seg))
+    return members[order]
+
+
+def assert_samples_equal(dev, ora):
+    assert np.array_equal(dev["src"], ora["src"])
+    assert np.array_equal(dev["retries"], ora["retries"])
+    assert np.array_equal(dev["len"].astype(np.int64), ora["len"])
+    assert np.array_equal(dev["coins"], ora["coins"])
+    assert np.array_equal(_canon(dev["member_off"], dev["members"]), _canon(ora["member_off"], ora["members"]))
+
+
+def _model(name):
+    return {"wc": (skis.SKIS_W_WC, oracle.W_WC), "p": (skis.SKIS_W_EXPLICIT_P, oracle.W_P),
+            "tau": (skis.SKIS_W_EXPLICIT_TAU, oracle.W_TAU), "tri": (skis.SKIS_W_TRI, oracle.W_TRI)}[name]
+
+
+def _pair(n, src, dst, model, weights=None, weight_seed=0):
+    dm, om = _model(model)
+    g = skis.skis_load_graph(n, src, dst, weights, dm, weight_seed)
+    o = oracle.OracleGraph(n, src, dst, weights=weights, model=om, weight_seed=weight_seed)
+    return g, o
+
+
+GRAPHS = {
+    "er-wc": lambda: (3000, *synth.er(3000, 24000, 11), "wc", None),
+    "chunglu-p": lambda: (20000, *synth.chunglu(20000, 150000, 2.1, 12), "p", synth.tri(150000, 12)),
+    "chunglu-tri": lambda: (5000, *synth.chunglu(5000, 40000, 2.1, 13), "tri", None),
+    "rmat-tau": lambda: (4096, *synth.rmat(12, 30000, 0.57, 0.19, 0.19, 14), "tau",
+                         (synth.uniform_p(30000, 14, 0.0, 0.3) * 2**32).astype(np.uint32)),
+    "tiny-ragged": lambda: (7, np.array([1, 2, 3, 4, 5, 6, 0, 2, 2], np.int32),
+                            np.array([0, 0, 0, 1, 1, 2, 3, 3, 3], np.int32), "p",
+                            np.array([0.5, 1.0, 0.2, 0.7, 0.0, 0.9, 0.3, 0.3, 1e-9])),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_graph_structures_match_oracle(name):
+    n, src, dst, model, w = GRAPHS[name]()
+    g, o = _pair(n, src, dst, model, w, weight_seed=5)
+    a, b = skis.skis_graph_export(g), o.arrays()
+    info = skis.skis_graph_get_info(g)
+    assert info["W"] == o.W and info["f"] == o.f
+    for k in ("off", "src", "tau", "perm", "w", "prob", "alias"):
+        assert np.array_equal(a[k], b[k]), k
+    g.close()
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_samples_match_oracle(name):
+    n, src, dst, model, w = GRAPHS[name]()
+    g, o = _pair(n, src, dst, model, w, weight_seed=5)
+    T = 20000
+    seed = 0x5EED0000 + len(name)
+    s = skis.skis_sketch_create(g, seed)
+    assert skis.skis_sample(s, T) == T
+    dev = skis.skis_sketch_export(s, 0, T)
+    ora = o.sample_ids(seed, np.arange(T, dtype=np.uint64))
+    assert_samples_equal(dev, ora)
+    st = skis.skis_sketch_stats(s)
+    assert st["T"] == T and st["entries"] == int(ora["len"].sum()) and st["coins"] == int(ora["coins"].sum())
+    s.close()
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def er_small():
+    """The 10,000-vertex / 100,000-edge ER workload (WC), full size."""
+    spec, src, dst, _ = synth.workload("er-1e4-wc")
+    g, o = _pair(spec["n"], src, dst, "wc")
+    seed = 0x5EED0001
+    T = spec["samples"]
+    osk = oracle.OracleSketch(o, seed, T)
+    return spec, src, dst, g, o, osk, seed, T
+
+
+def test_er_workload_full_parity(er_small):
+    spec, src, dst, g, o, osk, seed, T = er_small
+    s = skis.skis_sketch_create(g, seed)
+    skis.skis_sample(s, T)
+    st = skis.skis_sketch_stats(s)
+    assert st["deferred"] > 0  # the CTA tier took part
+    dev = skis.skis_sketch_export(s, 0, T)
+    a = osk.arrays()
+    ora = dict(src=a["src"], retries=a["retries"], len=np.diff(a["off"]), coins=a["coins"],
+               member_off=a["off"], members=a["mem"])
+    assert_samples_equal(dev, ora)
+    # estimator: 100 seed sets of 10 uniform vertices, plus ragged sizes
+    off, seeds = synth.seed_sets(spec["n"], [10] * 100 + [1, 2, 3, 500, 9999, 77], 7)
+    cov, est = skis.skis_estimate(s, off, seeds)
+    ocov, oest = osk.coverage(off, seeds)
+    assert np.array_equal(cov, ocov)
+    np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
+    # greedy max-coverage, k = 50
+    sd, sc, se = skis.skis_greedy_maxcover(s, 50)
+    od, oc, oe = osk.greedy(50)
+    assert np.array_equal(sd, od) and np.array_equal(sc, oc)
+    np.testing.assert_allclose(se, oe, rtol=REL, atol=0)
+    s.close()
+
+
+def test_results_do_not_depend_on_launch_configuration(er_small):
+    spec, src, dst, g, o, osk, seed, T = er_small
+    ref = None
+    for warp_blocks, cta_slots, arena in ((0, 0, 0), (3, 1, 1000), (1000, 7, 50_000)):
+        s = skis.skis_sketch_create(g, seed, arena)
+        if warp_blocks:
+            skis.skis_sketch_set_option(s, skis.SKIS_OPT_WARP_BLOCKS, warp_blocks)
+        if cta_slots:
+            skis.skis_sketch_set_option(s, skis.SKIS_OPT_CTA_SLOTS, cta_slots)
+        # appended in uneven pieces: ids continue across calls
+        for c in (1, 999, 30000, T - 31000):
+            skis.skis_sample(s, c)
+        dev = skis.skis_sketch_export(s, 0, T)
+        canon = (dev["src"], dev["retries"], dev["len"], dev["coins"], _canon(dev["member_off"], dev["members"]))
+        if ref is None:
+            ref = canon
+        else:
+            for x, y in zip(ref, canon):
+                assert np.array_equal(x, y)
+        s.close()
+
+
+def test_device_queries_and_batches_over_64(er_small):
+    torch = pytest.importorskip("torch")
+    spec, src, dst, g, o, osk, seed, T = er_small
+    s = skis.skis_sketch_create(g, seed)
+    skis.skis_sample(s, T)
+    sizes = synth.log_uniform_sizes(150, 1, 1000, 3)
+    off, seeds = synth.seed_sets(spec["n"], sizes, 9)
+    d_off = torch.from_numpy(off).cuda()
+    d_seeds = torch.from_numpy(seeds).cuda()
+    d_cov = torch.empty(len(sizes), dtype=torch.int64, device="cuda")
+    d_est = torch.empty(len(sizes), dtype=torch.float64, device="cuda")
+    skis.skis_estimate(s, d_off, d_seeds, d_cov, d_est)
+    torch.cuda.synchronize()
+    ocov, oest = osk.coverage(off, seeds)
+    assert np.array_equal(d_cov.cpu().numpy(), ocov)
+    np.testing.assert_allclose(d_est.cpu().numpy(), oest, rtol=REL, atol=0)
+    s.close()
+
+
+def test_bad_inputs_are_rejected():
+    n = 10
+    with pytest.raises(skis.SkisError) as e:
+        skis.skis_load_graph(n, np.array([1, 2], np.int32), np.array([0, 2], np.int32))  # self-loop
+    assert e.value.code == skis.SKIS_EINVAL
+    with pytest.raises(skis.SkisError):
+        skis.skis_load_graph(n, np.array([1, 10], np.int32), np.array([0, 0], np.int32))
+    with pytest.raises(skis.SkisError):
+        skis.skis_load_graph(n, np.array([1, 2], np.int32), np.array([0, 0], np.int32),
+                             np.array([0.5, np.nan]), skis.SKIS_W_EXPLICIT_P)
+    g = skis.skis_load_graph(n, np.array([1, 2, 3], np.int32), np.array([0, 0, 0], np.int32))
+    s = skis.skis_sketch_create(g, 1)
+    with pytest.raises(skis.SkisError):
+        skis.skis_estimate(s, np.array([0, 1], np.int64), np.array([0], np.int32))  # no samples yet
+    skis.skis_sample(s, 100)
+    for sets in ([[]], [[1, 1]], [[10]], [[-1]]):
+        off = np.concatenate([[0], np.cumsum([len(x) for x in sets])]).astype(np.int64)
+        seeds = np.array([v for x in sets for v in x], np.int32)
+        with pytest.raises(skis.SkisError) as e:
+            skis.skis_estimate(s, off, seeds)
+        assert e.value.code == skis.SKIS_EINVAL
+    with pytest.raises(skis.SkisError):
+        skis.skis_greedy_maxcover(s, n + 1)
+    s.close()
+    g.close()
+    # Gamma = 0: no non-singular sample exists
+    g = skis.skis_load_graph(3, np.array([1, 2], np.int32), np.array([0, 0], np.int32),
+                             np.array([0, 0], np.uint32), skis.SKIS_W_EXPLICIT_TAU)
+    s = skis.skis_sketch_create(g, 1)
+    with pytest.raises(skis.SkisError) as e:
+        skis.skis_sample(s, 10)
+    assert e.value.code == skis.SKIS_EINVAL
+    s.close()
+    g.close()
+
+
+def test_retry_cap_reports_error_with_the_oracle():
+    g, o = _pair(2, np.array([1], np.int32), np.array([0], np.int32), "tau", np.array([1], np.uint32))
+    s = skis.skis_sketch_create(g, 5)
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_RETRY_CAP, 8)
+    with pytest.raises(skis.SkisError) as e:
+        skis.skis_sample(s, 50)
+    assert e.value.code == skis.SKIS_ERR_RETRY_LIMIT
+    dev = skis.skis_sketch_export(s, 0, 50)
+    ora = o.sample_ids(5, np.arange(50, dtype=np.uint64), retry_cap=8)
+    assert (ora["status"] == oracle.ORC_ERETRY).all()
+    assert np.array_equal(dev["retries"], ora["retries"]) and (dev["len"] == 0).all()
+    assert np.array_equal(dev["coins"], ora["coins"])
+    s.close()
+    g.close()
+
+
+def test_always_live_giant_samples_take_the_cta_tier():
+    # every edge live on a dense ER graph: each sample is a large ancestor set
+    n, m = 6000, 30000
+    src, dst = synth.er(n, m, 21)
+    tau = np.full(m, 0xFFFFFFFF, np.uint32)
+    g, o = _pair(n, src, dst, "tau", tau)
+    s = skis.skis_sketch_create(g, 77, 1 << 16)
+    T = 300
+    skis.skis_sample(s, T)
+    st = skis.skis_sketch_stats(s)
+    assert st["deferred"] > 0 and st["arena_capacity"] > (1 << 16)  # the arena grew
+    assert_samples_equal(skis.skis_sketch_export(s, 0, T), o.sample_ids(77, np.arange(T, dtype=np.uint64)))
+    s.close()
+    g.close()
+
+
+def test_single_vertex_and_edgeless_graphs():
+    g = skis.skis_load_graph(1, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    info = skis.skis_graph_get_info(g)
+    assert info["W"] == 0 and info["m"] == 0
+    a = skis.skis_graph_export(g)
+    assert a["off"].tolist() == [0, 0]
+    g.close()
+
+
+# --------------------------------------------------- full-size workload
+@pytest.fixture(scope="module")
+def chunglu_full():
+    """The 1M-vertex / 10M-edge Chung-Lu TRI workload with 10M samples, in
+    the launch configuration the benchmark uses (defaults)."""
+    spec, src, dst, p = synth.workload("chunglu-1e6-tri")
+    seed = 0x5EED0002
+    g = skis.skis_load_graph(spec["n"], src, dst, p, skis.SKIS_W_EXPLICIT_P)
+    s = skis.skis_sketch_create(g, seed)
+    skis.skis_sample(s, spec["samples"])
+    o = oracle.OracleGraph(spec["n"], src, dst, weights=p, model=oracle.W_P)
+    yield spec, g, s, o, seed
+    s.close()
+    g.close()
+
+
+def test_full_size_graph_and_sampled_ids(chunglu_full):
+    spec, g, s, o, seed = chunglu_full
+    a, b = skis.skis_graph_export(g), o.arrays()
+    for k in ("off", "src", "tau", "perm", "w", "prob", "alias"):
+        assert np.array_equal(a[k], b[k]), k
+    T = spec["samples"]
+    dev = skis.skis_sketch_export(s, 0, T)
+    rng = np.random.default_rng(0)
+    ids = np.unique(np.concatenate([np.arange(2000), np.arange(T - 2000, T), rng.integers(0, T, 30000)]))
+    ora = o.sample_ids(seed, ids.astype(np.uint64))
+    mo = dev["member_off"]
+    sub = dict(src=dev["src"][ids], retries=dev["retries"][ids], len=dev["len"][ids], coins=dev["coins"][ids])
+    lens = np.diff(mo)[ids]
+    sub["member_off"] = np.concatenate([[0], np.cumsum(lens)])
+    sub["members"] = np.concatenate([dev["members"][mo[i]:mo[i + 1]] for i in ids])
+    assert_samples_equal(sub, ora)
+
+
+def test_full_size_greedy_and_coverage(chunglu_full):
+    spec, g, s, o, seed = chunglu_full
+    osk = oracle.OracleSketch(o, seed, spec["samples"])
+    k = spec["k"]
+    sd, sc, se = skis.skis_greedy_maxcover(s, k)
+    od, oc, oe = osk.greedy(k)
+    assert np.array_equal(sd, od) and np.array_equal(sc, oc)
+    np.testing.assert_allclose(se, oe, rtol=REL, atol=0)
+    off, seeds = synth.seed_sets(spec["n"], [10] * 64, 11)
+    cov, est = skis.skis_estimate(s, off, seeds)
+    ocov, oest = osk.coverage(off, seeds)
+    assert np.array_equal(cov, ocov)
+    np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
