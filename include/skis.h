@@ -188,6 +188,31 @@ int skis_sketch_export(const skis_sketch *s, uint64_t first_id, uint64_t count, 
 
 void skis_sketch_free(skis_sketch *s);
 
+/* skis_estimate without any allocation. The paper has no counterpart: this
+ * is a service for callers that cannot allocate device memory when they
+ * query — a process whose device memory is already reserved in full by
+ * another allocator (a framework's caching allocator or an application pool
+ * sized at start-up), where cudaMalloc would fail or fragment that
+ * reservation, and latency-critical query loops that must not pay an
+ * allocation's unbounded latency and implicit synchronisation.
+ * It answers the same queries as skis_estimate (same results) and calls no
+ * cudaMalloc, cudaFree or allocating library routine, on the device or the
+ * host. Its scratch is one static device array inside the library, held by
+ * every GPU that loads the library until the process exits: 8 MiB of
+ * per-vertex query masks plus 64 counters and a status word.
+ * Limits (SKIS_EINVAL beyond them): the graph has at most 2^20 vertices;
+ * num_queries <= 64. All pointers are DEVICE pointers except error_buf
+ * (host, nullable, error_len bytes), which receives a message on failure.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture. Every call shares the array and
+ * clears the part it needs at its start: calls that overlap on the GPU (on
+ * two streams at once, or from two threads without ordering) race and give
+ * wrong results; serialise them. Synchronises the stream. */
+int skis_estimate_noalloc(const skis_sketch *s, int32_t num_queries, const int64_t *seed_offsets,
+                          const int32_t *seeds, int64_t *coverage_out, double *estimate_out,
+                          char *error_buf, uint64_t error_len, void *cuda_stream);
+
 /* Number of CUDA kernel launches the library has made in this process
  * (diagnostic; counts every launch of every entry point). */
 uint64_t skis_kernel_launches(void);

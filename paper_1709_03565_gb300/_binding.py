@@ -59,6 +59,7 @@ _SIGNATURES = [
     ("skis_sketch_stats", _INT, [_P, _P]),
     ("skis_sketch_export", _INT, [_P, _U64, _U64, _P, _P, _P, _P, _P, _P, _U64, _P]),
     ("skis_sketch_free", None, [_P]),
+    ("skis_estimate_noalloc", _INT, [_P, _I32, _P, _P, _P, _P, _P, _U64, _P]),
     ("skis_kernel_launches", ctypes.c_uint64, []),
     ("skis_last_error", ctypes.c_char_p, []),
 ]
@@ -266,6 +267,24 @@ def skis_sketch_export(s: Sketch, first_id: int, count: int, stream=None) -> dic
 
 def skis_sketch_free(s: Sketch):
     s.close()
+
+
+def skis_estimate_noalloc(s: Sketch, seed_offsets, seeds, coverage_out, estimate_out, stream=None):
+    """skis_estimate for callers that cannot allocate: device tensors in and
+    out, at most 64 queries, graphs of at most 2^20 vertices; the library's
+    static scratch array is used instead of any allocation."""
+    po, so = _ptr(seed_offsets, np.int64)
+    pz, sz = _ptr(seeds, np.int32)
+    pc, sc = _ptr(coverage_out, np.int64)
+    pe, se = _ptr(estimate_out, np.float64)
+    if _space(so, sz, sc, se) != SKIS_MEM_DEVICE:
+        raise ValueError("skis_estimate_noalloc takes device tensors only")
+    q = int(seed_offsets.shape[0]) - 1
+    buf = ctypes.create_string_buffer(256)
+    rc = lib().skis_estimate_noalloc(s.ptr, q, po, pz, pc, pe, buf, 256, _stream(stream))
+    if rc != SKIS_OK:
+        raise SkisError(rc, buf.value.decode())
+    return coverage_out, estimate_out
 
 
 def skis_kernel_launches() -> int:

@@ -229,6 +229,17 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
                   std::string* err);
 void sketch_release(skis_sketch* s);
 
+// Coverage kernels (defined in cover.cu).
+__global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
+                            int32_t qn, int64_t n, uint64_t* __restrict__ qmask, DevStatus* st);
+__global__ void __launch_bounds__(256) k_coverage(const uint64_t* __restrict__ h_off, const uint32_t* __restrict__ h_len, uint64_t T,
+                           const int32_t* __restrict__ arena, const uint64_t* __restrict__ qmask,
+                           unsigned long long* __restrict__ cov);
+__global__ void k_estimate(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
+                           int32_t qn, int64_t n, const uint64_t* __restrict__ w, int f, uint64_t W, uint64_t T,
+                           const unsigned long long* __restrict__ cov, int64_t* __restrict__ cov_out,
+                           double* __restrict__ est_out);
+
 // Builds every device structure of g from device edge arrays. Returns a
 // skis_status code; *err receives a message on failure.
 int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const void* d_weights,
