@@ -271,6 +271,7 @@ def main():
         elapsed_ms = float(t.item())
     value = world * args.steps * T / (elapsed_ms / 1e3)
     coins, entries = stats[-1]["coins"], stats[-1]["entries"]
+    thread_ms = statistics.mean(s["last_thread_ms"] for s in stats)
     warp_ms = statistics.mean(s["last_warp_ms"] for s in stats)
     cta_ms = statistics.mean(s["last_cta_ms"] for s in stats)
     sample_ms = statistics.mean(s["last_sample_ms"] for s in stats)
@@ -321,13 +322,13 @@ def main():
 
     # ---- roofline of the dominant kernel (warp-tier IIS sampler)
     peak, peak_kind = _peaks()
-    # both sampling launches of one skis_sample call together produce the
-    # whole sketch; the warp tier carries almost all of it
+    # the three sampling launches of one skis_sample call (thread, warp and
+    # CTA tiers) together produce the whole sketch
     alg = algorithmic_bytes(T, entries, coins, per_edge_tau=True)
     achieved = alg / (sample_ms / 1e3) / 1e9
     tps = _traffic_per_sample()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tps * T if tps is not None else None), "kernel": "k_iis_warp + k_iis_cta",
+                "traffic": (tps * T if tps is not None else None), "kernel": "k_iis_thread + k_iis_warp + k_iis_cta",
                 "algorithmic_bytes": alg, "kernel_ms": sample_ms, "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
 
     # ---- CPU baseline: the oracle, as it stands, on a bounded sample
@@ -355,7 +356,9 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "sampled_edges_per_s": world * args.steps * coins / (elapsed_ms / 1e3),
         "sampling_only": {"rr_sets_per_s": T / (sample_ms / 1e3), "edges_per_s": coins / (sample_ms / 1e3),
-                          "warp_tier_ms": warp_ms, "cta_tier_ms": cta_ms, "deferred": stats[-1]["deferred"]},
+                          "thread_tier_ms": thread_ms, "warp_tier_ms": warp_ms, "cta_tier_ms": cta_ms,
+                          "to_warp_tier": stats[-1]["to_warp"], "to_cta_tier": stats[-1]["deferred"],
+                          "passes": stats[-1]["last_passes"], "arena_capacity": stats[-1]["arena_capacity"]},
         "per_sample": {"members": entries / T, "coins": coins / T},
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -86,16 +86,25 @@ typedef struct skis_stats {
     uint64_t retries;        /* sum of rejected first-step rounds */
     uint64_t arena_capacity; /* entries the arena can hold before it grows */
     uint64_t arena_reserved; /* entries reserved so far (>= entries) */
+    uint64_t to_warp;        /* samples of the last skis_sample call handed to the warp tier */
     uint64_t deferred;       /* samples of the last skis_sample call that ran on the CTA tier */
-    double last_warp_ms;     /* device time of the last warp-tier sampling launch */
-    double last_cta_ms;      /* device time of the last CTA-tier sampling launch */
-    double last_sample_ms;   /* device time of the whole last skis_sample call */
+    double last_thread_ms;   /* device time of the last thread-tier sampling launch(es) */
+    double last_warp_ms;     /* device time of the last warp-tier sampling launch(es) */
+    double last_cta_ms;      /* device time of the last CTA-tier sampling launch(es) */
+    double last_sample_ms;   /* device time of all sampling launches of the last skis_sample call */
+    uint64_t last_passes;    /* sampling passes of the last call (> 1: the arena grew and reran) */
 } skis_stats;
 
+/* Sampling runs in three tiers chained by sample id: one lane per sample
+ * (up to 16 members, in-rows up to THREAD_MAX_DEG edges), one warp per
+ * sample (up to 256 members), one CTA per sample (any size). Options tune
+ * the split; they never change the samples. */
 typedef enum skis_option {
-    SKIS_OPT_RETRY_CAP = 0,   /* cap on rejected first-step rounds (default 2^24) */
-    SKIS_OPT_CTA_SLOTS = 1,   /* CTAs of the large-sample tier (default 2 per SM) */
-    SKIS_OPT_WARP_BLOCKS = 2  /* CTAs of the warp tier (default: full occupancy) */
+    SKIS_OPT_RETRY_CAP = 0,      /* cap on rejected first-step rounds (default 2^24) */
+    SKIS_OPT_CTA_SLOTS = 1,      /* CTAs of the CTA tier (default 2 per SM) */
+    SKIS_OPT_WARP_BLOCKS = 2,    /* CTAs of the warp tier (default: full occupancy) */
+    SKIS_OPT_THREAD_MAX_DEG = 3, /* longest in-row the thread tier expands (default 256; 0 = tier off) */
+    SKIS_OPT_THREAD_BLOCKS = 4   /* CTAs of the thread tier (default: full occupancy) */
 } skis_option;
 
 /* Load G = (V, E, w) (Sec. II-A) and build the device structures every later

@@ -18,6 +18,7 @@ SKIS_ERR_RETRY_LIMIT, SKIS_ERR_ARENA_FULL, SKIS_ERR_ABORTED = 4, 5, 6
 SKIS_W_EXPLICIT_P, SKIS_W_EXPLICIT_TAU, SKIS_W_WC, SKIS_W_TRI = 0, 1, 2, 3
 SKIS_MEM_HOST, SKIS_MEM_DEVICE = 0, 1
 SKIS_OPT_RETRY_CAP, SKIS_OPT_CTA_SLOTS, SKIS_OPT_WARP_BLOCKS = 0, 1, 2
+SKIS_OPT_THREAD_MAX_DEG, SKIS_OPT_THREAD_BLOCKS = 3, 4
 
 
 class SkisError(RuntimeError):
@@ -34,9 +35,10 @@ class skis_graph_info(ctypes.Structure):
 class skis_stats(ctypes.Structure):
     _fields_ = [("T", ctypes.c_uint64), ("entries", ctypes.c_uint64), ("coins", ctypes.c_uint64),
                 ("retries", ctypes.c_uint64), ("arena_capacity", ctypes.c_uint64),
-                ("arena_reserved", ctypes.c_uint64), ("deferred", ctypes.c_uint64),
+                ("arena_reserved", ctypes.c_uint64), ("to_warp", ctypes.c_uint64),
+                ("deferred", ctypes.c_uint64), ("last_thread_ms", ctypes.c_double),
                 ("last_warp_ms", ctypes.c_double), ("last_cta_ms", ctypes.c_double),
-                ("last_sample_ms", ctypes.c_double)]
+                ("last_sample_ms", ctypes.c_double), ("last_passes", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

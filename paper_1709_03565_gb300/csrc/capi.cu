@@ -188,6 +188,14 @@ extern "C" int skis_sketch_set_option(skis_sketch* s, int option, uint64_t value
             if (value > (1u << 20)) return fail(SKIS_EINVAL, "warp blocks must be at most 2^20");
             s->warp_blocks = (int)value;
             return SKIS_OK;
+        case SKIS_OPT_THREAD_MAX_DEG:
+            if (value > (1u << 30)) return fail(SKIS_EINVAL, "thread-tier degree limit must be at most 2^30");
+            s->thread_max_deg = (uint32_t)value;
+            return SKIS_OK;
+        case SKIS_OPT_THREAD_BLOCKS:
+            if (value > (1u << 20)) return fail(SKIS_EINVAL, "thread blocks must be at most 2^20");
+            s->thread_blocks = (int)value;
+            return SKIS_OK;
         default:
             return fail(SKIS_EINVAL, "skis_sketch_set_option: unknown option");
     }
@@ -306,10 +314,13 @@ extern "C" int skis_sketch_stats(const skis_sketch* s, skis_stats* out) {
     std::fill((char*)out, (char*)out + sizeof(skis_stats), 0);
     out->T = s->T;
     out->arena_capacity = s->arena_cap;
+    out->to_warp = s->last_to_warp;
     out->deferred = s->last_deferred;
+    out->last_thread_ms = s->last_thread_ms;
     out->last_warp_ms = s->last_warp_ms;
     out->last_cta_ms = s->last_cta_ms;
     out->last_sample_ms = s->last_sample_ms;
+    out->last_passes = s->last_passes;
     if (s->T == 0) return SKIS_OK;
     cudaStream_t st = s->stream;
     unsigned long long* d = nullptr;
@@ -401,7 +412,8 @@ void skis::sketch_release(skis_sketch* s) {
     dev_free(s->arena, st);
     dev_free(s->ctr, st);
     dev_free(s->status, st);
-    dev_free(s->defer_ids, st);
+    dev_free(s->to_warp_ids, st);
+    dev_free(s->to_cta_ids, st);
     dev_free(s->ovf_ids[0], st);
     dev_free(s->ovf_ids[1], st);
     dev_free(s->bitmaps, st);

@@ -294,28 +294,41 @@ __device__ KeyId block_best(KeyId b, KeyId* s_part) {
 }
 
 // One argmax round of Alg. 3: exact key Delta_v W + T (2^f - w_v) over
-// v outside S; the last block to finish reduces the per-block winners and
-// commits round i.
+// v outside S. Vertices are grouped in cells of kCell; a cell keeps its best
+// (key, id) from the previous round and is recomputed only when marked dirty
+// (a member's Delta changed or its best joined S). The last block to finish
+// reduces the cell winners and commits round i.
+constexpr int kCellShift = 10;
+constexpr int kCell = 1 << kCellShift;
+
 __global__ void __launch_bounds__(kCovThreads) k_argmax(const uint32_t* __restrict__ delta,
                                                         const uint64_t* __restrict__ w,
                                                         uint8_t* __restrict__ inS, int64_t n, uint64_t W,
-                                                        uint64_t T, int f, KeyId* __restrict__ partial,
-                                                        GreedyState* gs, int32_t round,
-                                                        int32_t* __restrict__ seeds,
+                                                        uint64_t T, int f, KeyId* __restrict__ cell_best,
+                                                        uint32_t* __restrict__ dirty, GreedyState* gs,
+                                                        int32_t round, int32_t* __restrict__ seeds,
                                                         int64_t* __restrict__ cov_out,
                                                         double* __restrict__ est_out) {
     __shared__ KeyId s_part[kCovThreads / 32];
     __shared__ bool s_last;
     const uint64_t one_f = 1ull << f;
-    KeyId best{0, 0xFFFFFFFFu, 0};
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        if (inS[v]) continue;
-        const KeyId c{(u128)delta[v] * W + (u128)T * (one_f - w[v]), (uint32_t)v, 1u};
-        if (better(c, best)) best = c;
+    const unsigned cell = blockIdx.x;
+    if (dirty[cell]) {  // block-uniform
+        KeyId best{0, 0xFFFFFFFFu, 0};
+        const int64_t lo = (int64_t)cell << kCellShift;
+        const int64_t hi = min(lo + kCell, n);
+        for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+            if (inS[v]) continue;
+            const KeyId c{(u128)delta[v] * W + (u128)T * (one_f - w[v]), (uint32_t)v, 1u};
+            if (better(c, best)) best = c;
+        }
+        best = block_best(best, s_part);
+        if (threadIdx.x == 0) {
+            cell_best[cell] = best;
+            dirty[cell] = 0;
+        }
     }
-    best = block_best(best, s_part);
     if (threadIdx.x == 0) {
-        partial[blockIdx.x] = best;
         __threadfence();
         s_last = atomicAdd(&gs->done, 1ull) == gridDim.x - 1;
     }
@@ -324,7 +337,12 @@ __global__ void __launch_bounds__(kCovThreads) k_argmax(const uint32_t* __restri
     __threadfence();
     KeyId b{0, 0xFFFFFFFFu, 0};
     for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
-        const KeyId c = partial[i];
+        KeyId c;
+        c.key = ((u128)__ldcg(reinterpret_cast<const unsigned long long*>(&cell_best[i]) + 1) << 64) |
+                (u128)__ldcg(reinterpret_cast<const unsigned long long*>(&cell_best[i]));
+        const unsigned long long tail = __ldcg(reinterpret_cast<const unsigned long long*>(&cell_best[i]) + 2);
+        c.id = (uint32_t)tail;
+        c.valid = (uint32_t)(tail >> 32);
         if (better(c, b)) b = c;
     }
     __syncthreads();
@@ -332,6 +350,7 @@ __global__ void __launch_bounds__(kCovThreads) k_argmax(const uint32_t* __restri
     if (threadIdx.x == 0) {
         const uint32_t v = b.id;
         inS[v] = 1;
+        dirty[v >> kCellShift] = 1;  // its cell must forget v
         gs->cov += delta[v];
         gs->sum_c += one_f - w[v];
         gs->done = 0;
@@ -344,7 +363,7 @@ __global__ void __launch_bounds__(kCovThreads) k_argmax(const uint32_t* __restri
 }
 
 // Mark the still-uncovered samples of the chosen vertex covered and remove
-// their members' marginal coverage.
+// their members' marginal coverage; cells of changed vertices become dirty.
 __global__ void __launch_bounds__(kCovThreads) k_cover(const int32_t* __restrict__ seeds, int32_t round,
                                                        const uint64_t* __restrict__ inv_off,
                                                        const uint32_t* __restrict__ inv,
@@ -352,7 +371,7 @@ __global__ void __launch_bounds__(kCovThreads) k_cover(const int32_t* __restrict
                                                        const uint32_t* __restrict__ h_len,
                                                        const int32_t* __restrict__ arena,
                                                        uint32_t* __restrict__ covered,
-                                                       uint32_t* __restrict__ delta) {
+                                                       uint32_t* __restrict__ delta, uint32_t* __restrict__ dirty) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int32_t v = seeds[round];
     const uint64_t lo = inv_off[v], cnt = inv_off[v + 1] - lo;
@@ -369,7 +388,10 @@ __global__ void __launch_bounds__(kCovThreads) k_cover(const int32_t* __restrict
                 len = h_len[j];
             }
         }
-        warp_members(off, len, arena, [&](int, int32_t u) { atomicSub(&delta[u], 1u); });
+        warp_members(off, len, arena, [&](int, int32_t u) {
+            atomicSub(&delta[u], 1u);
+            dirty[(uint32_t)u >> kCellShift] = 1;
+        });
     }
 }
 
@@ -391,7 +413,8 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
     uint32_t *cnt = nullptr, *fill = nullptr, *inv = nullptr, *covered = nullptr;
     uint64_t* inv_off = nullptr;
     uint8_t* inS = nullptr;
-    KeyId* partial = nullptr;
+    KeyId* cell_best = nullptr;
+    uint32_t* dirty = nullptr;
     GreedyState* gs = nullptr;
     int32_t* d_seeds = nullptr;
     int64_t* d_cov = nullptr;
@@ -399,14 +422,15 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
     uint64_t E = 0;
     int rc = SKIS_OK;
     const int cblocks = coverage_blocks(T);
-    const int ablocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * 2, (n + 255) / 256));
+    const int ncells = (int)((n + kCell - 1) >> kCellShift);
     auto body = [&]() -> int {
         CV_CUDA(dev_alloc_t(&cnt, (size_t)n, st));
         CV_CUDA(dev_alloc_t(&fill, (size_t)n, st));
         CV_CUDA(dev_alloc_t(&inv_off, (size_t)n + 1, st));
         CV_CUDA(dev_alloc_t(&inS, (size_t)n, st));
         CV_CUDA(dev_alloc_t(&covered, (size_t)((T + 31) / 32), st));
-        CV_CUDA(dev_alloc_t(&partial, (size_t)ablocks, st));
+        CV_CUDA(dev_alloc_t(&cell_best, (size_t)ncells, st));
+        CV_CUDA(dev_alloc_t(&dirty, (size_t)ncells, st));
         CV_CUDA(dev_alloc_t(&gs, 1, st));
         CV_CUDA(dev_alloc_t(&d_seeds, (size_t)k, st));
         CV_CUDA(dev_alloc_t(&d_cov, (size_t)k, st));
@@ -416,6 +440,7 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
         CV_CUDA(cudaMemsetAsync(inS, 0, (size_t)n, st));
         CV_CUDA(cudaMemsetAsync(covered, 0, (size_t)((T + 31) / 32) * sizeof(uint32_t), st));
         CV_CUDA(cudaMemsetAsync(gs, 0, sizeof(GreedyState), st));
+        CV_CUDA(cudaMemsetAsync(dirty, 0x01, (size_t)ncells * sizeof(uint32_t), st));  // any nonzero = dirty
         // Delta_R(v, {}) = number of samples containing v, and the inverted index
         k_count_members<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, T, s->arena, cnt); note_launch();
         CV_CUDA(cudaGetLastError());
@@ -427,11 +452,11 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
         CV_CUDA(cudaGetLastError());
         const int cover_blocks = sm_count() * 4;
         for (int32_t i = 0; i < k; ++i) {
-            k_argmax<<<ablocks, kCovThreads, 0, st>>>(cnt, g->w, inS, n, g->W, T, g->f, partial, gs, i, d_seeds,
-                                                      d_cov, d_est); note_launch();
+            k_argmax<<<ncells, kCovThreads, 0, st>>>(cnt, g->w, inS, n, g->W, T, g->f, cell_best, dirty, gs, i,
+                                                     d_seeds, d_cov, d_est); note_launch();
             CV_CUDA(cudaGetLastError());
             k_cover<<<cover_blocks, kCovThreads, 0, st>>>(d_seeds, i, inv_off, inv, s->h_off, s->h_len, s->arena,
-                                                          covered, cnt); note_launch();
+                                                          covered, cnt, dirty); note_launch();
             CV_CUDA(cudaGetLastError());
         }
         CV_CUDA(cudaMemcpyAsync(h_seeds, d_seeds, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -447,7 +472,8 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
     dev_free(covered, st);
     dev_free(inv_off, st);
     dev_free(inS, st);
-    dev_free(partial, st);
+    dev_free(cell_best, st);
+    dev_free(dirty, st);
     dev_free(gs, st);
     dev_free(d_seeds, st);
     dev_free(d_cov, st);

@@ -1,17 +1,25 @@
-// Importance Influence Sampling (Sec. III, Alg. 1) on the device.
+// Importance Influence Sampling (Sec. III, Alg. 1) on the device, in three
+// tiers chained by sample id.
 //
-// Warp tier: one warp per sample. The member list doubles as the FIFO queue
-// (Alg. 1's Q is members[head .. len)) and lives in shared memory with an
-// open-addressing hash set as the visited set R_j. Edges of up to 32 queued
-// vertices are spread over the lanes one edge quad at a time, so one Philox
-// block serves the 4 coins of a quad and one 16-byte load brings their
-// thresholds and sources. A sample that outgrows the shared-memory queue is
-// handed, by id, to the CTA tier.
+// Thread tier: one lane per sample. Lanes are persistent: a lane that
+// finishes claims the next id while its neighbours carry on, so a warp keeps
+// 32 independent samples in flight and one warp instruction advances 32 of
+// them by one edge quad (one Philox block = the 4 coins of a quad). The member
+// list (which is also Alg. 1's FIFO queue Q = members[head .. len)) holds up to
+// 16 vertices per lane in shared memory, laid out so that entry k of lane l is
+// word 32 k + l (no bank conflicts whatever k each lane uses). A sample whose
+// member list outgrows it, or that meets an in-row longer than the degree
+// threshold, is handed by id to the warp tier.
+//
+// Warp tier: one warp per sample. The member list (256 entries) and an
+// open-addressing hash set (the visited set R_j) live in shared memory. Edges
+// of up to 32 queued vertices are spread over the lanes one edge quad at a
+// time. A sample that outgrows it is handed, by id, to the CTA tier.
 //
 // CTA tier: one block per sample with a global n-bit visited bitmap and an
 // n-entry global queue per block slot.
 //
-// Both tiers compute the same R_j: every coin is a pure function of
+// All tiers compute the same R_j: every coin is a pure function of
 // (seed, sample id, domain, round, edge), so R_j is the reverse-reachable set
 // of the source in one live-edge world, whatever the order of expansion.
 #include <algorithm>
@@ -27,8 +35,12 @@ constexpr int kQCap = 256;         // warp-tier member capacity
 constexpr int kHCap = 512;         // warp-tier hash slots (load <= 1/2 + one insert round)
 constexpr int kHashBits = 9;
 constexpr int kIdBatch = 16;       // sample ids taken per work-cursor atomic
-constexpr uint32_t kArenaChunk = 4096;  // entries reserved per arena atomic (warp tier)
+constexpr uint32_t kArenaChunk = 2048;        // entries reserved per arena atomic (warp tier)
+constexpr uint32_t kThreadArenaChunk = 512;   // entries reserved per arena atomic (thread tier)
 constexpr int kCtaThreads = 512;
+constexpr int kThreadQ = 16;       // thread-tier member capacity per lane
+constexpr uint32_t kThreadMaxRetries = 8;  // rejected rounds before the warp tier takes over
+constexpr int kThreadBlock = 256;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 struct SampleArgs {
@@ -37,9 +49,19 @@ struct SampleArgs {
     const int32_t* __restrict__ src;
     const uint32_t* __restrict__ tau;  // nullptr: thresholds are per row
     uint64_t n, W, seed;
-    const uint64_t* ids;  // nullptr: ids are first_id + t
-    uint64_t first_id, count;
     uint32_t retry_cap;
+    uint32_t max_deg;                  // thread tier: longest in-row it expands
+    // input ids: first_id + t (ids == nullptr) or ids[t], t < count (or
+    // t < *count_dev when the list was filled by the previous tier)
+    const uint64_t* ids;
+    uint64_t first_id, count;
+    const unsigned long long* count_dev;
+    unsigned long long* work;          // id cursor of this launch
+    uint64_t* out_ids;                 // samples handed to the next tier
+    unsigned long long* out_count;
+    uint64_t* ovf_ids;                 // samples whose arena reservation did not fit
+    unsigned long long* novf;
+    unsigned long long* arena_cursor;
     uint64_t* h_off;
     uint32_t* h_len;
     uint32_t* h_src;
@@ -47,14 +69,30 @@ struct SampleArgs {
     uint64_t* h_coins;
     int32_t* arena;
     uint64_t arena_cap;
-    SampleCounters* ctr;
-    uint64_t* defer_ids;
-    uint64_t* ovf_ids;
     DevStatus* status;
     uint32_t* bitmaps;
     int32_t* queues;
     uint64_t bitmap_words;
 };
+
+__device__ __forceinline__ uint64_t input_count(const SampleArgs& a) {
+    return a.count_dev ? (uint64_t)*a.count_dev : a.count;
+}
+
+__device__ __forceinline__ uint64_t input_id(const SampleArgs& a, uint64_t t) {
+    return a.ids ? a.ids[t] : a.first_id + t;
+}
+
+__device__ __forceinline__ void hand_on(const SampleArgs& a, uint64_t j) {
+    const unsigned long long k = atomicAdd(a.out_count, 1ull);
+    a.out_ids[k] = j;
+}
+
+__device__ __forceinline__ void arena_overflow(const SampleArgs& a, uint64_t j) {
+    const unsigned long long k = atomicAdd(a.novf, 1ull);
+    a.ovf_ids[k] = j;
+    atomicOr(&a.status->flags, kStArena);
+}
 
 // Eq. probu through the alias table: column floor(U1 n), threshold draw
 // floor(U2 W) from the SRC-domain block of sample j.
@@ -184,6 +222,65 @@ __device__ __forceinline__ bool expand_rows(const SampleArgs& a, uint64_t j, uin
     return __any_sync(kFull, any);
 }
 
+// Alg. 1 lines 2-6 for one warp: the rejection rounds r = 0, 1, ... of the
+// source row, until one round has a live coin; the live in-neighbours of that
+// round are inserted. Rounds are independent given (j, r), so a short row
+// (nq <= 16 edge quads) is searched 32 / nq rounds per pass: lane g takes
+// round r0 + g / nq and quad g % nq, and the lowest round with a live coin
+// (the first set lane of the ballot, as lanes are ordered by round) is the
+// accepted one, exactly as in sequential order. Longer rows take one round
+// per pass, spread over the lanes. Returns the accepted round, or the cap
+// with *failed set.
+template <class Ins>
+__device__ __forceinline__ uint32_t first_step_warp(const SampleArgs& a, uint64_t j, const RowInfo& rv, Ins& ins,
+                                                    bool* failed) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t q_first = rv.off >> 2;
+    const uint32_t nq = (uint32_t)(((rv.off + rv.deg - 1) >> 2) - q_first + 1);
+    *failed = false;
+    if (nq > 16) {
+        for (uint32_t r = 0;; ++r) {
+            if (r >= a.retry_cap) { *failed = true; return r; }
+            if (expand_rows(a, j, kDomFirst, r, rv.off, lane == 0 ? rv.deg : 0u, rv.tau, ins)) return r;
+        }
+    }
+    const uint32_t rounds = 32u / nq;
+    const uint32_t ri = (uint32_t)lane / nq, qi = (uint32_t)lane % nq;
+    const uint64_t q = q_first + qi;
+    const uint64_t e0 = q << 2, lo = rv.off, hi = rv.off + rv.deg;
+    const uint4 t4 = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q) : make_uint4(rv.tau, rv.tau, rv.tau, rv.tau);
+    for (uint32_t r0 = 0; r0 < a.retry_cap; r0 += rounds) {
+        const uint32_t r = r0 + ri;
+        unsigned live = 0;
+        if (ri < rounds && r < a.retry_cap) {
+            const uint4 x = coin_block(a.seed, q, r, kDomFirst, j);
+            live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
+            live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
+            live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
+            live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
+        }
+        const unsigned bal = __ballot_sync(kFull, live != 0);
+        if (bal) {
+            const uint32_t acc = (uint32_t)(__ffs(bal) - 1) / nq;  // accepted round = r0 + acc
+            int32_t c0 = -1, c1 = -1, c2 = -1, c3 = -1;
+            if (ri == acc && live) {
+                const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
+                if (live & 1u) c0 = s4.x;
+                if (live & 2u) c1 = s4.y;
+                if (live & 4u) c2 = s4.z;
+                if (live & 8u) c3 = s4.w;
+            }
+            if (__any_sync(kFull, c0 >= 0)) ins.insert(c0);
+            if (__any_sync(kFull, c1 >= 0)) ins.insert(c1);
+            if (__any_sync(kFull, c2 >= 0)) ins.insert(c2);
+            if (__any_sync(kFull, c3 >= 0)) ins.insert(c3);
+            return r0 + acc;
+        }
+    }
+    *failed = true;
+    return a.retry_cap;
+}
+
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(kFull, v, d);
@@ -201,6 +298,181 @@ __device__ __forceinline__ void record_retry_failure(const SampleArgs& a, uint64
     atomicMin(&a.status->first_bad, (unsigned long long)j);
 }
 
+// ----------------------------------------------------------- thread tier
+__global__ void __launch_bounds__(kThreadBlock) k_iis_thread(SampleArgs a) {
+    __shared__ int32_t s_q[kThreadBlock / 32][kThreadQ][32];
+    const int lane = threadIdx.x & 31;
+    int32_t(*const mq)[32] = s_q[threadIdx.x >> 5];  // mq[k][lane]: member k of this lane's sample
+    const uint64_t count = input_count(a);
+    const uint4* __restrict__ tau4 = reinterpret_cast<const uint4*>(a.tau);
+    const int4* __restrict__ src4 = reinterpret_cast<const int4*>(a.src);
+
+    // per-lane sample state
+    bool busy = false, first = true, any = false, rowleft = false;
+    uint64_t j = 0, qc = 0, q_first = 0, q_last = 0, lo = 0, hi = 0, coins = 0;
+    uint32_t v = 0, r = 0, len = 0, head = 0, src_deg = 0, tau_row = 0;
+    bool exhausted = false;                 // warp-uniform: no ids left to claim
+    uint64_t chunk_pos = 0, chunk_end = 0;  // this warp's arena reservation
+
+    for (;;) {
+        // idle lanes claim the next ids together (one atomic per warp)
+        const unsigned idle = __ballot_sync(kFull, !busy);
+        if (idle && !exhausted) {
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(idle));
+            base = __shfl_sync(kFull, base, leader);
+            if (base + __popc(idle) >= count) exhausted = true;
+            if (!busy) {
+                const uint64_t t = base + __popc(idle & lanemask_lt());
+                if (t < count) {
+                    j = input_id(a, t);
+                    v = draw_source(a, j);  // Alg. 1 line 1
+                    const RowInfo rv = a.rows[v];
+                    if (rv.deg > a.max_deg) {
+                        hand_on(a, j);
+                    } else {
+                        busy = true;
+                        first = true;
+                        any = false;
+                        r = 0;
+                        mq[0][lane] = (int32_t)v;
+                        len = 1;
+                        head = 1;
+                        src_deg = rv.deg;
+                        tau_row = rv.tau;
+                        lo = rv.off;
+                        hi = rv.off + rv.deg;
+                        q_first = lo >> 2;
+                        q_last = (hi - 1) >> 2;
+                        qc = q_first;
+                        rowleft = true;
+                        coins = 0;
+                    }
+                }
+            }
+        }
+        if (!__any_sync(kFull, busy)) {
+            if (exhausted) break;
+            continue;
+        }
+
+        bool done = false, handed = false, failed = false;
+        if (busy) {
+            // one edge quad of the current row: coins of lines 4-6 (first
+            // step, round r) or of line 9 (reverse BFS)
+            if (rowleft) {
+                const uint4 x = coin_block(a.seed, qc, first ? r : 0u, first ? kDomFirst : kDomBfs, j);
+                const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_row, tau_row, tau_row, tau_row);
+                const uint64_t e0 = qc << 2;
+                unsigned live = 0;
+                live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
+                live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
+                live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
+                live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
+                if (live) {
+                    any = true;
+                    const int4 s4 = __ldg(src4 + qc);
+                    const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (!((live >> k) & 1u) || handed) continue;
+                        const int32_t u = cand[k];
+                        bool seen = false;
+                        for (uint32_t i = 0; i < len; ++i)
+                            if (mq[i][lane] == u) { seen = true; break; }
+                        if (seen) continue;
+                        if (len == (uint32_t)kThreadQ) handed = true;
+                        else mq[len++][lane] = u;
+                    }
+                }
+                ++qc;
+                rowleft = qc <= q_last;
+            }
+            if (!handed && !rowleft) {
+                if (first) {  // end of a first-step round: accept it or redraw
+                    if (any) {
+                        first = false;
+                        coins = (uint64_t)src_deg * (r + 1);
+                    } else if (++r >= a.retry_cap) {
+                        failed = true;
+                    } else if (r >= kThreadMaxRetries) {
+                        handed = true;  // a rare source: the warp tier searches rounds in parallel
+                    } else {
+                        qc = q_first;
+                        rowleft = true;
+                    }
+                }
+                if (!first && !failed && !handed) {  // pop the next queued vertex
+                    if (head < len) {
+                        const RowInfo rw = a.rows[mq[head][lane]];
+                        ++head;
+                        coins += rw.deg;
+                        if (rw.deg > a.max_deg) {
+                            handed = true;
+                        } else if (rw.deg > 0) {
+                            lo = rw.off;
+                            hi = rw.off + rw.deg;
+                            tau_row = rw.tau;
+                            q_first = lo >> 2;
+                            q_last = (hi - 1) >> 2;
+                            qc = q_first;
+                            rowleft = true;
+                        }
+                    } else {
+                        done = true;
+                    }
+                }
+            }
+            if (handed) hand_on(a, j);
+            if (failed) record_retry_failure(a, j, v, r, src_deg);
+            if (handed || failed) busy = false;
+        }
+
+        // finished samples: one arena reservation for the warp's batch
+        const unsigned dm = __ballot_sync(kFull, done);
+        if (dm) {
+            const uint32_t mylen = done ? len : 0u;
+            uint32_t incl = mylen;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, d);
+                if (lane >= d) incl += y;
+            }
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            bool fits = true;
+            if (chunk_end - chunk_pos < total) {
+                const uint64_t size = max((uint64_t)kThreadArenaChunk, (uint64_t)total);
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.arena_cursor, (unsigned long long)size);
+                base = __shfl_sync(kFull, base, 0);
+                if (base + size > a.arena_cap) {
+                    fits = false;
+                    chunk_pos = chunk_end = 0;
+                } else {
+                    chunk_pos = base;
+                    chunk_end = base + size;
+                }
+            }
+            if (done) {
+                if (fits) {
+                    const uint64_t at = chunk_pos + (incl - mylen);
+                    for (uint32_t i = 0; i < len; ++i) a.arena[at + i] = mq[i][lane];
+                    a.h_off[j] = at;
+                    a.h_len[j] = len;
+                    a.h_src[j] = v;
+                    a.h_retries[j] = r;
+                    a.h_coins[j] = coins;
+                } else {
+                    arena_overflow(a, j);
+                }
+                busy = false;
+            }
+            if (fits) chunk_pos += total;
+        }
+    }
+}
+
 // ------------------------------------------------------------- warp tier
 __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
     __shared__ __align__(16) uint32_t s_hash[kWarpThreads / 32][kHCap];
@@ -210,14 +482,15 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
     int32_t* queue = s_queue[wib];
     uint64_t chunk_pos = 0, chunk_end = 0;  // this warp's arena reservation
 
+    const uint64_t count = input_count(a);
     for (;;) {
         unsigned long long t0 = 0;
-        if (lane == 0) t0 = atomicAdd(&a.ctr->work, (unsigned long long)kIdBatch);
+        if (lane == 0) t0 = atomicAdd(a.work, (unsigned long long)kIdBatch);
         t0 = __shfl_sync(kFull, t0, 0);
-        if (t0 >= a.count) break;
-        const uint64_t t1 = min((uint64_t)t0 + kIdBatch, a.count);
+        if (t0 >= count) break;
+        const uint64_t t1 = min((uint64_t)t0 + kIdBatch, count);
         for (uint64_t t = t0; t < t1; ++t) {
-            const uint64_t j = a.ids ? a.ids[t] : a.first_id + t;
+            const uint64_t j = input_id(a, t);
             // clear the visited set
 #pragma unroll
             for (int i = lane; i < kHCap / 4; i += 32)
@@ -231,13 +504,8 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
             ins.insert(lane == 0 ? (int32_t)v : -1);
 
             // lines 2-6 by rejection: all in-edge coins of v, round r
-            uint32_t r = 0;
             bool failed = false;
-            for (;;) {
-                const bool any = expand_rows(a, j, kDomFirst, r, rv.off, lane == 0 ? rv.deg : 0u, rv.tau, ins);
-                if (any) break;
-                if (++r >= a.retry_cap) { failed = true; break; }
-            }
+            const uint32_t r = first_step_warp(a, j, rv, ins, &failed);
             if (failed) {
                 if (lane == 0) record_retry_failure(a, j, v, r, rv.deg);
                 continue;
@@ -256,10 +524,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
                 head += cnt;
             }
             if (ins.overflow) {  // too large for shared memory: CTA tier
-                if (lane == 0) {
-                    const unsigned long long k = atomicAdd(&a.ctr->ndefer, 1ull);
-                    a.defer_ids[k] = j;
-                }
+                if (lane == 0) hand_on(a, j);
                 continue;
             }
             coins = warp_sum_u64(coins);
@@ -269,15 +534,11 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
             if (chunk_end - chunk_pos < len) {
                 const uint64_t size = max((uint64_t)kArenaChunk, (uint64_t)len);
                 unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&a.ctr->arena, (unsigned long long)size);
+                if (lane == 0) base = atomicAdd(a.arena_cursor, (unsigned long long)size);
                 base = __shfl_sync(kFull, base, 0);
                 if (base + size > a.arena_cap) {
                     chunk_pos = chunk_end = 0;
-                    if (lane == 0) {
-                        const unsigned long long k = atomicAdd(&a.ctr->novf, 1ull);
-                        a.ovf_ids[k] = j;
-                        atomicOr(&a.status->flags, kStArena);
-                    }
+                    if (lane == 0) arena_overflow(a, j);
                     continue;
                 }
                 chunk_pos = base;
@@ -303,16 +564,17 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
     __shared__ uint32_t s_qlen;
     __shared__ unsigned long long s_coins;
     __shared__ unsigned long long s_base;
+    __shared__ uint32_t s_r, s_failed;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int kWarps = kCtaThreads / 32;
     uint32_t* bitmap = a.bitmaps + (uint64_t)blockIdx.x * a.bitmap_words;
     int32_t* queue = a.queues + (uint64_t)blockIdx.x * a.n;
-    const unsigned long long ndefer = a.ctr->ndefer;
+    const uint64_t count = input_count(a);
 
     for (;;) {
         if (threadIdx.x == 0) {
-            const unsigned long long t = atomicAdd(&a.ctr->cta_work, 1ull);
-            s_j = t < ndefer ? a.defer_ids[t] : ~0ull;
+            const unsigned long long t = atomicAdd(a.work, 1ull);
+            s_j = t < count ? input_id(a, t) : ~0ull;
         }
         __syncthreads();
         const uint64_t j = s_j;
@@ -329,10 +591,24 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
         __syncthreads();
         CtaInserter ins{bitmap, queue, &s_qlen, false};
 
-        // first step: the source row split over the warps in whole quads
+        // first step: a short source row is searched by warp 0, several
+        // rounds per pass; a long one is split over the warps in whole quads
         uint32_t r = 0;
         bool failed = false;
-        {
+        const uint64_t nq_src = ((rv.off + rv.deg - 1) >> 2) - (rv.off >> 2) + 1;
+        if (nq_src <= 16) {
+            if (wid == 0) {
+                bool f = false;
+                const uint32_t rr = first_step_warp(a, j, rv, ins, &f);
+                if (lane == 0) {
+                    s_r = rr;
+                    s_failed = f ? 1u : 0u;
+                }
+            }
+            __syncthreads();
+            r = s_r;
+            failed = s_failed != 0;
+        } else {
             const uint64_t q_lo = rv.off >> 2;
             const uint64_t nq = rv.deg ? ((rv.off + rv.deg - 1) >> 2) - q_lo + 1 : 0;
             const uint64_t per = (nq + kWarps - 1) / kWarps;
@@ -379,11 +655,9 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
         __syncthreads();
         const uint32_t len = s_qlen;
         if (threadIdx.x == 0) {
-            const unsigned long long base = atomicAdd(&a.ctr->arena, (unsigned long long)len);
+            const unsigned long long base = atomicAdd(a.arena_cursor, (unsigned long long)len);
             if (base + len > a.arena_cap) {
-                const unsigned long long k = atomicAdd(&a.ctr->novf, 1ull);
-                a.ovf_ids[k] = j;
-                atomicOr(&a.status->flags, kStArena);
+                arena_overflow(a, j);
                 s_base = ~0ull;
             } else {
                 s_base = base;
@@ -448,11 +722,13 @@ static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st
         s->hcap = nc;
     }
     if (count > s->list_cap) {
-        dev_free(s->defer_ids, st);
+        dev_free(s->to_warp_ids, st);
+        dev_free(s->to_cta_ids, st);
         dev_free(s->ovf_ids[0], st);
         dev_free(s->ovf_ids[1], st);
-        s->defer_ids = s->ovf_ids[0] = s->ovf_ids[1] = nullptr;
-        SK_CUDA(dev_alloc_t(&s->defer_ids, (size_t)count, st));
+        s->to_warp_ids = s->to_cta_ids = s->ovf_ids[0] = s->ovf_ids[1] = nullptr;
+        SK_CUDA(dev_alloc_t(&s->to_warp_ids, (size_t)count, st));
+        SK_CUDA(dev_alloc_t(&s->to_cta_ids, (size_t)count, st));
         SK_CUDA(dev_alloc_t(&s->ovf_ids[0], (size_t)count, st));
         SK_CUDA(dev_alloc_t(&s->ovf_ids[1], (size_t)count, st));
         s->list_cap = count;
@@ -483,6 +759,18 @@ static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st
     return SKIS_OK;
 }
 
+static int occupancy_grid(const void* kernel, int threads, int override_blocks, uint64_t max_useful,
+                          std::string* err, int* out) {
+    int blocks = override_blocks;
+    if (blocks <= 0) {
+        int per_sm = 0;
+        SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0));
+        blocks = sm_count() * std::max(per_sm, 1);
+    }
+    *out = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)blocks, max_useful));
+    return SKIS_OK;
+}
+
 int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* err) {
     const skis_graph* g = s->g;
     if (g->W == 0) {
@@ -492,77 +780,108 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     if (count == 0) return SKIS_OK;
     int rc = ensure_sample_buffers(s, count, st, err);
     if (rc != SKIS_OK) return rc;
+    const bool thread_tier = s->thread_max_deg > 0;
+    int thread_blocks = 0, warp_blocks = 0;
+    rc = occupancy_grid((const void*)k_iis_thread, kThreadBlock, s->thread_blocks,
+                        (count + kThreadBlock - 1) / kThreadBlock, err, &thread_blocks);
+    if (rc != SKIS_OK) return rc;
+    rc = occupancy_grid((const void*)k_iis_warp, kWarpThreads, s->warp_blocks,
+                        thread_tier ? UINT64_MAX : (count + kIdBatch - 1) / kIdBatch, err, &warp_blocks);
+    if (rc != SKIS_OK) return rc;
 
-    int warp_blocks = s->warp_blocks;
-    if (warp_blocks <= 0) {
-        int per_sm = 0;
-        SK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_iis_warp, kWarpThreads, 0));
-        warp_blocks = sm_count() * std::max(per_sm, 1);
-    }
-    const uint64_t need_blocks = (count + kIdBatch - 1) / kIdBatch;  // at most one batch per warp... per block
-    warp_blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)warp_blocks, need_blocks));
-
-    SampleArgs a;
-    a.alias = g->alias;
-    a.rows = g->rows;
-    a.src = g->src;
-    a.tau = g->row_uniform ? nullptr : g->tau;
-    a.n = (uint64_t)g->n;
-    a.W = g->W;
-    a.seed = s->seed;
-    a.ids = nullptr;
-    a.first_id = s->T;
-    a.count = count;
-    a.retry_cap = s->retry_cap;
-    a.h_off = s->h_off;
-    a.h_len = s->h_len;
-    a.h_src = s->h_src;
-    a.h_retries = s->h_retries;
-    a.h_coins = s->h_coins;
-    a.arena = s->arena;
-    a.arena_cap = s->arena_cap;
-    a.ctr = s->ctr;
-    a.defer_ids = s->defer_ids;
-    a.status = s->status;
-    a.bitmaps = s->bitmaps;
-    a.queues = s->queues;
-    a.bitmap_words = s->bitmap_words;
+    SampleArgs base;
+    base.alias = g->alias;
+    base.rows = g->rows;
+    base.src = g->src;
+    base.tau = g->row_uniform ? nullptr : g->tau;
+    base.n = (uint64_t)g->n;
+    base.W = g->W;
+    base.seed = s->seed;
+    base.retry_cap = s->retry_cap;
+    base.max_deg = s->thread_max_deg;
+    base.ids = nullptr;
+    base.first_id = s->T;
+    base.count = count;
+    base.count_dev = nullptr;
+    base.arena_cursor = &s->ctr->arena;
+    base.novf = &s->ctr->novf;
+    base.h_off = s->h_off;
+    base.h_len = s->h_len;
+    base.h_src = s->h_src;
+    base.h_retries = s->h_retries;
+    base.h_coins = s->h_coins;
+    base.arena = s->arena;
+    base.arena_cap = s->arena_cap;
+    base.status = s->status;
+    base.bitmaps = s->bitmaps;
+    base.queues = s->queues;
+    base.bitmap_words = s->bitmap_words;
 
     DevStatus hst;
     SampleCounters hc;
     int pass = 0;
-    s->last_warp_ms = s->last_cta_ms = s->last_sample_ms = 0;
-    s->last_deferred = 0;
+    s->last_thread_ms = s->last_warp_ms = s->last_cta_ms = s->last_sample_ms = 0;
+    s->last_to_warp = s->last_deferred = 0;
+    s->last_passes = 0;
     SK_CUDA(cudaMemsetAsync(s->status, 0, sizeof(DevStatus), st));
     SK_CUDA(cudaMemsetAsync(&s->status->first_bad, 0xFF, sizeof(unsigned long long), st));
     for (;;) {
-        a.ovf_ids = s->ovf_ids[pass & 1];
-        // reset the per-pass cursors, keep the arena cursor
-        SK_CUDA(cudaMemsetAsync(&s->ctr->work, 0, sizeof(unsigned long long) * 2, st));
-        SK_CUDA(cudaMemsetAsync(&s->ctr->ndefer, 0, sizeof(unsigned long long) * 2, st));
+        base.ovf_ids = s->ovf_ids[pass & 1];
+        // reset every per-pass cursor and count; the arena cursor persists
+        SK_CUDA(cudaMemsetAsync(&s->ctr->novf, 0, sizeof(SampleCounters) - sizeof(unsigned long long), st));
+        SampleArgs at = base, aw = base, ac = base;
+        // thread tier: the input ids; hands on to the warp tier
+        at.work = &s->ctr->work_thread;
+        at.out_ids = s->to_warp_ids;
+        at.out_count = &s->ctr->n_to_warp;
+        // warp tier: the thread tier's hand-ons (or the input ids without it)
+        if (thread_tier) {
+            aw.ids = s->to_warp_ids;
+            aw.count_dev = &s->ctr->n_to_warp;
+        }
+        aw.work = &s->ctr->work_warp;
+        aw.out_ids = s->to_cta_ids;
+        aw.out_count = &s->ctr->n_to_cta;
+        // CTA tier: the warp tier's hand-ons
+        ac.ids = s->to_cta_ids;
+        ac.count_dev = &s->ctr->n_to_cta;
+        ac.work = &s->ctr->work_cta;
+        ac.out_ids = nullptr;
+        ac.out_count = nullptr;
+
         SK_CUDA(cudaEventRecord(s->ev[0], st));
-        k_iis_warp<<<warp_blocks, kWarpThreads, 0, st>>>(a); note_launch();
-        SK_CUDA(cudaGetLastError());
+        if (thread_tier) {
+            k_iis_thread<<<thread_blocks, kThreadBlock, 0, st>>>(at); note_launch();
+            SK_CUDA(cudaGetLastError());
+        }
         SK_CUDA(cudaEventRecord(s->ev[1], st));
-        k_iis_cta<<<s->cta_slots_alloc, kCtaThreads, 0, st>>>(a); note_launch();
+        k_iis_warp<<<warp_blocks, kWarpThreads, 0, st>>>(aw); note_launch();
         SK_CUDA(cudaGetLastError());
         SK_CUDA(cudaEventRecord(s->ev[2], st));
+        k_iis_cta<<<s->cta_slots_alloc, kCtaThreads, 0, st>>>(ac); note_launch();
+        SK_CUDA(cudaGetLastError());
+        SK_CUDA(cudaEventRecord(s->ev[3], st));
         SK_CUDA(cudaMemcpyAsync(&hc, s->ctr, sizeof(SampleCounters), cudaMemcpyDeviceToHost, st));
         SK_CUDA(cudaMemcpyAsync(&hst, s->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
         SK_CUDA(cudaStreamSynchronize(st));
-        float ms_w = 0, ms_c = 0;
-        cudaEventElapsedTime(&ms_w, s->ev[0], s->ev[1]);
-        cudaEventElapsedTime(&ms_c, s->ev[1], s->ev[2]);
+        float ms_t = 0, ms_w = 0, ms_c = 0;
+        cudaEventElapsedTime(&ms_t, s->ev[0], s->ev[1]);
+        cudaEventElapsedTime(&ms_w, s->ev[1], s->ev[2]);
+        cudaEventElapsedTime(&ms_c, s->ev[2], s->ev[3]);
+        s->last_thread_ms += ms_t;
         s->last_warp_ms += ms_w;
         s->last_cta_ms += ms_c;
-        s->last_sample_ms += ms_w + ms_c;
-        s->last_deferred += hc.ndefer;
+        s->last_sample_ms += ms_t + ms_w + ms_c;
+        s->last_to_warp += thread_tier ? hc.n_to_warp : count;
+        s->last_deferred += hc.n_to_cta;
+        s->last_passes += 1;
         if (hc.novf == 0) break;
         // some reservations did not fit: grow the arena (keeping every
         // completed sample, all of which lie below the old capacity) and
         // rerun exactly the samples that failed
         const uint64_t old_cap = s->arena_cap;
-        const uint64_t new_cap = old_cap * 2 + (uint64_t)kArenaChunk * (uint64_t)warp_blocks * 8;
+        const uint64_t new_cap = old_cap * 2 + (uint64_t)kThreadArenaChunk * thread_blocks * (kThreadBlock / 32) +
+                                 (uint64_t)kArenaChunk * warp_blocks * (kWarpThreads / 32);
         rc = [&]() -> int {
             SK_CUDA(grow_copy(&s->arena, old_cap, new_cap, st));
             return SKIS_OK;
@@ -574,11 +893,11 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
         s->arena_cap = new_cap;
         unsigned long long cur = old_cap;
         SK_CUDA(cudaMemcpyAsync(&s->ctr->arena, &cur, sizeof(cur), cudaMemcpyHostToDevice, st));
-        a.arena = s->arena;
-        a.arena_cap = s->arena_cap;
-        a.ids = s->ovf_ids[pass & 1];
-        a.first_id = 0;
-        a.count = hc.novf;
+        base.arena = s->arena;
+        base.arena_cap = s->arena_cap;
+        base.ids = s->ovf_ids[pass & 1];
+        base.first_id = 0;
+        base.count = hc.novf;
         ++pass;
     }
     s->T += count;

@@ -174,12 +174,14 @@ struct skis_graph {
 namespace skis {
 // Device cursors and counters of one skis_sample call.
 struct SampleCounters {
-    unsigned long long work;      // warp-tier id cursor
-    unsigned long long cta_work;  // CTA-tier list cursor
-    unsigned long long arena;     // arena reservation cursor (persists across calls)
-    unsigned long long ndefer;    // samples handed to the CTA tier
-    unsigned long long novf;      // samples whose arena reservation did not fit
-    unsigned long long pad[3];
+    unsigned long long arena;        // arena reservation cursor (persists across calls)
+    unsigned long long novf;         // samples whose arena reservation did not fit
+    unsigned long long work_thread;  // id cursors of the three tiers
+    unsigned long long work_warp;
+    unsigned long long work_cta;
+    unsigned long long n_to_warp;    // samples handed from the thread tier to the warp tier
+    unsigned long long n_to_cta;     // samples handed from the warp tier to the CTA tier
+    unsigned long long pad;
 };
 }  // namespace skis
 
@@ -199,7 +201,8 @@ struct skis_sketch {
     uint64_t arena_hint = 0;
     skis::SampleCounters* ctr = nullptr;
     skis::DevStatus* status = nullptr;
-    uint64_t* defer_ids = nullptr;
+    uint64_t* to_warp_ids = nullptr;     // thread tier -> warp tier
+    uint64_t* to_cta_ids = nullptr;      // warp tier -> CTA tier
     uint64_t* ovf_ids[2] = {nullptr, nullptr};
     uint64_t list_cap = 0;
     uint32_t* bitmaps = nullptr;         // CTA tier: one n-bit visited bitmap per slot
@@ -210,9 +213,11 @@ struct skis_sketch {
     uint32_t retry_cap = 1u << 24;
     int cta_slots = 0;                   // 0 = automatic
     int warp_blocks = 0;                 // 0 = automatic
+    int thread_blocks = 0;               // 0 = automatic
+    uint32_t thread_max_deg = 256;       // longest in-row the thread tier expands (0 = tier off)
     // last-call statistics
-    uint64_t last_deferred = 0;
-    double last_warp_ms = 0, last_cta_ms = 0, last_sample_ms = 0;
+    uint64_t last_to_warp = 0, last_deferred = 0, last_passes = 0;
+    double last_thread_ms = 0, last_warp_ms = 0, last_cta_ms = 0, last_sample_ms = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // query / greedy scratch (allocated on first use)
     uint64_t* qmask = nullptr;           // n per-vertex query bits

@@ -108,7 +108,7 @@ def test_er_workload_full_parity(er_small):
     s = skis.skis_sketch_create(g, seed)
     skis.skis_sample(s, T)
     st = skis.skis_sketch_stats(s)
-    assert st["deferred"] > 0  # the CTA tier took part
+    assert st["deferred"] > 0 and st["to_warp"] > 0  # all three tiers took part
     dev = skis.skis_sketch_export(s, 0, T)
     a = osk.arrays()
     ora = dict(src=a["src"], retries=a["retries"], len=np.diff(a["off"]), coins=a["coins"],
@@ -131,8 +131,14 @@ def test_er_workload_full_parity(er_small):
 def test_results_do_not_depend_on_launch_configuration(er_small):
     spec, src, dst, g, o, osk, seed, T = er_small
     ref = None
-    for warp_blocks, cta_slots, arena in ((0, 0, 0), (3, 1, 1000), (1000, 7, 50_000)):
+    # (thread-tier degree limit, thread blocks, warp blocks, CTA slots, initial arena)
+    configs = ((None, 0, 0, 0, 0), (0, 0, 3, 1, 1000), (1 << 30, 5, 1000, 7, 50_000), (8, 1, 2, 2, 0))
+    for max_deg, thread_blocks, warp_blocks, cta_slots, arena in configs:
         s = skis.skis_sketch_create(g, seed, arena)
+        if max_deg is not None:
+            skis.skis_sketch_set_option(s, skis.SKIS_OPT_THREAD_MAX_DEG, max_deg)
+        if thread_blocks:
+            skis.skis_sketch_set_option(s, skis.SKIS_OPT_THREAD_BLOCKS, thread_blocks)
         if warp_blocks:
             skis.skis_sketch_set_option(s, skis.SKIS_OPT_WARP_BLOCKS, warp_blocks)
         if cta_slots:
