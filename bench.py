@@ -49,6 +49,7 @@ def _args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step and exit (the command profiled with ncu)")
     return ap.parse_args()
@@ -114,6 +115,19 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def reduce_over_ranks(x: float, op: str = "max") -> float:
+    """Max (or sum) of a per-rank scalar over all ranks; identity on one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
 
 
 def _peaks():
@@ -186,6 +200,77 @@ def run_reference(args, rank, world):
         "e2e": {"value": value, "unit": "RR sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+# --------------------------------------------------------------- serving
+SERVE_WORKLOAD = "chunglu-4e6-wc-serve"
+
+
+def serve_run(skis, s, queries, arrivals, slots, max_batch):
+    """Drive the native server with requests arriving at the given times
+    (seconds from start); returns per-request latency (s) and wall time."""
+    srv = skis.skis_server_create(s, slots=slots, max_batch=max_batch, seed_capacity=1 << 16)
+    nq = len(queries)
+    done_at = np.zeros(nq)
+    ticket_of = {}
+    nxt = 0
+    finished = 0
+    t0 = time.perf_counter()
+    while finished < nq:
+        now = time.perf_counter() - t0
+        while nxt < nq and arrivals[nxt] <= now:
+            ticket_of[skis.skis_server_submit(srv, queries[nxt])] = nxt
+            nxt += 1
+        idle_wait = nxt == nq  # nothing left to admit: block on the GPU
+        for t in skis.skis_server_progress(srv, wait=idle_wait):
+            done_at[ticket_of[int(t)]] = time.perf_counter() - t0
+            finished += 1
+    wall = time.perf_counter() - t0
+    srv.close()
+    return done_at - arrivals, wall
+
+
+def serving_benchmark(skis, torch, dev, stream):
+    """Influence-oracle serving on a device-resident sketch: saturation
+    throughput (all requests at t = 0) of continuous batching versus one
+    query per launch, and latency under Poisson arrivals at half the batched
+    saturation rate."""
+    import synth
+
+    spec, src, dst, _ = synth.workload(SERVE_WORKLOAD)
+    n, T = spec["n"], spec["samples"]
+    d_src, d_dst = torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev)
+    g = skis.skis_load_graph(n, d_src, d_dst, None, skis.SKIS_W_WC, stream=stream)
+    s = skis.skis_sketch_create(g, SKETCH_SEED + 2, T * 16, stream=stream)
+    skis.skis_sample(s, T, stream=stream)
+    st = skis.skis_sketch_stats(s)
+    rng = np.random.Generator(np.random.PCG64(12345))
+    nq = 3000
+    sizes = synth.log_uniform_sizes(nq, 1, 1000, 44)
+    off, seeds = synth.seed_sets(n, sizes, 45)
+    queries = [seeds[off[b]:off[b + 1]] for b in range(nq)]
+    serve_run(skis, s, queries[:200], np.zeros(200), 4, 64)  # warm-up
+    lat_b, wall_b = serve_run(skis, s, queries, np.zeros(nq), 4, 64)
+    sat_batched = nq / wall_b
+    n1 = 300
+    lat_1, wall_1 = serve_run(skis, s, queries[:n1], np.zeros(n1), 1, 1)
+    sat_single = n1 / wall_1
+    rate = 0.5 * sat_batched
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nq))
+    lat_p, wall_p = serve_run(skis, s, queries, arrivals, 4, 64)
+    s.close()
+    g.close()
+    return {
+        "workload": SERVE_WORKLOAD, "n": n, "m": spec["m"], "samples": T, "entries": st["entries"],
+        "query_sizes": "log-uniform in [1, 1000]", "requests": nq,
+        "saturation_queries_per_s": sat_batched,
+        "one_query_per_launch_queries_per_s": sat_single,
+        "speedup_vs_one_per_launch": sat_batched / sat_single,
+        "poisson_rate_per_s": rate, "queries_per_s": nq / wall_p,
+        "p50_ms": float(np.percentile(lat_p, 50) * 1e3), "p99_ms": float(np.percentile(lat_p, 99) * 1e3),
+        "saturation_p50_ms": float(np.percentile(lat_b, 50) * 1e3),
+        "slots": 4, "max_batch": 64,
+    }
 
 
 # ----------------------------------------------------------------- ours
@@ -264,12 +349,8 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = skis.skis_kernel_launches() - launches0
-    elapsed_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * args.steps * T / (elapsed_ms / 1e3)
+    elapsed_ms = reduce_over_ranks(e0.elapsed_time(e1), "max")
+    value = reduce_over_ranks(args.steps * T, "sum") / (elapsed_ms / 1e3)
     coins, entries = stats[-1]["coins"], stats[-1]["entries"]
     thread_ms = statistics.mean(s["last_thread_ms"] for s in stats)
     warp_ms = statistics.mean(s["last_warp_ms"] for s in stats)
@@ -306,12 +387,8 @@ def main():
     e3.record(stream)
     torch.cuda.synchronize()
     wall_e2e = time.perf_counter() - t0
-    e2e_ms = max(e2.elapsed_time(e3), wall_e2e * 1e3)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * args.e2e_steps * T / (e2e_ms / 1e3)
+    e2e_ms = reduce_over_ranks(max(e2.elapsed_time(e3), wall_e2e * 1e3), "max")
+    e2e_value = reduce_over_ranks(args.e2e_steps * T, "sum") / (e2e_ms / 1e3)
     h2d = m * (4 + 4 + 8) + q_off.nbytes + q_seeds.nbytes
     d2h = k * (4 + 8 + 8) + QUERIES * (8 + 8)
 
@@ -330,6 +407,9 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tps * T if tps is not None else None), "kernel": "k_iis_thread + k_iis_warp + k_iis_cta",
                 "algorithmic_bytes": alg, "kernel_ms": sample_ms, "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
+
+    # ---- influence-oracle serving (queries/s, p50/p99)
+    serving = None if args.no_serving else serving_benchmark(skis, torch, dev, stream)
 
     # ---- CPU baseline: the oracle, as it stands, on a bounded sample
     cpu = None
@@ -361,6 +441,7 @@ def main():
                           "passes": stats[-1]["last_passes"], "arena_capacity": stats[-1]["arena_capacity"]},
         "per_sample": {"members": entries / T, "coins": coins / T},
         "roofline": roofline,
+        "serving": serving,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "RR sets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

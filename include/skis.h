@@ -222,6 +222,33 @@ int skis_estimate_noalloc(const skis_sketch *s, int32_t num_queries, const int64
                           const int32_t *seeds, int64_t *coverage_out, double *estimate_out,
                           char *error_buf, uint64_t error_len, void *cuda_stream);
 
+/* Continuous-batching influence-oracle server over a device-resident sketch
+ * (Alg. 2 line 2 for a stream of requests). skis_server_submit validates a
+ * seed set (host array, copied; non-empty, ids in [0, n), no repeats) and
+ * queues it, returning a ticket. skis_server_progress retires finished
+ * batches and admits queued requests, in arrival order, into every free
+ * in-flight slot: up to max_batch requests (<= 64, one query-mask bit each)
+ * whose seeds fit the slot's seed_capacity. Each of the `slots` slots has its
+ * own stream, pinned staging, device buffers and n-word query-mask scratch
+ * (allocated at creation), so batches on different slots overlap on the
+ * device. With wait != 0, progress first blocks until one in-flight batch
+ * completes. Completed tickets are written to done_tickets (capacity cap).
+ * skis_server_poll reports a ticket's state (0 pending, 1 ready, 2 failed)
+ * and, when ready, its Cov_R(S) and I_R(S) — the same values skis_estimate
+ * gives for that seed set. The sketch must not change while a server uses
+ * it; one host thread drives a server. */
+typedef struct skis_server skis_server;
+int skis_server_create(skis_server **out, skis_sketch *s, int32_t slots, int32_t max_batch,
+                       uint64_t seed_capacity);
+int skis_server_submit(skis_server *srv, const int32_t *seeds, int32_t nseeds, uint64_t *ticket_out);
+int skis_server_progress(skis_server *srv, int32_t wait, uint64_t *done_tickets, int32_t cap,
+                         int32_t *ndone_out);
+int skis_server_poll(skis_server *srv, uint64_t ticket, int64_t *coverage_out, double *estimate_out,
+                     int32_t *state_out);
+int skis_server_counts(const skis_server *srv, uint64_t *queued, uint64_t *in_flight, uint64_t *batches,
+                       uint64_t *served);
+void skis_server_free(skis_server *srv);
+
 /* Number of CUDA kernel launches the library has made in this process
  * (diagnostic; counts every launch of every entry point). */
 uint64_t skis_kernel_launches(void);

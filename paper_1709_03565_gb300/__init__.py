@@ -8,7 +8,7 @@ coverage counting with the SKIS estimator (Eq. 21) and greedy max-coverage
 and streams.
 """
 from ._binding import *  # noqa: F401,F403
-from ._binding import lib, LIB_PATH, SkisError, Graph, Sketch  # noqa: F401
+from ._binding import lib, LIB_PATH, SkisError, Graph, Sketch, Server  # noqa: F401
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

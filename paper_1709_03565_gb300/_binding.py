@@ -62,6 +62,12 @@ _SIGNATURES = [
     ("skis_sketch_export", _INT, [_P, _U64, _U64, _P, _P, _P, _P, _P, _P, _U64, _P]),
     ("skis_sketch_free", None, [_P]),
     ("skis_estimate_noalloc", _INT, [_P, _I32, _P, _P, _P, _P, _P, _U64, _P]),
+    ("skis_server_create", _INT, [_P, _P, _I32, _I32, _U64]),
+    ("skis_server_submit", _INT, [_P, _P, _I32, _P]),
+    ("skis_server_progress", _INT, [_P, _I32, _P, _I32, _P]),
+    ("skis_server_poll", _INT, [_P, _U64, _P, _P, _P]),
+    ("skis_server_counts", _INT, [_P, _P, _P, _P, _P]),
+    ("skis_server_free", None, [_P]),
     ("skis_kernel_launches", ctypes.c_uint64, []),
     ("skis_last_error", ctypes.c_char_p, []),
 ]
@@ -163,6 +169,14 @@ class Graph(_Handle):
 
 class Sketch(_Handle):
     _free = "skis_sketch_free"
+
+
+class Server(_Handle):
+    _free = "skis_server_free"
+
+    def __init__(self, ptr, keep=None):
+        super().__init__(ptr, keep)
+        self._done = np.empty(4096, np.uint64)
 
 
 # ------------------------------------------------------------ entry points
@@ -287,6 +301,46 @@ def skis_estimate_noalloc(s: Sketch, seed_offsets, seeds, coverage_out, estimate
     if rc != SKIS_OK:
         raise SkisError(rc, buf.value.decode())
     return coverage_out, estimate_out
+
+
+def skis_server_create(s: Sketch, slots: int = 4, max_batch: int = 64, seed_capacity: int = 1 << 16) -> Server:
+    out = ctypes.c_void_p()
+    _check(lib().skis_server_create(ctypes.byref(out), s.ptr, int(slots), int(max_batch), int(seed_capacity)))
+    return Server(out, keep=s)
+
+
+def skis_server_submit(srv: Server, seeds) -> int:
+    seeds = np.ascontiguousarray(seeds, dtype=np.int32)
+    t = ctypes.c_uint64()
+    _check(lib().skis_server_submit(srv.ptr, ctypes.c_void_p(seeds.ctypes.data), int(seeds.shape[0]),
+                                    ctypes.byref(t)))
+    return t.value
+
+
+def skis_server_progress(srv: Server, wait: bool = False) -> np.ndarray:
+    """Retire finished batches and launch new ones; returns completed tickets."""
+    nd = ctypes.c_int32()
+    buf = srv._done
+    _check(lib().skis_server_progress(srv.ptr, 1 if wait else 0, ctypes.c_void_p(buf.ctypes.data),
+                                      int(buf.shape[0]), ctypes.byref(nd)))
+    return buf[: nd.value].copy()
+
+
+def skis_server_poll(srv: Server, ticket: int):
+    """(state, coverage, estimate); state 0 pending, 1 ready, 2 failed."""
+    c, e, st = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int32()
+    _check(lib().skis_server_poll(srv.ptr, int(ticket), ctypes.byref(c), ctypes.byref(e), ctypes.byref(st)))
+    return st.value, c.value, e.value
+
+
+def skis_server_counts(srv: Server) -> dict:
+    v = [ctypes.c_uint64() for _ in range(4)]
+    _check(lib().skis_server_counts(srv.ptr, *[ctypes.byref(x) for x in v]))
+    return dict(queued=v[0].value, in_flight=v[1].value, batches=v[2].value, served=v[3].value)
+
+
+def skis_server_free(srv: Server):
+    srv.close()
 
 
 def skis_kernel_launches() -> int:

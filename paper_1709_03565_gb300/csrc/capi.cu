@@ -17,6 +17,8 @@ static int fail(int code, const std::string& msg) {
     return code;
 }
 
+int skis::set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+
 static int cuda_fail(const char* where, cudaError_t e) {
     return fail(e == cudaErrorMemoryAllocation ? SKIS_ENOMEM : SKIS_ERR_CUDA,
                 std::string(where) + ": CUDA error: " + cudaGetErrorString(e));

@@ -234,9 +234,14 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
                   std::string* err);
 void sketch_release(skis_sketch* s);
 
+// Records msg as the calling thread's last error (skis_last_error); returns code.
+int set_last_error(int code, const std::string& msg);
+
 // Coverage kernels (defined in cover.cu).
 __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
                             int32_t qn, int64_t n, uint64_t* __restrict__ qmask, DevStatus* st);
+__global__ void k_qmask_clear(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
+                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask);
 __global__ void __launch_bounds__(256) k_coverage(const uint64_t* __restrict__ h_off, const uint32_t* __restrict__ h_len, uint64_t T,
                            const int32_t* __restrict__ arena, const uint64_t* __restrict__ qmask,
                            unsigned long long* __restrict__ cov);
