@@ -4,8 +4,9 @@
 One step = one pass of the whole hot path over the Chung-Lu workload
 (n = 1M, m = 10M, exponent 2.1, trivalency probabilities, 10M IIS samples,
 greedy max-coverage k = 50): graph load (canonical in-CSR, thresholds,
-fixed-point gamma, alias table), IIS sampling, one batch of 64 influence
-queries (seed sets of 10 uniform vertices) and greedy max-coverage.
+fixed-point gamma, alias table), IIS sampling, greedy max-coverage (with the
+inverted index it builds) and one batch of 64 influence queries (seed sets
+of 10 uniform vertices).
 
 `value` is RR sets/s with the edge arrays already in HBM; `e2e` is the same
 metric through the C ABI with host buffers (pinned), the host->device copy
@@ -309,8 +310,8 @@ def main():
         g = skis.skis_load_graph(n, d_src, d_dst, d_p, skis.SKIS_W_EXPLICIT_P, stream=stream)
         s = skis.skis_sketch_create(g, seed, arena_hint, stream=stream)
         skis.skis_sample(s, T, stream=stream)
-        skis.skis_estimate(s, d_off, d_seeds, d_cov, d_est, stream=stream)
-        sd, sc, se = skis.skis_greedy_maxcover(s, k, stream=stream)
+        sd, sc, se = skis.skis_greedy_maxcover(s, k, stream=stream)  # builds the inverted index
+        skis.skis_estimate(s, d_off, d_seeds, d_cov, d_est, stream=stream)  # walks it
         st = skis.skis_sketch_stats(s)
         s.close()
         g.close()
@@ -370,8 +371,8 @@ def main():
         g = skis.skis_load_graph(n, h_src, h_dst, h_p, skis.SKIS_W_EXPLICIT_P, stream=stream)
         s = skis.skis_sketch_create(g, seed, arena_hint, stream=stream)
         skis.skis_sample(s, T, stream=stream)
-        skis.skis_estimate(s, h_off, h_seeds, h_cov, h_est, stream=stream)
         out = skis.skis_greedy_maxcover(s, k, stream=stream)
+        skis.skis_estimate(s, h_off, h_seeds, h_cov, h_est, stream=stream)
         s.close()
         g.close()
         return out

@@ -104,7 +104,10 @@ typedef enum skis_option {
     SKIS_OPT_CTA_SLOTS = 1,      /* CTAs of the CTA tier (default 2 per SM) */
     SKIS_OPT_WARP_BLOCKS = 2,    /* CTAs of the warp tier (default: full occupancy) */
     SKIS_OPT_THREAD_MAX_DEG = 3, /* longest in-row the thread tier expands (default 256; 0 = tier off) */
-    SKIS_OPT_THREAD_BLOCKS = 4   /* CTAs of the thread tier (default: full occupancy) */
+    SKIS_OPT_THREAD_BLOCKS = 4,  /* CTAs of the thread tier (default: full occupancy) */
+    SKIS_OPT_QUERY_INDEX = 5     /* skis_estimate: 0 = walk the inverted index (vertex -> samples) when
+                                    it is built for the current samples, else scan the sketch (default);
+                                    1 = build it if needed and walk it; 2 = always scan */
 } skis_option;
 
 /* Load G = (V, E, w) (Sec. II-A) and build the device structures every later

@@ -194,6 +194,10 @@ extern "C" int skis_sketch_set_option(skis_sketch* s, int option, uint64_t value
             if (value > (1u << 30)) return fail(SKIS_EINVAL, "thread-tier degree limit must be at most 2^30");
             s->thread_max_deg = (uint32_t)value;
             return SKIS_OK;
+        case SKIS_OPT_QUERY_INDEX:
+            if (value > 2) return fail(SKIS_EINVAL, "query-index mode must be 0, 1 or 2");
+            s->query_index = (int)value;
+            return SKIS_OK;
         case SKIS_OPT_THREAD_BLOCKS:
             if (value > (1u << 20)) return fail(SKIS_EINVAL, "thread blocks must be at most 2^20");
             s->thread_blocks = (int)value;
@@ -243,7 +247,7 @@ extern "C" int skis_estimate(skis_sketch* s, int32_t num_queries, const int64_t*
     std::string err;
     int rc;
     if (mem_space == SKIS_MEM_DEVICE) {
-        rc = sketch_estimate(s, num_queries, seed_offsets, seeds, coverage_out, estimate_out, st, &err);
+        rc = sketch_estimate(s, num_queries, seed_offsets, seeds, off.data(), coverage_out, estimate_out, st, &err);
     } else {
         const int64_t nseeds = off[num_queries];
         int64_t* d_off = nullptr;
@@ -257,7 +261,7 @@ extern "C" int skis_estimate(skis_sketch* s, int32_t num_queries, const int64_t*
         API_CUDA("skis_estimate", cudaMemcpyAsync(d_off, off.data(), (num_queries + 1) * 8, cudaMemcpyHostToDevice, st));
         if (nseeds)
             API_CUDA("skis_estimate", cudaMemcpyAsync(d_seeds, seeds, nseeds * 4, cudaMemcpyHostToDevice, st));
-        rc = sketch_estimate(s, num_queries, d_off, d_seeds, d_cov, d_est, st, &err);
+        rc = sketch_estimate(s, num_queries, d_off, d_seeds, off.data(), d_cov, d_est, st, &err);
         if (rc == SKIS_OK) {
             if (coverage_out)
                 API_CUDA("skis_estimate",
@@ -421,6 +425,9 @@ void skis::sketch_release(skis_sketch* s) {
     dev_free(s->bitmaps, st);
     dev_free(s->queues, st);
     dev_free(s->qmask, st);
+    dev_free(s->inv_off, st);
+    dev_free(s->inv, st);
+    dev_free(s->smask, st);
     dev_free(s->qcov, st);
     dev_free(s->qstatus, st);
     for (int i = 0; i < 4; ++i)

@@ -11,6 +11,8 @@
 // coverage Delta_v, then per round an exact argmax of the integer key
 // Delta_v W + T (2^f - w_v) (ties to the lowest id), and the samples of the
 // chosen vertex are marked covered and their members' Delta decremented.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <string>
 
@@ -169,19 +171,122 @@ static int coverage_blocks(uint64_t T) {
     return (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sm_count() * 8));
 }
 
-int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds, int64_t* d_cov,
-                    double* d_est, cudaStream_t st, std::string* err) {
+// ------------------------------------------- coverage by inverted index
+// Cov_R(S) for small seed sets: walk the sample list of every seed and set
+// the query's bit in a per-sample mask; the first setter of (sample, query)
+// counts it. Lists are cut into chunks of kInvChunk entries; one warp takes
+// one chunk, found by binary search over the batch's chunk prefix sums.
+constexpr uint32_t kInvChunk = 2048;
+
+__global__ void k_seed_chunks(const int32_t* __restrict__ seeds, int64_t seed_base, int64_t nseeds, int64_t n,
+                              const uint64_t* __restrict__ inv_off, uint32_t* __restrict__ chunk_cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nseeds; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = seeds[seed_base + i];
+        uint32_t c = 0;
+        if (v >= 0 && v < n) c = (uint32_t)((inv_off[v + 1] - inv_off[v] + kInvChunk - 1) / kInvChunk);
+        chunk_cnt[i] = c;
+    }
+}
+
+__global__ void __launch_bounds__(kCovThreads) k_cover_inv(const int64_t* __restrict__ off,
+                                                           const int32_t* __restrict__ seeds, int32_t q0, int32_t qn,
+                                                           int64_t seed_base, int64_t nseeds,
+                                                           const uint64_t* __restrict__ chunk_off,
+                                                           const uint64_t* __restrict__ inv_off,
+                                                           const uint32_t* __restrict__ inv,
+                                                           uint64_t* __restrict__ smask,
+                                                           unsigned long long* __restrict__ cov, int clear) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t C = chunk_off[nseeds];
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; c < C; c += nwarps) {
+        int64_t lo = 0, hi = nseeds - 1;  // last seed i with chunk_off[i] <= c
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (chunk_off[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const int64_t i = lo;
+        int32_t blo = q0, bhi = q0 + qn - 1;  // last query b with off[b] <= seed_base + i
+        while (blo < bhi) {
+            const int32_t mid = (blo + bhi + 1) / 2;
+            if (off[mid] <= seed_base + i) blo = mid;
+            else bhi = mid - 1;
+        }
+        const uint64_t bit = 1ull << (blo - q0);
+        const int32_t v = seeds[seed_base + i];
+        const uint64_t start = inv_off[v] + (c - chunk_off[i]) * kInvChunk;
+        const uint64_t end = min(start + kInvChunk, inv_off[v + 1]);
+        uint32_t fresh = 0;
+        for (uint64_t x = start + lane; x < end; x += 32) {
+            const uint32_t j = inv[x];
+            if (clear) {
+                smask[j] = 0;
+            } else {
+                const unsigned long long old = atomicOr((unsigned long long*)&smask[j], (unsigned long long)bit);
+                fresh += (old & bit) ? 0u : 1u;
+            }
+        }
+        if (!clear) {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) fresh += __shfl_down_sync(kFull, fresh, d);
+            if (lane == 0 && fresh) atomicAdd(&cov[blo - q0], (unsigned long long)fresh);
+        }
+    }
+}
+
+cudaError_t coverage_by_index(const skis_sketch* s, const int64_t* off, const int32_t* seeds, int32_t q0,
+                              int32_t qn, int64_t seed_base, int64_t nseeds, uint32_t* chunk_cnt,
+                              uint64_t* chunk_off, uint64_t* smask, unsigned long long* cov, cudaStream_t st) {
+    if (nseeds <= 0) return cudaSuccess;
+    const int b1 = (int)std::max<int64_t>(1, std::min<int64_t>((nseeds + 255) / 256, (int64_t)sm_count() * 4));
+    k_seed_chunks<<<b1, 256, 0, st>>>(seeds, seed_base, nseeds, s->g->n, s->inv_off, chunk_cnt); note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = scan_u32_to_u64(chunk_cnt, chunk_off, nseeds, st);
+    if (e != cudaSuccess) return e;
+    const int b2 = sm_count() * 8;
+    k_cover_inv<<<b2, kCovThreads, 0, st>>>(off, seeds, q0, qn, seed_base, nseeds, chunk_off, s->inv_off, s->inv,
+                                            smask, cov, 0); note_launch();
+    k_cover_inv<<<b2, kCovThreads, 0, st>>>(off, seeds, q0, qn, seed_base, nseeds, chunk_off, s->inv_off, s->inv,
+                                            smask, cov, 1); note_launch();
+    return cudaGetLastError();
+}
+
+int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds, const int64_t* h_off,
+                    int64_t* d_cov, double* d_est, cudaStream_t st, std::string* err) {
     const char* where = "skis_estimate";
     const skis_graph* g = s->g;
     if (s->T == 0) {
         *err = "skis_estimate: the sketch has no samples";
         return SKIS_EINVAL;
     }
+    if (s->query_index == 1) {
+        const int rc = sketch_inverted(s, st, err);
+        if (rc != SKIS_OK) return rc;
+    }
+    const bool by_index = s->query_index != 2 && s->inv && s->inv_T == s->T;
     if (!s->qmask) {
         CV_CUDA(dev_alloc_t(&s->qmask, (size_t)g->n, st));
         CV_CUDA(cudaMemsetAsync(s->qmask, 0, (size_t)g->n * sizeof(uint64_t), st));
         CV_CUDA(dev_alloc_t(&s->qcov, 64, st));
         CV_CUDA(dev_alloc_t(&s->qstatus, 1, st));
+    }
+    uint32_t* chunk_cnt = nullptr;
+    uint64_t* chunk_off = nullptr;
+    if (by_index) {
+        if (s->smask_cap < s->T) {
+            dev_free(s->smask, st);
+            s->smask = nullptr;
+            CV_CUDA(dev_alloc_t(&s->smask, (size_t)s->T, st));
+            CV_CUDA(cudaMemsetAsync(s->smask, 0, (size_t)s->T * sizeof(uint64_t), st));
+            s->smask_cap = s->T;
+        }
+        int64_t most = 1;
+        for (int32_t q0 = 0; q0 < q; q0 += 64)
+            most = std::max<int64_t>(most, h_off[std::min<int32_t>(q, q0 + 64)] - h_off[q0]);
+        CV_CUDA(dev_alloc_t(&chunk_cnt, (size_t)most, st));
+        CV_CUDA(dev_alloc_t(&chunk_off, (size_t)most + 1, st));
     }
     CV_CUDA(cudaMemsetAsync(s->qstatus, 0, sizeof(DevStatus), st));
     CV_CUDA(cudaMemsetAsync(&s->qstatus->first_bad, 0xFF, sizeof(unsigned long long), st));
@@ -192,13 +297,20 @@ int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32
         CV_CUDA(cudaMemsetAsync(s->qcov, 0, 64 * sizeof(unsigned long long), st));
         k_qmask_set<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask, s->qstatus); note_launch();
         CV_CUDA(cudaGetLastError());
-        k_coverage<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, s->qmask, s->qcov); note_launch();
-        CV_CUDA(cudaGetLastError());
+        if (by_index) {
+            CV_CUDA(coverage_by_index(s, d_off, d_seeds, q0, qn, h_off[q0], h_off[q0 + qn] - h_off[q0], chunk_cnt,
+                                      chunk_off, s->smask, s->qcov, st));
+        } else {
+            k_coverage<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, s->qmask, s->qcov); note_launch();
+            CV_CUDA(cudaGetLastError());
+        }
         k_estimate<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, g->w, g->f, g->W, s->T, s->qcov, d_cov, d_est); note_launch();
         CV_CUDA(cudaGetLastError());
         k_qmask_clear<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask); note_launch();
         CV_CUDA(cudaGetLastError());
     }
+    dev_free(chunk_cnt, st);
+    dev_free(chunk_off, st);
     DevStatus h;
     CV_CUDA(cudaMemcpyAsync(&h, s->qstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     CV_CUDA(cudaStreamSynchronize(st));
@@ -293,106 +405,153 @@ __device__ KeyId block_best(KeyId b, KeyId* s_part) {
     return b;  // valid in thread 0
 }
 
-// One argmax round of Alg. 3: exact key Delta_v W + T (2^f - w_v) over
-// v outside S. Vertices are grouped in cells of kCell; a cell keeps its best
-// (key, id) from the previous round and is recomputed only when marked dirty
-// (a member's Delta changed or its best joined S). The last block to finish
-// reduces the cell winners and commits round i.
-constexpr int kCellShift = 10;
-constexpr int kCell = 1 << kCellShift;
+// All k rounds of Alg. 3 in one cooperative launch. Per round: every block
+// scans its share of the vertices for the exact key Delta_v W + T (2^f - w_v)
+// (v outside S, ties to the lowest id); the last block to finish commits the
+// winner; a grid barrier; every warp walks the winner's inverted list,
+// marking uncovered samples and decrementing their members' Delta; a grid
+// barrier. Every block executes the same sequence of barriers. Data that
+// other blocks change during the launch (Delta, S, the committed seed) is
+// read through L2 (ld.global.cg), never from a possibly stale L1 line.
+struct GreedyArgs {
+    const uint64_t* w;
+    uint8_t* inS;
+    uint32_t* delta;
+    int64_t n;
+    uint64_t W, T;
+    int f;
+    int32_t k;
+    const uint64_t* inv_off;
+    const uint32_t* inv;
+    const uint64_t* h_off;
+    const uint32_t* h_len;
+    const int32_t* arena;
+    uint32_t* covered;
+    KeyId* partial;
+    GreedyState* gs;
+    int32_t* seeds;
+    int64_t* cov_out;
+    double* est_out;
+};
 
-__global__ void __launch_bounds__(kCovThreads) k_argmax(const uint32_t* __restrict__ delta,
-                                                        const uint64_t* __restrict__ w,
-                                                        uint8_t* __restrict__ inS, int64_t n, uint64_t W,
-                                                        uint64_t T, int f, KeyId* __restrict__ cell_best,
-                                                        uint32_t* __restrict__ dirty, GreedyState* gs,
-                                                        int32_t round, int32_t* __restrict__ seeds,
-                                                        int64_t* __restrict__ cov_out,
-                                                        double* __restrict__ est_out) {
+__device__ __forceinline__ KeyId ldcg_keyid(const KeyId* p) {
+    const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
+    KeyId c;
+    c.key = ((u128)__ldcg(q + 1) << 64) | (u128)__ldcg(q);
+    const unsigned long long tail = __ldcg(q + 2);
+    c.id = (uint32_t)tail;
+    c.valid = (uint32_t)(tail >> 32);
+    return c;
+}
+
+__global__ void __launch_bounds__(kCovThreads) k_greedy_rounds(GreedyArgs a) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
     __shared__ KeyId s_part[kCovThreads / 32];
     __shared__ bool s_last;
-    const uint64_t one_f = 1ull << f;
-    const unsigned cell = blockIdx.x;
-    if (dirty[cell]) {  // block-uniform
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t one_f = 1ull << a.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int32_t round = 0; round < a.k; ++round) {
         KeyId best{0, 0xFFFFFFFFu, 0};
-        const int64_t lo = (int64_t)cell << kCellShift;
-        const int64_t hi = min(lo + kCell, n);
-        for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) {
-            if (inS[v]) continue;
-            const KeyId c{(u128)delta[v] * W + (u128)T * (one_f - w[v]), (uint32_t)v, 1u};
+        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
+            if (__ldcg(a.inS + v)) continue;
+            const KeyId c{(u128)__ldcg(a.delta + v) * a.W + (u128)a.T * (one_f - a.w[v]), (uint32_t)v, 1u};
             if (better(c, best)) best = c;
         }
         best = block_best(best, s_part);
         if (threadIdx.x == 0) {
-            cell_best[cell] = best;
-            dirty[cell] = 0;
+            a.partial[blockIdx.x] = best;
+            __threadfence();
+            s_last = atomicAdd(&a.gs->done, 1ull) == gridDim.x - 1;
         }
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&gs->done, 1ull) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    KeyId b{0, 0xFFFFFFFFu, 0};
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
-        KeyId c;
-        c.key = ((u128)__ldcg(reinterpret_cast<const unsigned long long*>(&cell_best[i]) + 1) << 64) |
-                (u128)__ldcg(reinterpret_cast<const unsigned long long*>(&cell_best[i]));
-        const unsigned long long tail = __ldcg(reinterpret_cast<const unsigned long long*>(&cell_best[i]) + 2);
-        c.id = (uint32_t)tail;
-        c.valid = (uint32_t)(tail >> 32);
-        if (better(c, b)) b = c;
-    }
-    __syncthreads();
-    b = block_best(b, s_part);
-    if (threadIdx.x == 0) {
-        const uint32_t v = b.id;
-        inS[v] = 1;
-        dirty[v >> kCellShift] = 1;  // its cell must forget v
-        gs->cov += delta[v];
-        gs->sum_c += one_f - w[v];
-        gs->done = 0;
-        seeds[round] = (int32_t)v;
-        cov_out[round] = (int64_t)gs->cov;
-        const u128 N = (u128)gs->cov * W + (u128)T * gs->sum_c;
-        const u128 D = (u128)T << f;
-        est_out[round] = u128_to_double(N) / u128_to_double(D);
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            KeyId b{0, 0xFFFFFFFFu, 0};
+            for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+                const KeyId c = ldcg_keyid(a.partial + i);
+                if (better(c, b)) b = c;
+            }
+            __syncthreads();
+            b = block_best(b, s_part);
+            if (threadIdx.x == 0) {
+                const uint32_t v = b.id;
+                a.inS[v] = 1;
+                // the committing block differs between rounds: running
+                // totals are read through L2 as well
+                const unsigned long long cov = __ldcg(&a.gs->cov) + __ldcg(a.delta + v);
+                const unsigned long long sum_c = __ldcg(&a.gs->sum_c) + (one_f - a.w[v]);
+                a.gs->cov = cov;
+                a.gs->sum_c = sum_c;
+                a.gs->done = 0;
+                a.seeds[round] = (int32_t)v;
+                a.cov_out[round] = (int64_t)cov;
+                const u128 N = (u128)cov * a.W + (u128)a.T * sum_c;
+                const u128 D = (u128)a.T << a.f;
+                a.est_out[round] = u128_to_double(N) / u128_to_double(D);
+                __threadfence();
+            }
+        }
+        grid.sync();
+        // cover the uncovered samples of the committed vertex
+        const int32_t v = __ldcg(a.seeds + round);
+        const uint64_t lo = a.inv_off[v], cnt = a.inv_off[v + 1] - lo;
+        const uint64_t nwarps = (uint64_t)gridDim.x * (kCovThreads / 32);
+        for (uint64_t base = ((uint64_t)blockIdx.x * (kCovThreads / 32) + wib) * 32; base < cnt;
+             base += nwarps * 32) {
+            const uint64_t x = base + lane;
+            uint64_t off = 0;
+            uint32_t len = 0;
+            if (x < cnt) {
+                const uint32_t j = a.inv[lo + x];
+                const uint32_t bit = 1u << (j & 31);
+                if ((atomicOr(&a.covered[j >> 5], bit) & bit) == 0) {
+                    off = a.h_off[j];
+                    len = a.h_len[j];
+                }
+            }
+            warp_members(off, len, a.arena, [&](int, int32_t u) { atomicSub(&a.delta[u], 1u); });
+        }
+        grid.sync();
     }
 }
 
-// Mark the still-uncovered samples of the chosen vertex covered and remove
-// their members' marginal coverage; cells of changed vertices become dirty.
-__global__ void __launch_bounds__(kCovThreads) k_cover(const int32_t* __restrict__ seeds, int32_t round,
-                                                       const uint64_t* __restrict__ inv_off,
-                                                       const uint32_t* __restrict__ inv,
-                                                       const uint64_t* __restrict__ h_off,
-                                                       const uint32_t* __restrict__ h_len,
-                                                       const int32_t* __restrict__ arena,
-                                                       uint32_t* __restrict__ covered,
-                                                       uint32_t* __restrict__ delta, uint32_t* __restrict__ dirty) {
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int32_t v = seeds[round];
-    const uint64_t lo = inv_off[v], cnt = inv_off[v + 1] - lo;
-    const uint64_t nwarps = (uint64_t)gridDim.x * (kCovThreads / 32);
-    for (uint64_t base = ((uint64_t)blockIdx.x * (kCovThreads / 32) + wib) * 32; base < cnt; base += nwarps * 32) {
-        const uint64_t x = base + lane;
-        uint64_t off = 0;
-        uint32_t len = 0;
-        if (x < cnt) {
-            const uint32_t j = inv[lo + x];
-            const uint32_t bit = 1u << (j & 31);
-            if ((atomicOr(&covered[j >> 5], bit) & bit) == 0) {
-                off = h_off[j];
-                len = h_len[j];
-            }
-        }
-        warp_members(off, len, arena, [&](int, int32_t u) {
-            atomicSub(&delta[u], 1u);
-            dirty[(uint32_t)u >> kCellShift] = 1;
-        });
+__global__ void k_delta_from_index(const uint64_t* __restrict__ inv_off, int64_t n, uint32_t* __restrict__ delta) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        delta[v] = (uint32_t)(inv_off[v + 1] - inv_off[v]);
+}
+
+int sketch_inverted(skis_sketch* s, cudaStream_t st, std::string* err) {
+    const char* where = "inverted index";
+    if (s->inv && s->inv_T == s->T) return SKIS_OK;
+    const int64_t n = s->g->n;
+    const uint64_t T = s->T;
+    if (T >= (1ull << 32)) {
+        *err = "inverted index: the sketch must hold fewer than 2^32 samples";
+        return SKIS_EINVAL;
     }
+    dev_free(s->inv, st);
+    s->inv = nullptr;
+    s->inv_T = 0;
+    if (!s->inv_off) CV_CUDA(dev_alloc_t(&s->inv_off, (size_t)n + 1, st));
+    uint32_t* cnt = nullptr;
+    uint64_t E = 0;
+    const int cblocks = coverage_blocks(T);
+    CV_CUDA(dev_alloc_t(&cnt, (size_t)n, st));
+    CV_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), st));
+    k_count_members<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, T, s->arena, cnt); note_launch();
+    CV_CUDA(cudaGetLastError());
+    CV_CUDA(scan_u32_to_u64(cnt, s->inv_off, n, st));
+    CV_CUDA(cudaMemcpyAsync(&E, s->inv_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CV_CUDA(cudaStreamSynchronize(st));
+    CV_CUDA(dev_alloc_t(&s->inv, (size_t)std::max<uint64_t>(E, 1), st));
+    CV_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), st));  // reused as fill cursors
+    k_fill_inverted<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, T, s->arena, s->inv_off, cnt, s->inv); note_launch();
+    CV_CUDA(cudaGetLastError());
+    dev_free(cnt, st);
+    s->inv_T = T;
+    return SKIS_OK;
 }
 
 int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, double* h_est, cudaStream_t st,
@@ -410,55 +569,57 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
         return SKIS_EINVAL;
     }
     if (k == 0) return SKIS_OK;
-    uint32_t *cnt = nullptr, *fill = nullptr, *inv = nullptr, *covered = nullptr;
-    uint64_t* inv_off = nullptr;
+    int rc = sketch_inverted(s, st, err);
+    if (rc != SKIS_OK) return rc;
+    uint32_t *delta = nullptr, *covered = nullptr;
     uint8_t* inS = nullptr;
-    KeyId* cell_best = nullptr;
-    uint32_t* dirty = nullptr;
+    KeyId* partial = nullptr;
     GreedyState* gs = nullptr;
     int32_t* d_seeds = nullptr;
     int64_t* d_cov = nullptr;
     double* d_est = nullptr;
-    uint64_t E = 0;
-    int rc = SKIS_OK;
-    const int cblocks = coverage_blocks(T);
-    const int ncells = (int)((n + kCell - 1) >> kCellShift);
     auto body = [&]() -> int {
-        CV_CUDA(dev_alloc_t(&cnt, (size_t)n, st));
-        CV_CUDA(dev_alloc_t(&fill, (size_t)n, st));
-        CV_CUDA(dev_alloc_t(&inv_off, (size_t)n + 1, st));
+        int per_sm = 0;
+        CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_rounds, kCovThreads, 0));
+        const int gblocks = sm_count() * std::max(1, std::min(per_sm, 4));
+        CV_CUDA(dev_alloc_t(&delta, (size_t)n, st));
         CV_CUDA(dev_alloc_t(&inS, (size_t)n, st));
         CV_CUDA(dev_alloc_t(&covered, (size_t)((T + 31) / 32), st));
-        CV_CUDA(dev_alloc_t(&cell_best, (size_t)ncells, st));
-        CV_CUDA(dev_alloc_t(&dirty, (size_t)ncells, st));
+        CV_CUDA(dev_alloc_t(&partial, (size_t)gblocks, st));
         CV_CUDA(dev_alloc_t(&gs, 1, st));
         CV_CUDA(dev_alloc_t(&d_seeds, (size_t)k, st));
         CV_CUDA(dev_alloc_t(&d_cov, (size_t)k, st));
         CV_CUDA(dev_alloc_t(&d_est, (size_t)k, st));
-        CV_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), st));
-        CV_CUDA(cudaMemsetAsync(fill, 0, (size_t)n * sizeof(uint32_t), st));
         CV_CUDA(cudaMemsetAsync(inS, 0, (size_t)n, st));
         CV_CUDA(cudaMemsetAsync(covered, 0, (size_t)((T + 31) / 32) * sizeof(uint32_t), st));
         CV_CUDA(cudaMemsetAsync(gs, 0, sizeof(GreedyState), st));
-        CV_CUDA(cudaMemsetAsync(dirty, 0x01, (size_t)ncells * sizeof(uint32_t), st));  // any nonzero = dirty
-        // Delta_R(v, {}) = number of samples containing v, and the inverted index
-        k_count_members<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, T, s->arena, cnt); note_launch();
+        // Delta_R(v, {}) = number of samples containing v = length of v's list
+        const int b1 = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8));
+        k_delta_from_index<<<b1, 256, 0, st>>>(s->inv_off, n, delta); note_launch();
         CV_CUDA(cudaGetLastError());
-        CV_CUDA(scan_u32_to_u64(cnt, inv_off, n, st));
-        CV_CUDA(cudaMemcpyAsync(&E, inv_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-        CV_CUDA(cudaStreamSynchronize(st));
-        CV_CUDA(dev_alloc_t(&inv, (size_t)std::max<uint64_t>(E, 1), st));
-        k_fill_inverted<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, T, s->arena, inv_off, fill, inv); note_launch();
-        CV_CUDA(cudaGetLastError());
-        const int cover_blocks = sm_count() * 4;
-        for (int32_t i = 0; i < k; ++i) {
-            k_argmax<<<ncells, kCovThreads, 0, st>>>(cnt, g->w, inS, n, g->W, T, g->f, cell_best, dirty, gs, i,
-                                                     d_seeds, d_cov, d_est); note_launch();
-            CV_CUDA(cudaGetLastError());
-            k_cover<<<cover_blocks, kCovThreads, 0, st>>>(d_seeds, i, inv_off, inv, s->h_off, s->h_len, s->arena,
-                                                          covered, cnt, dirty); note_launch();
-            CV_CUDA(cudaGetLastError());
-        }
+        GreedyArgs ga;
+        ga.w = g->w;
+        ga.inS = inS;
+        ga.delta = delta;
+        ga.n = n;
+        ga.W = g->W;
+        ga.T = T;
+        ga.f = g->f;
+        ga.k = k;
+        ga.inv_off = s->inv_off;
+        ga.inv = s->inv;
+        ga.h_off = s->h_off;
+        ga.h_len = s->h_len;
+        ga.arena = s->arena;
+        ga.covered = covered;
+        ga.partial = partial;
+        ga.gs = gs;
+        ga.seeds = d_seeds;
+        ga.cov_out = d_cov;
+        ga.est_out = d_est;
+        void* kargs[] = {&ga};
+        CV_CUDA(cudaLaunchCooperativeKernel((const void*)k_greedy_rounds, gblocks, kCovThreads, kargs, 0, st));
+        note_launch();
         CV_CUDA(cudaMemcpyAsync(h_seeds, d_seeds, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         if (h_cov) CV_CUDA(cudaMemcpyAsync(h_cov, d_cov, (size_t)k * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         if (h_est) CV_CUDA(cudaMemcpyAsync(h_est, d_est, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -466,14 +627,10 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
         return SKIS_OK;
     };
     rc = body();
-    dev_free(cnt, st);
-    dev_free(fill, st);
-    dev_free(inv, st);
+    dev_free(delta, st);
     dev_free(covered, st);
-    dev_free(inv_off, st);
     dev_free(inS, st);
-    dev_free(cell_best, st);
-    dev_free(dirty, st);
+    dev_free(partial, st);
     dev_free(gs, st);
     dev_free(d_seeds, st);
     dev_free(d_cov, st);

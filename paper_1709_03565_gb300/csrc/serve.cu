@@ -1,13 +1,15 @@
 // Continuous-batching influence-oracle server (Alg. 2 line 2, Eq. 21, served
-// against a device-resident sketch).
+// against a device-resident sketch and its inverted index).
 //
 // Requests (seed sets) are validated and queued on the host at submit time.
 // Each progress call retires finished batches (event polling, no host
 // threads) and admits queued requests, in arrival order, into every free
 // in-flight slot: up to max_batch requests (one query-mask bit each, at most
 // 64) whose seeds fit the slot's staging capacity. A slot owns a stream,
-// pinned host staging, device buffers and its own per-vertex query-mask
-// scratch, so batches on different slots overlap on the device. Results are
+// pinned host staging, device buffers and its own per-sample query-mask
+// scratch, so batches on different slots overlap on the device. Coverage is
+// counted through the sketch's inverted index, so a batch costs the total
+// length of its seeds' sample lists, not a scan of the sketch. Results are
 // exact integers (coverage) and the same binary64 quotient as skis_estimate,
 // whatever batch a request lands in.
 #include <algorithm>
@@ -35,7 +37,9 @@ struct Slot {
     int32_t* d_seeds = nullptr;
     int64_t* d_cov = nullptr;
     double* d_est = nullptr;
-    uint64_t* d_qmask = nullptr;
+    uint64_t* d_smask = nullptr;   // T per-sample query bits, zero between batches
+    uint32_t* d_chunk_cnt = nullptr;
+    uint64_t* d_chunk_off = nullptr;
     unsigned long long* d_qcov = nullptr;
     DevStatus* d_status = nullptr;
     std::vector<uint64_t> tickets;
@@ -87,7 +91,9 @@ static void release_slot(Slot& sl) {
     cudaFree(sl.d_seeds);
     cudaFree(sl.d_cov);
     cudaFree(sl.d_est);
-    cudaFree(sl.d_qmask);
+    cudaFree(sl.d_smask);
+    cudaFree(sl.d_chunk_cnt);
+    cudaFree(sl.d_chunk_off);
     cudaFree(sl.d_qcov);
     cudaFree(sl.d_status);
     if (sl.done) cudaEventDestroy(sl.done);
@@ -112,13 +118,20 @@ extern "C" int skis_server_create(skis_server** out, skis_sketch* s, int32_t slo
         if (seed_capacity < 1 || seed_capacity > (1ull << 31))
             return serve_fail(SKIS_EINVAL, "skis_server_create: seed_capacity must be in [1, 2^31]");
         if (s->T == 0) return serve_fail(SKIS_EINVAL, "skis_server_create: the sketch has no samples");
+        {
+            // requests are answered through the sketch's inverted index
+            std::string err;
+            const int rc = sketch_inverted(s, s->stream, &err);
+            if (rc != SKIS_OK) return serve_fail(rc, err);
+            const cudaError_t e = cudaStreamSynchronize(s->stream);
+            if (e != cudaSuccess) return serve_fail(SKIS_ERR_CUDA, std::string("skis_server_create: ") + cudaGetErrorString(e));
+        }
         skis_server* srv = new skis_server();
         srv->s = s;
         srv->max_batch = max_batch;
         srv->seed_cap = seed_capacity;
         srv->slots.resize((size_t)slots);
         srv->mark.assign((size_t)s->g->n, 0);
-        const int64_t n = s->g->n;
         for (Slot& sl : srv->slots) {
             cudaError_t e = cudaSuccess;
             auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
@@ -133,10 +146,12 @@ extern "C" int skis_server_create(skis_server** out, skis_sketch* s, int32_t slo
             chk(cudaMalloc((void**)&sl.d_seeds, seed_capacity * sizeof(int32_t)));
             chk(cudaMalloc((void**)&sl.d_cov, 64 * sizeof(int64_t)));
             chk(cudaMalloc((void**)&sl.d_est, 64 * sizeof(double)));
-            chk(cudaMalloc((void**)&sl.d_qmask, (size_t)n * sizeof(uint64_t)));
+            chk(cudaMalloc((void**)&sl.d_smask, (size_t)s->T * sizeof(uint64_t)));
+            chk(cudaMalloc((void**)&sl.d_chunk_cnt, seed_capacity * sizeof(uint32_t)));
+            chk(cudaMalloc((void**)&sl.d_chunk_off, (seed_capacity + 1) * sizeof(uint64_t)));
             chk(cudaMalloc((void**)&sl.d_qcov, 64 * sizeof(unsigned long long)));
             chk(cudaMalloc((void**)&sl.d_status, sizeof(DevStatus)));
-            if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_qmask, 0, (size_t)n * sizeof(uint64_t), sl.stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_smask, 0, (size_t)s->T * sizeof(uint64_t), sl.stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(sl.stream);
             if (e != cudaSuccess) {
                 skis_server_free(srv);
@@ -203,13 +218,10 @@ static int launch_batch(skis_server* srv, Slot& sl) {
     SV_CUDA(cudaMemsetAsync(sl.d_qcov, 0, 64 * sizeof(unsigned long long), st));
     SV_CUDA(cudaMemsetAsync(sl.d_status, 0, sizeof(DevStatus), st));
     const int wb = (q * 32 + 255) / 256;
-    const uint64_t groups = (s->T + 31) / 32;
-    const uint64_t cb = std::max<uint64_t>(1, std::min<uint64_t>((groups + 7) / 8, (uint64_t)sm_count() * 8));
-    k_qmask_set<<<wb, 256, 0, st>>>(sl.d_off, sl.d_seeds, 0, q, g->n, sl.d_qmask, sl.d_status); note_launch();
-    k_coverage<<<(unsigned)cb, 256, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, sl.d_qmask, sl.d_qcov); note_launch();
+    SV_CUDA(coverage_by_index(s, sl.d_off, sl.d_seeds, 0, q, 0, (int64_t)used, sl.d_chunk_cnt, sl.d_chunk_off,
+                              sl.d_smask, sl.d_qcov, st));
     k_estimate<<<wb, 256, 0, st>>>(sl.d_off, sl.d_seeds, 0, q, g->n, g->w, g->f, g->W, s->T, sl.d_qcov, sl.d_cov,
                                    sl.d_est); note_launch();
-    k_qmask_clear<<<wb, 256, 0, st>>>(sl.d_off, sl.d_seeds, 0, q, g->n, sl.d_qmask); note_launch();
     SV_CUDA(cudaGetLastError());
     SV_CUDA(cudaMemcpyAsync(sl.h_cov, sl.d_cov, (size_t)q * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     SV_CUDA(cudaMemcpyAsync(sl.h_est, sl.d_est, (size_t)q * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -219,7 +219,14 @@ struct skis_sketch {
     uint64_t last_to_warp = 0, last_deferred = 0, last_passes = 0;
     double last_thread_ms = 0, last_warp_ms = 0, last_cta_ms = 0, last_sample_ms = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // inverted index vertex -> samples (built on demand for the current T)
+    uint64_t* inv_off = nullptr;         // n+1
+    uint32_t* inv = nullptr;             // sample ids, vertex after vertex
+    uint64_t inv_T = 0;                  // T when the index was built (0 = none)
+    int query_index = 0;                 // 0 auto (use the index if built), 1 always, 2 never
     // query / greedy scratch (allocated on first use)
+    uint64_t* smask = nullptr;           // T per-sample query bits (inverted-index path)
+    uint64_t smask_cap = 0;
     uint64_t* qmask = nullptr;           // n per-vertex query bits
     unsigned long long* qcov = nullptr;  // 64 coverage counters
     skis::DevStatus* qstatus = nullptr;
@@ -228,10 +235,18 @@ struct skis_sketch {
 
 namespace skis {
 int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* err);
-int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds, int64_t* d_cov,
-                    double* d_est, cudaStream_t st, std::string* err);
+int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds, const int64_t* h_off,
+                    int64_t* d_cov, double* d_est, cudaStream_t st, std::string* err);
 int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, double* h_est, cudaStream_t st,
                   std::string* err);
+// Builds (or reuses) the inverted index of the current T samples.
+int sketch_inverted(skis_sketch* s, cudaStream_t st, std::string* err);
+// Coverage of queries [q0, q0 + qn) of a CSR batch through the inverted
+// index: cov[b - q0] = #samples meeting S_b. smask (T words, all zero on
+// entry) is restored to zero; chunk_cnt/chunk_off hold nseeds (+1) entries.
+cudaError_t coverage_by_index(const skis_sketch* s, const int64_t* off, const int32_t* seeds, int32_t q0,
+                              int32_t qn, int64_t seed_base, int64_t nseeds, uint32_t* chunk_cnt,
+                              uint64_t* chunk_off, uint64_t* smask, unsigned long long* cov, cudaStream_t st);
 void sketch_release(skis_sketch* s);
 
 // Records msg as the calling thread's last error (skis_last_error); returns code.

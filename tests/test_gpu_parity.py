@@ -125,6 +125,9 @@ def test_er_workload_full_parity(er_small):
     od, oc, oe = osk.greedy(50)
     assert np.array_equal(sd, od) and np.array_equal(sc, oc)
     np.testing.assert_allclose(se, oe, rtol=REL, atol=0)
+    # greedy built the inverted index: the same queries now walk it
+    cov2, est2 = skis.skis_estimate(s, off, seeds)
+    assert np.array_equal(cov2, ocov) and np.array_equal(est2, est)
     s.close()
 
 
@@ -165,13 +168,15 @@ def test_device_queries_and_batches_over_64(er_small):
     off, seeds = synth.seed_sets(spec["n"], sizes, 9)
     d_off = torch.from_numpy(off).cuda()
     d_seeds = torch.from_numpy(seeds).cuda()
-    d_cov = torch.empty(len(sizes), dtype=torch.int64, device="cuda")
-    d_est = torch.empty(len(sizes), dtype=torch.float64, device="cuda")
-    skis.skis_estimate(s, d_off, d_seeds, d_cov, d_est)
-    torch.cuda.synchronize()
     ocov, oest = osk.coverage(off, seeds)
-    assert np.array_equal(d_cov.cpu().numpy(), ocov)
-    np.testing.assert_allclose(d_est.cpu().numpy(), oest, rtol=REL, atol=0)
+    for mode in (2, 1, 0):  # scan the sketch; walk the inverted index; automatic
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_QUERY_INDEX, mode)
+        d_cov = torch.empty(len(sizes), dtype=torch.int64, device="cuda")
+        d_est = torch.empty(len(sizes), dtype=torch.float64, device="cuda")
+        skis.skis_estimate(s, d_off, d_seeds, d_cov, d_est)
+        torch.cuda.synchronize()
+        assert np.array_equal(d_cov.cpu().numpy(), ocov)
+        np.testing.assert_allclose(d_est.cpu().numpy(), oest, rtol=REL, atol=0)
     s.close()
 
 
