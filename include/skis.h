@@ -96,7 +96,8 @@ typedef struct skis_stats {
 } skis_stats;
 
 /* Sampling runs in three tiers chained by sample id: one lane per sample
- * (up to 16 members, in-rows up to THREAD_MAX_DEG edges), one warp per
+ * (up to 16 members, in-rows up to THREAD_MAX_DEG edges, up to
+ * THREAD_MAX_STEPS edge quads, up to 8 rejected rounds), one warp per
  * sample (up to 256 members), one CTA per sample (any size). Options tune
  * the split; they never change the samples. */
 typedef enum skis_option {
@@ -105,9 +106,11 @@ typedef enum skis_option {
     SKIS_OPT_WARP_BLOCKS = 2,    /* CTAs of the warp tier (default: full occupancy) */
     SKIS_OPT_THREAD_MAX_DEG = 3, /* longest in-row the thread tier expands (default 256; 0 = tier off) */
     SKIS_OPT_THREAD_BLOCKS = 4,  /* CTAs of the thread tier (default: full occupancy) */
-    SKIS_OPT_QUERY_INDEX = 5     /* skis_estimate: 0 = walk the inverted index (vertex -> samples) when
+    SKIS_OPT_QUERY_INDEX = 5,    /* skis_estimate: 0 = walk the inverted index (vertex -> samples) when
                                     it is built for the current samples, else scan the sketch (default);
                                     1 = build it if needed and walk it; 2 = always scan */
+    SKIS_OPT_THREAD_MAX_STEPS = 6 /* edge quads a sample may take in the thread tier before the warp
+                                     tier takes it over (default 256) */
 } skis_option;
 
 /* Load G = (V, E, w) (Sec. II-A) and build the device structures every later
@@ -147,6 +150,17 @@ int skis_sketch_create(skis_sketch **out, const skis_graph *g, uint64_t seed,
                        uint64_t arena_entries, void *cuda_stream);
 
 int skis_sketch_set_option(skis_sketch *s, int option, uint64_t value);
+
+/* Autotuner of the sampling tiers: times pilot sampling of ids
+ * [0, pilot_samples) on a scratch sketch under each candidate split
+ * (SKIS_OPT_THREAD_MAX_DEG in {0, 32, 64, 128, 256, 1024} x
+ * SKIS_OPT_THREAD_MAX_STEPS in {64, 128, 256}), keeps the fastest on s and
+ * reports it (outputs nullable; candidate_ms receives up to candidate_cap
+ * pilot times in that order, candidates_out their number). The pilot samples
+ * are discarded; the samples of s never depend on the split. */
+int skis_sketch_autotune(skis_sketch *s, uint64_t pilot_samples, uint32_t *chosen_max_deg,
+                         uint32_t *chosen_max_steps, double *candidate_ms, int32_t candidate_cap,
+                         int32_t *candidates_out, void *cuda_stream);
 
 /* Append IIS samples (Alg. 1) with ids [T, T + count) to the sketch. For
  * sample j:
@@ -224,6 +238,37 @@ void skis_sketch_free(skis_sketch *s);
 int skis_estimate_noalloc(const skis_sketch *s, int32_t num_queries, const int64_t *seed_offsets,
                           const int32_t *seeds, int64_t *coverage_out, double *estimate_out,
                           char *error_buf, uint64_t error_len, void *cuda_stream);
+
+/* Influence maximisation with DSSA-style doubling over SKIS sketches
+ * (Sec. V-B; the appendix "Improvements of SSA/DSSA using SKIS sketch"):
+ * two independent sketches R (Philox key seed_r) and R^c (seed_rc) start with
+ * n0 samples and double in place (capped at n_max) each round t = 1, 2, ...;
+ * greedy (Alg. 3) on R gives S_k, which is re-estimated on R^c; the run stops
+ * when Cov_R(S_k) >= lambda2 and
+ *   (e1 + e2 + e1 e2)(1 - 1/e - eps) + (1 - 1/e) e3 <= eps, with
+ *   e1 = I_R / I_Rc - 1, e2 = eps sqrt(n (1 + eps) / (2^(t-1) I_Rc)),
+ *   e3 = eps sqrt(n (1 + eps)(1 - 1/e - eps) / ((1 + eps/3) 2^(t-1) I_Rc)),
+ * or when R holds n_max samples. The paper gives Lambda_2 only up to a
+ * constant: lambda2 = 0 selects ceil((2 Gamma/n + 2 eps/3) ln(2 t_max / delta)
+ * / eps^2), t_max = the number of rounds from n0 to n_max. Estimates are
+ * formed on the host from exact integers with correctly rounded
+ * conversions, so the stopping decisions are reproducible. seeds_out:
+ * host int32[k]. Rejected with SKIS_EINVAL: k outside [1, n], eps outside
+ * (0, 1 - 1/e), delta outside (0, 1), not 1 <= n0 <= n_max < 2^32, Gamma = 0. */
+typedef struct skis_dssa_result {
+    int32_t rounds;      /* rounds run (t) */
+    int32_t stopped_by;  /* 1: the stop test held; 2: the sample cap was reached */
+    uint64_t samples;    /* |R| = |R^c| at the end */
+    uint64_t lambda2;    /* coverage threshold used */
+    int64_t coverage;    /* Cov_R(S_k) */
+    int64_t coverage_c;  /* Cov_{R^c}(S_k) */
+    double estimate;     /* I_R(S_k) */
+    double estimate_c;   /* I_{R^c}(S_k) */
+    double eps1, eps2, eps3;
+} skis_dssa_result;
+int skis_dssa_maxinf(const skis_graph *g, uint64_t seed_r, uint64_t seed_rc, int32_t k, double eps, double delta,
+                     uint64_t lambda2, uint64_t n0, uint64_t n_max, int32_t *seeds_out, skis_dssa_result *res,
+                     void *cuda_stream);
 
 /* Continuous-batching influence-oracle server over a device-resident sketch
  * (Alg. 2 line 2 for a stream of requests). skis_server_submit validates a

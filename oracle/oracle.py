@@ -54,9 +54,9 @@ def _lib():
         lib.orc_graph_scalars.restype = None
         lib.orc_graph_arrays.argtypes = [P] * 8
         lib.orc_graph_arrays.restype = None
-        lib.orc_sample_ids.argtypes = [P, u64, P, i64, u32, P, P, P, P, P, P, i64, P]
+        lib.orc_sample_ids.argtypes = [P, u64, P, i64, u32, ctypes.c_int, P, P, P, P, P, P, i64, P]
         lib.orc_sample_ids.restype = ctypes.c_int
-        lib.orc_sketch_build.argtypes = [P, u64, i64, u32, ctypes.POINTER(P)]
+        lib.orc_sketch_build.argtypes = [P, u64, i64, u32, ctypes.c_int, ctypes.POINTER(P)]
         lib.orc_sketch_build.restype = ctypes.c_int
         lib.orc_sketch_free.argtypes = [P]
         lib.orc_sketch_free.restype = None
@@ -126,7 +126,7 @@ class OracleGraph:
                                 _p(a["w"]), _p(a["prob"]), _p(a["alias"]))
         return a
 
-    def sample_ids(self, seed, ids, retry_cap=1 << 24, members_cap=None):
+    def sample_ids(self, seed, ids, retry_cap=1 << 24, members_cap=None, ris=False):
         """Samples for explicit ids: dict of per-sample arrays plus the
         concatenated members (insertion order) and their offsets."""
         ids = np.ascontiguousarray(ids, dtype=np.uint64)
@@ -138,7 +138,7 @@ class OracleGraph:
                        status=np.empty(c, np.int32))
             mem = np.empty(cap, np.int32)
             used = ctypes.c_int64()
-            rc = _lib().orc_sample_ids(self._h, seed, _p(ids), c, retry_cap, _p(out["src"]),
+            rc = _lib().orc_sample_ids(self._h, seed, _p(ids), c, retry_cap, 1 if ris else 0, _p(out["src"]),
                                        _p(out["retries"]), _p(out["len"]), _p(out["coins"]),
                                        _p(out["status"]), _p(mem), cap, ctypes.byref(used))
             if rc == ORC_ENOMEM and members_cap is None:
@@ -156,9 +156,9 @@ class OracleSketch:
     """The SKIS sketch R = {R_1..R_T} (sample ids 0..T-1) with Eq. 21 queries
     and Alg. 3 greedy."""
 
-    def __init__(self, graph: OracleGraph, seed: int, T: int, retry_cap: int = 1 << 24):
+    def __init__(self, graph: OracleGraph, seed: int, T: int, retry_cap: int = 1 << 24, ris: bool = False):
         h = ctypes.c_void_p()
-        rc = _lib().orc_sketch_build(graph._h, seed, T, retry_cap, ctypes.byref(h))
+        rc = _lib().orc_sketch_build(graph._h, seed, T, retry_cap, 1 if ris else 0, ctypes.byref(h))
         if rc != ORC_OK:
             raise OracleError(rc, "orc_sketch_build")
         self._h = h

@@ -50,6 +50,12 @@
  *      the other members: every in-edge of every popped vertex, which does
  *      not depend on the order of the queue.
  *   R8 Self-loops are rejected; parallel edges are independent coins.
+ *
+ * Variant (flag `ris`): plain reverse influence sampling (RIS, Borgs et al.;
+ * Sec. II-C): the source is uniform (the column draw alone), the source's
+ * in-edges get one unconditioned round (FIRST coins, round 0), so a sample
+ * may be singular; the estimator is n Cov / T (Lemma 1) and greedy maximises
+ * coverage alone.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -348,18 +354,29 @@ static int64_t draw_source(const orc_graph *g, uint64_t seed, uint64_t j)
 /* One IIS sample R_j (Alg. 1). visited must be all-zero on entry and is
  * restored before returning; members receives R_j in insertion order (the
  * source first); it must hold n entries. Returns ORC_OK or ORC_ERETRY. */
-static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t retry_cap,
+/* RIS source: uniform over V, the column draw of the SRC block alone. */
+static int64_t draw_source_uniform(const orc_graph *g, uint64_t seed, uint64_t j)
+{
+    uint32_t x[4];
+    philox_block(seed, 0, 0, DOM_SRC, j, x);
+    uint64_t u1 = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+    return (int64_t)(((u128)u1 * (u128)(uint64_t)g->n) >> 64);
+}
+
+static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t retry_cap, int ris,
                       char *visited, int32_t *members, int64_t *len_out, int32_t *src_out,
                       uint32_t *retries_out, uint64_t *coins_out)
 {
-    /* line 1: the source, Eq. probu */
-    int64_t v = draw_source(g, seed, j);
+    /* line 1: the source, Eq. probu (RIS: uniform) */
+    int64_t v = ris ? draw_source_uniform(g, seed, j) : draw_source(g, seed, j);
     int64_t b = g->off[v], e_end = g->off[v + 1];
     *src_out = (int32_t)v;
 
-    /* lines 2-6 in rejection form (R5): round r flips every in-edge of v */
+    /* lines 2-6 in rejection form (R5): round r flips every in-edge of v
+     * (RIS: round 0 only, accepted whatever its coins) */
     uint32_t r = 0;
     for (;; r++) {
+        if (ris) break;
         if (r >= retry_cap) {
             *retries_out = r;
             *len_out = 0;
@@ -409,11 +426,11 @@ static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t re
  * whose capacity is members_cap; *members_used receives the total. Returns
  * ORC_OK, or ORC_ENOMEM if members_cap is too small (outputs then partial). */
 int orc_sample_ids(const orc_graph *g, uint64_t seed, const uint64_t *ids, int64_t count,
-                   uint32_t retry_cap, int32_t *src_out, uint32_t *retries_out, int64_t *len_out,
-                   uint64_t *coins_out, int32_t *status_out, int32_t *members_out,
+                   uint32_t retry_cap, int ris, int32_t *src_out, uint32_t *retries_out,
+                   int64_t *len_out, uint64_t *coins_out, int32_t *status_out, int32_t *members_out,
                    int64_t members_cap, int64_t *members_used)
 {
-    if (g->W == 0) return ORC_EINVAL;
+    if (g->W == 0 && !ris) return ORC_EINVAL;
     char *visited = (char *)calloc((size_t)g->n, 1);
     int32_t *buf = (int32_t *)malloc((size_t)g->n * sizeof(int32_t));
     if (!visited || !buf) { free(visited); free(buf); return ORC_ENOMEM; }
@@ -421,7 +438,7 @@ int orc_sample_ids(const orc_graph *g, uint64_t seed, const uint64_t *ids, int64
     int rc = ORC_OK;
     for (int64_t t = 0; t < count; t++) {
         int64_t len;
-        status_out[t] = sample_one(g, seed, ids[t], retry_cap, visited, buf, &len, &src_out[t],
+        status_out[t] = sample_one(g, seed, ids[t], retry_cap, ris, visited, buf, &len, &src_out[t],
                                    &retries_out[t], &coins_out[t]);
         len_out[t] = len;
         if (used + len > members_cap) { rc = ORC_ENOMEM; break; }
@@ -439,6 +456,7 @@ int orc_sample_ids(const orc_graph *g, uint64_t seed, const uint64_t *ids, int64
  * with ids 0 .. T-1. */
 typedef struct orc_sketch {
     const orc_graph *g;
+    int ris;          /* plain RIS samples (n Cov / T estimator) */
     int64_t T;
     int64_t *off;     /* T+1 */
     int32_t *mem;     /* members, sample after sample */
@@ -454,14 +472,14 @@ void orc_sketch_free(orc_sketch *s)
     free(s);
 }
 
-int orc_sketch_build(const orc_graph *g, uint64_t seed, int64_t T, uint32_t retry_cap,
+int orc_sketch_build(const orc_graph *g, uint64_t seed, int64_t T, uint32_t retry_cap, int ris,
                      orc_sketch **out)
 {
     *out = NULL;
-    if (T < 1 || g->W == 0) return ORC_EINVAL;
+    if (T < 1 || (g->W == 0 && !ris)) return ORC_EINVAL;
     orc_sketch *s = (orc_sketch *)calloc(1, sizeof(orc_sketch));
     if (!s) return ORC_ENOMEM;
-    s->g = g; s->T = T;
+    s->g = g; s->T = T; s->ris = ris;
     s->off = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
     s->src = (int32_t *)malloc((size_t)T * sizeof(int32_t));
     s->retries = (uint32_t *)malloc((size_t)T * sizeof(uint32_t));
@@ -476,7 +494,7 @@ int orc_sketch_build(const orc_graph *g, uint64_t seed, int64_t T, uint32_t retr
     s->off[0] = 0;
     for (int64_t j = 0; j < T; j++) {
         int64_t len;
-        int rc = sample_one(g, seed, (uint64_t)j, retry_cap, visited, buf, &len, &s->src[j],
+        int rc = sample_one(g, seed, (uint64_t)j, retry_cap, ris, visited, buf, &len, &s->src[j],
                             &s->retries[j], &s->coins[j]);
         if (rc != ORC_OK) { free(visited); free(buf); orc_sketch_free(s); return rc; }
         if (s->off[j] + len > cap) {
@@ -510,6 +528,11 @@ void orc_sketch_arrays(const orc_sketch *s, int64_t *off, int32_t *mem, int32_t 
  * so that I_R(S) = N / D = Cov/T * Gamma~ + sum (1 - gamma~_v). */
 static void estimate_nd(const orc_sketch *s, int64_t cov, u128 sum_c, u128 *N, u128 *D)
 {
+    if (s->ris) {  /* Lemma 1: I(S) = n Pr[R meets S] */
+        *N = (u128)(uint64_t)cov * (u128)(uint64_t)s->g->n;
+        *D = (u128)(uint64_t)s->T;
+        return;
+    }
     *N = (u128)(uint64_t)cov * (u128)s->g->W + (u128)(uint64_t)s->T * sum_c;
     *D = (u128)(uint64_t)s->T << s->g->f;
 }
@@ -592,7 +615,8 @@ int orc_greedy(const orc_sketch *s, int32_t k, int32_t *seeds_out, int64_t *cov_
         u128 best_key = 0;
         for (int64_t v = 0; v < n; v++) {
             if (inS[v]) continue;
-            u128 key = (u128)(uint64_t)delta[v] * (u128)g->W + (u128)(uint64_t)T * (u128)(one_f - g->w[v]);
+            u128 key = s->ris ? (u128)(uint64_t)delta[v]
+                              : (u128)(uint64_t)delta[v] * (u128)g->W + (u128)(uint64_t)T * (u128)(one_f - g->w[v]);
             if (best < 0 || key > best_key) { best = v; best_key = key; }
         }
         inS[best] = 1;

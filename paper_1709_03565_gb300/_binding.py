@@ -18,7 +18,7 @@ SKIS_ERR_RETRY_LIMIT, SKIS_ERR_ARENA_FULL, SKIS_ERR_ABORTED = 4, 5, 6
 SKIS_W_EXPLICIT_P, SKIS_W_EXPLICIT_TAU, SKIS_W_WC, SKIS_W_TRI = 0, 1, 2, 3
 SKIS_MEM_HOST, SKIS_MEM_DEVICE = 0, 1
 SKIS_OPT_RETRY_CAP, SKIS_OPT_CTA_SLOTS, SKIS_OPT_WARP_BLOCKS = 0, 1, 2
-SKIS_OPT_THREAD_MAX_DEG, SKIS_OPT_THREAD_BLOCKS, SKIS_OPT_QUERY_INDEX = 3, 4, 5
+SKIS_OPT_THREAD_MAX_DEG, SKIS_OPT_THREAD_BLOCKS, SKIS_OPT_QUERY_INDEX, SKIS_OPT_THREAD_MAX_STEPS = 3, 4, 5, 6
 
 
 class SkisError(RuntimeError):
@@ -44,6 +44,13 @@ class skis_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class skis_dssa_result(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("stopped_by", ctypes.c_int32), ("samples", ctypes.c_uint64),
+                ("lambda2", ctypes.c_uint64), ("coverage", ctypes.c_int64), ("coverage_c", ctypes.c_int64),
+                ("estimate", ctypes.c_double), ("estimate_c", ctypes.c_double), ("eps1", ctypes.c_double),
+                ("eps2", ctypes.c_double), ("eps3", ctypes.c_double)]
+
+
 _lib = None
 
 # (name, restype, argtypes) of every entry point declared in include/skis.h
@@ -55,6 +62,7 @@ _SIGNATURES = [
     ("skis_graph_free", None, [_P]),
     ("skis_sketch_create", _INT, [_P, _P, _U64, _U64, _P]),
     ("skis_sketch_set_option", _INT, [_P, _INT, _U64]),
+    ("skis_sketch_autotune", _INT, [_P, _U64, _P, _P, _P, _I32, _P, _P]),
     ("skis_sample", _INT, [_P, _U64, _P, _P]),
     ("skis_estimate", _INT, [_P, _I32, _P, _P, _P, _P, _INT, _P]),
     ("skis_greedy_maxcover", _INT, [_P, _I32, _P, _P, _P, _P]),
@@ -62,6 +70,8 @@ _SIGNATURES = [
     ("skis_sketch_export", _INT, [_P, _U64, _U64, _P, _P, _P, _P, _P, _P, _U64, _P]),
     ("skis_sketch_free", None, [_P]),
     ("skis_estimate_noalloc", _INT, [_P, _I32, _P, _P, _P, _P, _P, _U64, _P]),
+    ("skis_dssa_maxinf", _INT, [_P, _U64, _U64, _I32, ctypes.c_double, ctypes.c_double, _U64, _U64, _U64, _P, _P,
+                                _P]),
     ("skis_server_create", _INT, [_P, _P, _I32, _I32, _U64]),
     ("skis_server_submit", _INT, [_P, _P, _I32, _P]),
     ("skis_server_progress", _INT, [_P, _I32, _P, _I32, _P]),
@@ -224,6 +234,16 @@ def skis_sketch_set_option(s: Sketch, option: int, value: int):
     _check(lib().skis_sketch_set_option(s.ptr, int(option), int(value)))
 
 
+def skis_sketch_autotune(s: Sketch, pilot_samples: int, stream=None) -> dict:
+    """Pick the fastest tier split on a pilot; returns the choice and the
+    pilot time of every candidate."""
+    d, m, nc = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_int32()
+    ms = np.zeros(32, np.float64)
+    _check(lib().skis_sketch_autotune(s.ptr, int(pilot_samples), ctypes.byref(d), ctypes.byref(m),
+                                      ctypes.c_void_p(ms.ctypes.data), 32, ctypes.byref(nc), _stream(stream)))
+    return dict(max_deg=d.value, max_steps=m.value, candidate_ms=ms[: nc.value].tolist())
+
+
 def skis_sample(s: Sketch, count: int, stream=None) -> int:
     nxt = ctypes.c_uint64()
     _check(lib().skis_sample(s.ptr, int(count), ctypes.byref(nxt), _stream(stream)))
@@ -301,6 +321,17 @@ def skis_estimate_noalloc(s: Sketch, seed_offsets, seeds, coverage_out, estimate
     if rc != SKIS_OK:
         raise SkisError(rc, buf.value.decode())
     return coverage_out, estimate_out
+
+
+def skis_dssa_maxinf(g: Graph, seed_r: int, seed_rc: int, k: int, eps: float, delta: float, lambda2: int = 0,
+                     n0: int = 1 << 12, n_max: int = 1 << 24, stream=None):
+    """DSSA-style doubling influence maximisation; returns (seeds, result dict)."""
+    seeds = np.empty(k, np.int32)
+    res = skis_dssa_result()
+    _check(lib().skis_dssa_maxinf(g.ptr, int(seed_r), int(seed_rc), int(k), float(eps), float(delta), int(lambda2),
+                                  int(n0), int(n_max), ctypes.c_void_p(seeds.ctypes.data), ctypes.byref(res),
+                                  _stream(stream)))
+    return seeds, {f: getattr(res, f) for f, _ in res._fields_}
 
 
 def skis_server_create(s: Sketch, slots: int = 4, max_batch: int = 64, seed_capacity: int = 1 << 16) -> Server:

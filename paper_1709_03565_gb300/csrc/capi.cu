@@ -194,6 +194,10 @@ extern "C" int skis_sketch_set_option(skis_sketch* s, int option, uint64_t value
             if (value > (1u << 30)) return fail(SKIS_EINVAL, "thread-tier degree limit must be at most 2^30");
             s->thread_max_deg = (uint32_t)value;
             return SKIS_OK;
+        case SKIS_OPT_THREAD_MAX_STEPS:
+            if (value < 1 || value > (1u << 30)) return fail(SKIS_EINVAL, "thread-tier step budget must be in [1, 2^30]");
+            s->thread_max_steps = (uint32_t)value;
+            return SKIS_OK;
         case SKIS_OPT_QUERY_INDEX:
             if (value > 2) return fail(SKIS_EINVAL, "query-index mode must be 0, 1 or 2");
             s->query_index = (int)value;
@@ -217,6 +221,26 @@ extern "C" int skis_sample(skis_sketch* s, uint64_t count, uint64_t* next_sample
     const int rc = sketch_sample(s, count, st, &err);
     if (next_sample_id_out) *next_sample_id_out = s->T;
     if (rc != SKIS_OK) return fail(rc, err);
+    return SKIS_OK;
+    API_CATCH
+}
+
+extern "C" int skis_sketch_autotune(skis_sketch* s, uint64_t pilot_samples, uint32_t* chosen_max_deg,
+                                    uint32_t* chosen_max_steps, double* candidate_ms, int32_t candidate_cap,
+                                    int32_t* candidates_out, void* cuda_stream) {
+    API_TRY
+    if (!s) return fail(SKIS_EINVAL, "skis_sketch_autotune: NULL sketch");
+    if (pilot_samples < 1 || pilot_samples > (1ull << 32))
+        return fail(SKIS_EINVAL, "skis_sketch_autotune: pilot_samples must be in [1, 2^32]");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s->stream = st;
+    std::string err;
+    int nc = 0;
+    const int rc = sketch_autotune(s, pilot_samples, st, candidate_ms, candidate_cap, &nc, &err);
+    if (candidates_out) *candidates_out = nc;
+    if (rc != SKIS_OK) return fail(rc, "skis_sketch_autotune: " + err);
+    if (chosen_max_deg) *chosen_max_deg = s->thread_max_deg;
+    if (chosen_max_steps) *chosen_max_steps = s->thread_max_steps;
     return SKIS_OK;
     API_CATCH
 }
@@ -420,6 +444,7 @@ void skis::sketch_release(skis_sketch* s) {
     dev_free(s->status, st);
     dev_free(s->to_warp_ids, st);
     dev_free(s->to_cta_ids, st);
+    dev_free(s->srcrec, st);
     dev_free(s->ovf_ids[0], st);
     dev_free(s->ovf_ids[1], st);
     dev_free(s->bitmaps, st);

@@ -50,6 +50,19 @@ __device__ __forceinline__ void warp_members(uint64_t off, uint32_t len, const i
     }
 }
 
+// Lanes adding to the same counter in one step (hub vertices recur across
+// samples) are merged: one atomic per distinct address among the calling
+// lanes, carrying the number of lanes.
+__device__ __forceinline__ void add_aggregated(uint32_t* counter, int32_t u, int sign) {
+    const unsigned active = __activemask();
+    const unsigned peers = __match_any_sync(active, u);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) {
+        const uint32_t c = (uint32_t)__popc(peers);
+        if (sign > 0) atomicAdd(&counter[u], c);
+        else atomicSub(&counter[u], c);
+    }
+}
+
 // ------------------------------------------------------------- coverage
 __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
                             int32_t qn, int64_t n, uint64_t* __restrict__ qmask, DevStatus* st) {
@@ -334,7 +347,7 @@ __global__ void __launch_bounds__(kCovThreads) k_count_members(const uint64_t* _
         const uint64_t j = gidx * 32 + lane;
         const bool valid = j < T;
         warp_members(valid ? h_off[j] : 0, valid ? h_len[j] : 0u, arena,
-                     [&](int, int32_t u) { atomicAdd(&cnt[u], 1u); });
+                     [&](int, int32_t u) { add_aggregated(cnt, u, +1); });
     }
 }
 
@@ -352,7 +365,14 @@ __global__ void __launch_bounds__(kCovThreads) k_fill_inverted(const uint64_t* _
         const uint64_t j = j0 + lane;
         const bool valid = j < T;
         warp_members(valid ? h_off[j] : 0, valid ? h_len[j] : 0u, arena, [&](int owner, int32_t u) {
-            const uint32_t pos = atomicAdd(&fill[u], 1u);
+            // lanes holding the same vertex reserve their slots with one atomic
+            const unsigned active = __activemask();
+            const unsigned peers = __match_any_sync(active, u);
+            const int leader = __ffs(peers) - 1;
+            uint32_t base = 0;
+            if ((threadIdx.x & 31) == leader) base = atomicAdd(&fill[u], (uint32_t)__popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            const uint32_t pos = base + __popc(peers & lanemask_lt());
             inv[inv_off[u] + pos] = (uint32_t)(j0 + owner);
         });
     }
@@ -511,7 +531,7 @@ __global__ void __launch_bounds__(kCovThreads) k_greedy_rounds(GreedyArgs a) {
                     len = a.h_len[j];
                 }
             }
-            warp_members(off, len, a.arena, [&](int, int32_t u) { atomicSub(&a.delta[u], 1u); });
+            warp_members(off, len, a.arena, [&](int, int32_t u) { add_aggregated(a.delta, u, -1); });
         }
         grid.sync();
     }

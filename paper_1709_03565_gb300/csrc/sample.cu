@@ -51,6 +51,7 @@ struct SampleArgs {
     uint64_t n, W, seed;
     uint32_t retry_cap;
     uint32_t max_deg;                  // thread tier: longest in-row it expands
+    uint32_t max_steps;                // thread tier: edge quads per sample before handing it on
     // input ids: first_id + t (ids == nullptr) or ids[t], t < count (or
     // t < *count_dev when the list was filled by the previous tier)
     const uint64_t* ids;
@@ -73,6 +74,7 @@ struct SampleArgs {
     uint32_t* bitmaps;
     int32_t* queues;
     uint64_t bitmap_words;
+    const uint4* srcrec;  // thread tier: source record per input t (k_sources), or nullptr
 };
 
 __device__ __forceinline__ uint64_t input_count(const SampleArgs& a) {
@@ -298,8 +300,29 @@ __device__ __forceinline__ void record_retry_failure(const SampleArgs& a, uint64
     atomicMin(&a.status->first_bad, (unsigned long long)j);
 }
 
+// Alg. 1 line 1 for every input id at once: the source of sample j and its
+// in-row, as 16 bytes (source, degree, row offset, row threshold), so that a
+// thread-tier lane starting a sample makes one coalesced load. Row offsets
+// fit 32 bits because graphs hold fewer than 2^32 - 8 edges.
+__global__ void k_sources(SampleArgs a, uint4* __restrict__ rec) {
+    const uint64_t count = input_count(a);
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = draw_source(a, input_id(a, t));
+        const RowInfo rv = a.rows[v];
+        rec[t] = make_uint4(v, rv.deg, (uint32_t)rv.off, rv.tau);
+    }
+}
+
 // ----------------------------------------------------------- thread tier
-__global__ void __launch_bounds__(kThreadBlock) k_iis_thread(SampleArgs a) {
+// Lane states of the thread tier. A load issued in one iteration is first
+// read in a later one (kStart: the source record; kRowWait: the next row),
+// so a lane that just claimed a sample or popped a vertex never stalls its
+// warp; a row prefetched while the current row is still being expanded lets
+// the lane switch rows without losing an iteration.
+enum : uint32_t { kIdle = 0, kStart = 1, kRun = 2, kRowWait = 3 };
+
+__global__ void __launch_bounds__(kThreadBlock, 5) k_iis_thread(SampleArgs a) {
     __shared__ int32_t s_q[kThreadBlock / 32][kThreadQ][32];
     const int lane = threadIdx.x & 31;
     int32_t(*const mq)[32] = s_q[threadIdx.x >> 5];  // mq[k][lane]: member k of this lane's sample
@@ -307,127 +330,158 @@ __global__ void __launch_bounds__(kThreadBlock) k_iis_thread(SampleArgs a) {
     const uint4* __restrict__ tau4 = reinterpret_cast<const uint4*>(a.tau);
     const int4* __restrict__ src4 = reinterpret_cast<const int4*>(a.src);
 
-    // per-lane sample state
-    bool busy = false, first = true, any = false, rowleft = false;
-    uint64_t j = 0, qc = 0, q_first = 0, q_last = 0, lo = 0, hi = 0, coins = 0;
+    // per-lane sample state; edge positions fit 32 bits (m < 2^32 - 8)
+    uint32_t state = kIdle;
+    uint64_t j = 0, coins = 0;
+    uint4 rec = make_uint4(0, 0, 0, 0);
     uint32_t v = 0, r = 0, len = 0, head = 0, src_deg = 0, tau_row = 0;
+    uint32_t qc = 0, q_first = 0, q_last = 0, lo = 0, hi = 0, steps = 0;
+    bool first = true, any = false, rowleft = false;
+    bool nx = false;  // a row record for member `head` is loaded (or in flight) in nxr
+    RowInfo nxr;
+    nxr.off = 0; nxr.deg = 0; nxr.tau = 0;
     bool exhausted = false;                 // warp-uniform: no ids left to claim
     uint64_t chunk_pos = 0, chunk_end = 0;  // this warp's arena reservation
 
     for (;;) {
         // idle lanes claim the next ids together (one atomic per warp)
-        const unsigned idle = __ballot_sync(kFull, !busy);
+        bool claimed_now = false;
+        const unsigned idle = __ballot_sync(kFull, state == kIdle);
         if (idle && !exhausted) {
             const int leader = __ffs(idle) - 1;
             unsigned long long base = 0;
             if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(idle));
             base = __shfl_sync(kFull, base, leader);
             if (base + __popc(idle) >= count) exhausted = true;
-            if (!busy) {
+            if (state == kIdle) {
                 const uint64_t t = base + __popc(idle & lanemask_lt());
                 if (t < count) {
                     j = input_id(a, t);
-                    v = draw_source(a, j);  // Alg. 1 line 1
-                    const RowInfo rv = a.rows[v];
-                    if (rv.deg > a.max_deg) {
-                        hand_on(a, j);
+                    if (a.srcrec) {
+                        rec = __ldg(a.srcrec + t);  // Alg. 1 line 1, drawn by k_sources
                     } else {
-                        busy = true;
-                        first = true;
-                        any = false;
-                        r = 0;
-                        mq[0][lane] = (int32_t)v;
-                        len = 1;
-                        head = 1;
-                        src_deg = rv.deg;
-                        tau_row = rv.tau;
-                        lo = rv.off;
-                        hi = rv.off + rv.deg;
-                        q_first = lo >> 2;
-                        q_last = (hi - 1) >> 2;
-                        qc = q_first;
-                        rowleft = true;
-                        coins = 0;
+                        const uint32_t sv = draw_source(a, j);
+                        const RowInfo rv = a.rows[sv];
+                        rec = make_uint4(sv, rv.deg, (uint32_t)rv.off, rv.tau);
                     }
+                    state = kStart;
+                    claimed_now = true;
                 }
             }
         }
-        if (!__any_sync(kFull, busy)) {
+        if (!__any_sync(kFull, state != kIdle)) {
             if (exhausted) break;
             continue;
         }
 
         bool done = false, handed = false, failed = false;
-        if (busy) {
-            // one edge quad of the current row: coins of lines 4-6 (first
-            // step, round r) or of line 9 (reverse BFS)
-            if (rowleft) {
-                const uint4 x = coin_block(a.seed, qc, first ? r : 0u, first ? kDomFirst : kDomBfs, j);
-                const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_row, tau_row, tau_row, tau_row);
-                const uint64_t e0 = qc << 2;
-                unsigned live = 0;
-                live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
-                live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
-                live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
-                live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
-                if (live) {
-                    any = true;
-                    const int4 s4 = __ldg(src4 + qc);
-                    const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (!((live >> k) & 1u) || handed) continue;
-                        const int32_t u = cand[k];
-                        bool seen = false;
-                        for (uint32_t i = 0; i < len; ++i)
-                            if (mq[i][lane] == u) { seen = true; break; }
-                        if (seen) continue;
-                        if (len == (uint32_t)kThreadQ) handed = true;
-                        else mq[len++][lane] = u;
-                    }
-                }
-                ++qc;
-                rowleft = qc <= q_last;
+        // transitions (register moves; loads consumed here were issued earlier)
+        if (state == kStart && !claimed_now) {
+            v = rec.x;
+            src_deg = rec.y;
+            if (src_deg > a.max_deg) {
+                handed = true;
+            } else {
+                lo = rec.z;
+                hi = rec.z + rec.y;
+                tau_row = rec.w;
+                first = true;
+                any = false;
+                r = 0;
+                mq[0][lane] = (int32_t)v;
+                len = 1;
+                head = 1;
+                nx = false;
+                coins = 0;
+                steps = 0;
+                q_first = lo >> 2;
+                q_last = (hi - 1) >> 2;
+                qc = q_first;
+                rowleft = true;
+                state = kRun;
             }
-            if (!handed && !rowleft) {
-                if (first) {  // end of a first-step round: accept it or redraw
-                    if (any) {
-                        first = false;
-                        coins = (uint64_t)src_deg * (r + 1);
-                    } else if (++r >= a.retry_cap) {
-                        failed = true;
-                    } else if (r >= kThreadMaxRetries) {
-                        handed = true;  // a rare source: the warp tier searches rounds in parallel
-                    } else {
-                        qc = q_first;
-                        rowleft = true;
-                    }
-                }
-                if (!first && !failed && !handed) {  // pop the next queued vertex
-                    if (head < len) {
-                        const RowInfo rw = a.rows[mq[head][lane]];
-                        ++head;
-                        coins += rw.deg;
-                        if (rw.deg > a.max_deg) {
-                            handed = true;
-                        } else if (rw.deg > 0) {
-                            lo = rw.off;
-                            hi = rw.off + rw.deg;
-                            tau_row = rw.tau;
-                            q_first = lo >> 2;
-                            q_last = (hi - 1) >> 2;
-                            qc = q_first;
-                            rowleft = true;
-                        }
-                    } else {
-                        done = true;
-                    }
-                }
-            }
-            if (handed) hand_on(a, j);
-            if (failed) record_retry_failure(a, j, v, r, src_deg);
-            if (handed || failed) busy = false;
         }
+        if (state == kRun && !rowleft && first) {  // end of a first-step round
+            if (any) {
+                first = false;
+                coins = (uint64_t)src_deg * (r + 1);
+            } else if (++r >= a.retry_cap) {
+                failed = true;
+            } else if (r >= kThreadMaxRetries) {
+                handed = true;  // a rare source: the warp tier searches rounds in parallel
+            } else {
+                qc = q_first;
+                rowleft = true;
+            }
+        }
+        if (state == kRowWait || (state == kRun && !rowleft && !first && !failed && !handed)) {
+            // next row of the reverse BFS (Alg. 1 line 8: pop)
+            if (nx) {
+                ++head;
+                nx = false;
+                state = kRun;
+                coins += nxr.deg;
+                if (nxr.deg > a.max_deg) {
+                    handed = true;
+                } else if (nxr.deg > 0) {
+                    lo = (uint32_t)nxr.off;
+                    hi = lo + nxr.deg;
+                    tau_row = nxr.tau;
+                    q_first = lo >> 2;
+                    q_last = (hi - 1) >> 2;
+                    qc = q_first;
+                    rowleft = true;
+                }
+            } else if (head < len) {
+                nxr = a.rows[mq[head][lane]];
+                nx = true;
+                state = kRowWait;  // read next iteration
+            } else {
+                done = true;
+            }
+        }
+
+        // one edge quad of the current row: coins of lines 4-6 (first step,
+        // round r) or of line 9 (reverse BFS)
+        if (state == kRun && rowleft && !handed && !failed) {
+            const uint4 x = coin_block(a.seed, qc, first ? r : 0u, first ? kDomFirst : kDomBfs, j);
+            const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_row, tau_row, tau_row, tau_row);
+            const uint32_t e0 = qc << 2;
+            uint32_t inrow = 0xFu;
+            if (e0 < lo) inrow &= 0xFu << (lo - e0);
+            if (e0 + 4 > hi) inrow &= 0xFu >> (e0 + 4 - hi);
+            uint32_t live = (coin_live(x.x, t4.x) ? 1u : 0u) | (coin_live(x.y, t4.y) ? 2u : 0u) |
+                            (coin_live(x.z, t4.z) ? 4u : 0u) | (coin_live(x.w, t4.w) ? 8u : 0u);
+            live &= inrow;
+            if (live) {
+                any = true;
+                const int4 s4 = __ldg(src4 + qc);
+                const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!((live >> k) & 1u) || handed) continue;
+                    const int32_t u = cand[k];
+                    bool seen = false;
+                    for (uint32_t i = 0; i < len; ++i)
+                        if (mq[i][lane] == u) { seen = true; break; }
+                    if (seen) continue;
+                    if (len == (uint32_t)kThreadQ) handed = true;
+                    else mq[len++][lane] = u;
+                }
+            }
+            ++qc;
+            rowleft = qc <= q_last;
+            // a sample with much work is finished faster by a whole warp
+            if (++steps > a.max_steps) handed = true;
+        }
+        // prefetch the row of the next queued vertex while this row runs
+        if (state == kRun && !nx && (any || !first) && head < len && !handed && !failed) {
+            nxr = a.rows[mq[head][lane]];
+            nx = true;
+        }
+        if (handed) hand_on(a, j);
+        if (failed) record_retry_failure(a, j, v, r, src_deg);
+        if (handed || failed) state = kIdle;
 
         // finished samples: one arena reservation for the warp's batch
         const unsigned dm = __ballot_sync(kFull, done);
@@ -466,7 +520,7 @@ __global__ void __launch_bounds__(kThreadBlock) k_iis_thread(SampleArgs a) {
                 } else {
                     arena_overflow(a, j);
                 }
-                busy = false;
+                state = kIdle;
             }
             if (fits) chunk_pos += total;
         }
@@ -731,6 +785,9 @@ static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st
         SK_CUDA(dev_alloc_t(&s->to_cta_ids, (size_t)count, st));
         SK_CUDA(dev_alloc_t(&s->ovf_ids[0], (size_t)count, st));
         SK_CUDA(dev_alloc_t(&s->ovf_ids[1], (size_t)count, st));
+        dev_free(s->srcrec, st);
+        s->srcrec = nullptr;
+        SK_CUDA(dev_alloc_t(&s->srcrec, (size_t)count, st));
         s->list_cap = count;
     }
     if (!s->arena) {
@@ -799,6 +856,7 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.seed = s->seed;
     base.retry_cap = s->retry_cap;
     base.max_deg = s->thread_max_deg;
+    base.max_steps = s->thread_max_steps;
     base.ids = nullptr;
     base.first_id = s->T;
     base.count = count;
@@ -816,6 +874,7 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.bitmaps = s->bitmaps;
     base.queues = s->queues;
     base.bitmap_words = s->bitmap_words;
+    base.srcrec = nullptr;
 
     DevStatus hst;
     SampleCounters hc;
@@ -851,6 +910,10 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
 
         SK_CUDA(cudaEventRecord(s->ev[0], st));
         if (thread_tier) {
+            const uint64_t in_count = base.count;
+            k_sources<<<(int)std::max<uint64_t>(1, std::min<uint64_t>((in_count + 255) / 256, (uint64_t)sm_count() * 16)),
+                        256, 0, st>>>(at, s->srcrec); note_launch();
+            at.srcrec = s->srcrec;
             k_iis_thread<<<thread_blocks, kThreadBlock, 0, st>>>(at); note_launch();
             SK_CUDA(cudaGetLastError());
         }
@@ -906,6 +969,59 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
                " rounds) at sample id " + std::to_string(hst.first_bad) + "; failed samples are empty";
         return SKIS_ERR_RETRY_LIMIT;
     }
+    return SKIS_OK;
+}
+
+// Autotuner of the tier split: pilot sampling of ids [0, pilot) on a scratch
+// sketch under each candidate (thread-tier degree limit, step budget), best of
+// two runs each, fastest kept. Samples do not depend on the split, so only
+// time is compared.
+int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* cand_ms, int cand_cap, int* ncand,
+                    std::string* err) {
+    static const uint32_t kDeg[] = {0, 32, 64, 128, 256, 1024};
+    static const uint32_t kSteps[] = {64, 128, 256};
+    skis_sketch tmp;
+    tmp.g = s->g;
+    tmp.seed = s->seed;
+    tmp.retry_cap = s->retry_cap;
+    tmp.cta_slots = s->cta_slots;
+    tmp.warp_blocks = s->warp_blocks;
+    tmp.thread_blocks = s->thread_blocks;
+    tmp.stream = st;
+    double best = 1e300;
+    uint32_t best_deg = s->thread_max_deg, best_steps = s->thread_max_steps;
+    int k = 0, rc = SKIS_OK;
+    for (uint32_t d : kDeg) {
+        for (uint32_t m : kSteps) {
+            if (d == 0 && m != kSteps[0]) continue;  // no thread tier: the budget is moot
+            tmp.thread_max_deg = d;
+            tmp.thread_max_steps = m;
+            double ms = 1e300;
+            for (int rep = 0; rep < 2 && rc == SKIS_OK; ++rep) {
+                tmp.T = 0;
+                if (tmp.ctr) {
+                    const cudaError_t e = cudaMemsetAsync(&tmp.ctr->arena, 0, sizeof(unsigned long long), st);
+                    if (e != cudaSuccess) { *err = cudaGetErrorString(e); rc = SKIS_ERR_CUDA; }
+                }
+                if (rc == SKIS_OK) rc = sketch_sample(&tmp, pilot, st, err);
+                if (rc == SKIS_OK) ms = std::min(ms, tmp.last_sample_ms);
+            }
+            if (rc != SKIS_OK) break;
+            if (cand_ms && k < cand_cap) cand_ms[k] = ms;
+            ++k;
+            if (ms < best) {
+                best = ms;
+                best_deg = d;
+                best_steps = m;
+            }
+        }
+        if (rc != SKIS_OK) break;
+    }
+    sketch_release(&tmp);
+    if (ncand) *ncand = k;
+    if (rc != SKIS_OK) return rc;
+    s->thread_max_deg = best_deg;
+    s->thread_max_steps = best_steps;
     return SKIS_OK;
 }
 

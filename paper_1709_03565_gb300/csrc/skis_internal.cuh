@@ -55,11 +55,10 @@ enum : unsigned int {
 __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
-        const uint32_t hi_a = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo_a = 0xD2511F53u * c.x;
-        const uint32_t hi_b = __umulhi(0xCD9E8D57u, c.z);
-        const uint32_t lo_b = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        // one 32 x 32 -> 64-bit product per multiplier gives both halves
+        const uint64_t pa = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t pb = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(pb >> 32) ^ c.y ^ k0, (uint32_t)pb, (uint32_t)(pa >> 32) ^ c.w ^ k1, (uint32_t)pa);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
@@ -204,6 +203,7 @@ struct skis_sketch {
     uint64_t* to_warp_ids = nullptr;     // thread tier -> warp tier
     uint64_t* to_cta_ids = nullptr;      // warp tier -> CTA tier
     uint64_t* ovf_ids[2] = {nullptr, nullptr};
+    uint4* srcrec = nullptr;             // thread tier: prepared source records
     uint64_t list_cap = 0;
     uint32_t* bitmaps = nullptr;         // CTA tier: one n-bit visited bitmap per slot
     int32_t* queues = nullptr;           // CTA tier: one n-entry queue per slot
@@ -215,6 +215,7 @@ struct skis_sketch {
     int warp_blocks = 0;                 // 0 = automatic
     int thread_blocks = 0;               // 0 = automatic
     uint32_t thread_max_deg = 256;       // longest in-row the thread tier expands (0 = tier off)
+    uint32_t thread_max_steps = 256;     // edge quads per sample in the thread tier
     // last-call statistics
     uint64_t last_to_warp = 0, last_deferred = 0, last_passes = 0;
     double last_thread_ms = 0, last_warp_ms = 0, last_cta_ms = 0, last_sample_ms = 0;
@@ -248,6 +249,8 @@ cudaError_t coverage_by_index(const skis_sketch* s, const int64_t* off, const in
                               int32_t qn, int64_t seed_base, int64_t nseeds, uint32_t* chunk_cnt,
                               uint64_t* chunk_off, uint64_t* smask, unsigned long long* cov, cudaStream_t st);
 void sketch_release(skis_sketch* s);
+int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* cand_ms, int cand_cap, int* ncand,
+                    std::string* err);
 
 // Records msg as the calling thread's last error (skis_last_error); returns code.
 int set_last_error(int code, const std::string& msg);

@@ -304,3 +304,16 @@ def test_full_size_greedy_and_coverage(chunglu_full):
     ocov, oest = osk.coverage(off, seeds)
     assert np.array_equal(cov, ocov)
     np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
+
+
+def test_autotuned_split_gives_the_same_samples(er_small):
+    spec, src, dst, g, o, osk, seed, T = er_small
+    s = skis.skis_sketch_create(g, seed)
+    tune = skis.skis_sketch_autotune(s, 20_000)
+    assert tune["max_deg"] in (0, 32, 64, 128, 256, 1024) and tune["max_steps"] in (64, 128, 256)
+    assert len(tune["candidate_ms"]) == 16 and all(x > 0 for x in tune["candidate_ms"])
+    skis.skis_sample(s, 30_000)
+    dev = skis.skis_sketch_export(s, 0, 30_000)
+    ora = o.sample_ids(seed, np.arange(30_000, dtype=np.uint64))
+    assert_samples_equal(dev, ora)
+    s.close()
