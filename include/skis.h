@@ -109,8 +109,13 @@ typedef enum skis_option {
     SKIS_OPT_QUERY_INDEX = 5,    /* skis_estimate: 0 = walk the inverted index (vertex -> samples) when
                                     it is built for the current samples, else scan the sketch (default);
                                     1 = build it if needed and walk it; 2 = always scan */
-    SKIS_OPT_THREAD_MAX_STEPS = 6 /* edge quads a sample may take in the thread tier before the warp
-                                     tier takes it over (default 256) */
+    SKIS_OPT_THREAD_MAX_STEPS = 6, /* edge quads a sample may take in the thread tier before the warp
+                                      tier takes it over (default 256) */
+    SKIS_OPT_SAMPLER = 7          /* 0 = IIS samples (Alg. 1, default); 1 = plain RIS samples (Sec. II-C,
+                                     Borgs et al.): uniform source (the column draw alone), one
+                                     unconditioned round of the source's in-edges (singular samples
+                                     occur), estimator n Cov / T (Lemma 1), greedy key Delta alone.
+                                     Set before the first skis_sample. */
 } skis_option;
 
 /* Load G = (V, E, w) (Sec. II-A) and build the device structures every later

@@ -19,6 +19,7 @@ SKIS_W_EXPLICIT_P, SKIS_W_EXPLICIT_TAU, SKIS_W_WC, SKIS_W_TRI = 0, 1, 2, 3
 SKIS_MEM_HOST, SKIS_MEM_DEVICE = 0, 1
 SKIS_OPT_RETRY_CAP, SKIS_OPT_CTA_SLOTS, SKIS_OPT_WARP_BLOCKS = 0, 1, 2
 SKIS_OPT_THREAD_MAX_DEG, SKIS_OPT_THREAD_BLOCKS, SKIS_OPT_QUERY_INDEX, SKIS_OPT_THREAD_MAX_STEPS = 3, 4, 5, 6
+SKIS_OPT_SAMPLER = 7
 
 
 class SkisError(RuntimeError):

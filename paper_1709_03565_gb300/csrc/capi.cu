@@ -198,6 +198,11 @@ extern "C" int skis_sketch_set_option(skis_sketch* s, int option, uint64_t value
             if (value < 1 || value > (1u << 30)) return fail(SKIS_EINVAL, "thread-tier step budget must be in [1, 2^30]");
             s->thread_max_steps = (uint32_t)value;
             return SKIS_OK;
+        case SKIS_OPT_SAMPLER:
+            if (value > 1) return fail(SKIS_EINVAL, "sampler must be 0 (IIS) or 1 (RIS)");
+            if (s->T != 0) return fail(SKIS_EINVAL, "the sampler is chosen before the first sample");
+            s->ris = (int)value;
+            return SKIS_OK;
         case SKIS_OPT_QUERY_INDEX:
             if (value > 2) return fail(SKIS_EINVAL, "query-index mode must be 0, 1 or 2");
             s->query_index = (int)value;

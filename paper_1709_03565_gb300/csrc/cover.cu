@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kCovThreads) k_coverage(const uint64_t* __rest
 __global__ void k_estimate(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
                            int32_t qn, int64_t n, const uint64_t* __restrict__ w, int f, uint64_t W, uint64_t T,
                            const unsigned long long* __restrict__ cov, int64_t* __restrict__ cov_out,
-                           double* __restrict__ est_out) {
+                           double* __restrict__ est_out, int ris) {
     const int lane = threadIdx.x & 31;
     const int32_t b = q0 + (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (b >= q0 + qn) return;
@@ -162,8 +162,9 @@ __global__ void k_estimate(const int64_t* __restrict__ off, const int32_t* __res
     for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(kFull, s, d);
     if (lane == 0) {
         const uint64_t c = cov[b - q0];
-        const u128 N = (u128)c * W + (u128)T * s;
-        const u128 D = (u128)T << f;
+        // RIS (Lemma 1): n Cov / T; SKIS (Eq. 21): (Cov W + T sum) / (T 2^f)
+        const u128 N = ris ? (u128)c * (uint64_t)n : (u128)c * W + (u128)T * s;
+        const u128 D = ris ? (u128)T : (u128)T << f;
         if (cov_out) cov_out[b] = (int64_t)c;
         est_out[b] = u128_to_double(N) / u128_to_double(D);
     }
@@ -317,7 +318,8 @@ int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32
             k_coverage<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, s->qmask, s->qcov); note_launch();
             CV_CUDA(cudaGetLastError());
         }
-        k_estimate<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, g->w, g->f, g->W, s->T, s->qcov, d_cov, d_est); note_launch();
+        k_estimate<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, g->w, g->f, g->W, s->T, s->qcov, d_cov, d_est,
+                                       s->ris); note_launch();
         CV_CUDA(cudaGetLastError());
         k_qmask_clear<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask); note_launch();
         CV_CUDA(cudaGetLastError());
@@ -452,6 +454,7 @@ struct GreedyArgs {
     int32_t* seeds;
     int64_t* cov_out;
     double* est_out;
+    int ris;
 };
 
 __device__ __forceinline__ KeyId ldcg_keyid(const KeyId* p) {
@@ -476,7 +479,8 @@ __global__ void __launch_bounds__(kCovThreads) k_greedy_rounds(GreedyArgs a) {
         KeyId best{0, 0xFFFFFFFFu, 0};
         for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
             if (__ldcg(a.inS + v)) continue;
-            const KeyId c{(u128)__ldcg(a.delta + v) * a.W + (u128)a.T * (one_f - a.w[v]), (uint32_t)v, 1u};
+            const u128 dv = (u128)__ldcg(a.delta + v);
+            const KeyId c{a.ris ? dv : dv * a.W + (u128)a.T * (one_f - a.w[v]), (uint32_t)v, 1u};
             if (better(c, best)) best = c;
         }
         best = block_best(best, s_part);
@@ -507,8 +511,8 @@ __global__ void __launch_bounds__(kCovThreads) k_greedy_rounds(GreedyArgs a) {
                 a.gs->done = 0;
                 a.seeds[round] = (int32_t)v;
                 a.cov_out[round] = (int64_t)cov;
-                const u128 N = (u128)cov * a.W + (u128)a.T * sum_c;
-                const u128 D = (u128)a.T << a.f;
+                const u128 N = a.ris ? (u128)cov * (uint64_t)a.n : (u128)cov * a.W + (u128)a.T * sum_c;
+                const u128 D = a.ris ? (u128)a.T : (u128)a.T << a.f;
                 a.est_out[round] = u128_to_double(N) / u128_to_double(D);
                 __threadfence();
             }
@@ -637,6 +641,7 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
         ga.seeds = d_seeds;
         ga.cov_out = d_cov;
         ga.est_out = d_est;
+        ga.ris = s->ris;
         void* kargs[] = {&ga};
         CV_CUDA(cudaLaunchCooperativeKernel((const void*)k_greedy_rounds, gblocks, kCovThreads, kargs, 0, st));
         note_launch();

@@ -116,7 +116,7 @@ extern "C" int skis_estimate_noalloc(const skis_sketch* s, int32_t num_queries, 
     k_qmask_set<<<wb, 256, 0, st>>>(seed_offsets, seeds, 0, num_queries, g->n, qmask, status); note_launch();
     k_coverage<<<(unsigned)cb, 256, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, qmask, qcov); note_launch();
     k_estimate<<<wb, 256, 0, st>>>(seed_offsets, seeds, 0, num_queries, g->n, g->w, g->f, g->W, s->T, qcov,
-                                   coverage_out, estimate_out); note_launch();
+                                   coverage_out, estimate_out, s->ris); note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(error_buf, error_len, SKIS_ERR_CUDA, "skis_estimate_noalloc: launch: ", cudaGetErrorString(e));
     DevStatus h;

@@ -52,6 +52,7 @@ struct SampleArgs {
     uint32_t retry_cap;
     uint32_t max_deg;                  // thread tier: longest in-row it expands
     uint32_t max_steps;                // thread tier: edge quads per sample before handing it on
+    int ris;                           // plain RIS: uniform source, one unconditioned round
     // input ids: first_id + t (ids == nullptr) or ids[t], t < count (or
     // t < *count_dev when the list was filled by the previous tier)
     const uint64_t* ids;
@@ -103,6 +104,7 @@ __device__ __forceinline__ uint32_t draw_source(const SampleArgs& a, uint64_t j)
     const uint64_t u1 = (uint64_t)x.x | ((uint64_t)x.y << 32);
     const uint64_t u2 = (uint64_t)x.z | ((uint64_t)x.w << 32);
     const uint64_t col = __umul64hi(u1, a.n);
+    if (a.ris) return (uint32_t)col;  // RIS: the uniform column alone
     const uint64_t y = __umul64hi(u2, a.W);
     const AliasEntry e = a.alias[col];
     return y < e.prob ? (uint32_t)col : e.alias;
@@ -237,9 +239,13 @@ template <class Ins>
 __device__ __forceinline__ uint32_t first_step_warp(const SampleArgs& a, uint64_t j, const RowInfo& rv, Ins& ins,
                                                     bool* failed) {
     const int lane = threadIdx.x & 31;
+    *failed = false;
+    if (a.ris) {  // RIS: round 0, accepted whatever its coins
+        expand_rows(a, j, kDomFirst, 0, rv.off, lane == 0 ? rv.deg : 0u, rv.tau, ins);
+        return 0;
+    }
     const uint64_t q_first = rv.off >> 2;
     const uint32_t nq = (uint32_t)(((rv.off + rv.deg - 1) >> 2) - q_first + 1);
-    *failed = false;
     if (nq > 16) {
         for (uint32_t r = 0;; ++r) {
             if (r >= a.retry_cap) { *failed = true; return r; }
@@ -315,13 +321,6 @@ __global__ void k_sources(SampleArgs a, uint4* __restrict__ rec) {
 }
 
 // ----------------------------------------------------------- thread tier
-// Lane states of the thread tier. A load issued in one iteration is first
-// read in a later one (kStart: the source record; kRowWait: the next row),
-// so a lane that just claimed a sample or popped a vertex never stalls its
-// warp; a row prefetched while the current row is still being expanded lets
-// the lane switch rows without losing an iteration.
-enum : uint32_t { kIdle = 0, kStart = 1, kRun = 2, kRowWait = 3 };
-
 __global__ void __launch_bounds__(kThreadBlock, 5) k_iis_thread(SampleArgs a) {
     __shared__ int32_t s_q[kThreadBlock / 32][kThreadQ][32];
     const int lane = threadIdx.x & 31;
@@ -330,158 +329,139 @@ __global__ void __launch_bounds__(kThreadBlock, 5) k_iis_thread(SampleArgs a) {
     const uint4* __restrict__ tau4 = reinterpret_cast<const uint4*>(a.tau);
     const int4* __restrict__ src4 = reinterpret_cast<const int4*>(a.src);
 
-    // per-lane sample state; edge positions fit 32 bits (m < 2^32 - 8)
-    uint32_t state = kIdle;
-    uint64_t j = 0, coins = 0;
-    uint4 rec = make_uint4(0, 0, 0, 0);
-    uint32_t v = 0, r = 0, len = 0, head = 0, src_deg = 0, tau_row = 0;
-    uint32_t qc = 0, q_first = 0, q_last = 0, lo = 0, hi = 0, steps = 0;
-    bool first = true, any = false, rowleft = false;
-    bool nx = false;  // a row record for member `head` is loaded (or in flight) in nxr
-    RowInfo nxr;
-    nxr.off = 0; nxr.deg = 0; nxr.tau = 0;
+    // per-lane sample state
+    bool busy = false, first = true, any = false, rowleft = false;
+    uint64_t j = 0, qc = 0, q_first = 0, q_last = 0, lo = 0, hi = 0, coins = 0;
+    uint32_t v = 0, r = 0, len = 0, head = 0, src_deg = 0, tau_row = 0, steps = 0;
     bool exhausted = false;                 // warp-uniform: no ids left to claim
     uint64_t chunk_pos = 0, chunk_end = 0;  // this warp's arena reservation
 
     for (;;) {
         // idle lanes claim the next ids together (one atomic per warp)
-        bool claimed_now = false;
-        const unsigned idle = __ballot_sync(kFull, state == kIdle);
+        const unsigned idle = __ballot_sync(kFull, !busy);
         if (idle && !exhausted) {
             const int leader = __ffs(idle) - 1;
             unsigned long long base = 0;
             if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(idle));
             base = __shfl_sync(kFull, base, leader);
             if (base + __popc(idle) >= count) exhausted = true;
-            if (state == kIdle) {
+            if (!busy) {
                 const uint64_t t = base + __popc(idle & lanemask_lt());
                 if (t < count) {
                     j = input_id(a, t);
-                    if (a.srcrec) {
-                        rec = __ldg(a.srcrec + t);  // Alg. 1 line 1, drawn by k_sources
+                    RowInfo rv;
+                    if (a.srcrec) {  // Alg. 1 line 1, drawn by k_sources
+                        const uint4 sr = __ldg(a.srcrec + t);
+                        v = sr.x;
+                        rv.deg = sr.y;
+                        rv.off = sr.z;
+                        rv.tau = sr.w;
                     } else {
-                        const uint32_t sv = draw_source(a, j);
-                        const RowInfo rv = a.rows[sv];
-                        rec = make_uint4(sv, rv.deg, (uint32_t)rv.off, rv.tau);
+                        v = draw_source(a, j);  // Alg. 1 line 1
+                        rv = a.rows[v];
                     }
-                    state = kStart;
-                    claimed_now = true;
+                    if (rv.deg > a.max_deg) {
+                        hand_on(a, j);
+                    } else {
+                        busy = true;
+                        first = true;
+                        any = false;
+                        r = 0;
+                        mq[0][lane] = (int32_t)v;
+                        len = 1;
+                        head = 1;
+                        src_deg = rv.deg;
+                        tau_row = rv.tau;
+                        lo = rv.off;
+                        hi = rv.off + rv.deg;
+                        q_first = lo >> 2;
+                        q_last = hi > lo ? (hi - 1) >> 2 : q_first;
+                        qc = q_first;
+                        rowleft = hi > lo;  // a RIS source may have no in-edges
+                        coins = 0;
+                        steps = 0;
+                    }
                 }
             }
         }
-        if (!__any_sync(kFull, state != kIdle)) {
+        if (!__any_sync(kFull, busy)) {
             if (exhausted) break;
             continue;
         }
 
         bool done = false, handed = false, failed = false;
-        // transitions (register moves; loads consumed here were issued earlier)
-        if (state == kStart && !claimed_now) {
-            v = rec.x;
-            src_deg = rec.y;
-            if (src_deg > a.max_deg) {
-                handed = true;
-            } else {
-                lo = rec.z;
-                hi = rec.z + rec.y;
-                tau_row = rec.w;
-                first = true;
-                any = false;
-                r = 0;
-                mq[0][lane] = (int32_t)v;
-                len = 1;
-                head = 1;
-                nx = false;
-                coins = 0;
-                steps = 0;
-                q_first = lo >> 2;
-                q_last = (hi - 1) >> 2;
-                qc = q_first;
-                rowleft = true;
-                state = kRun;
-            }
-        }
-        if (state == kRun && !rowleft && first) {  // end of a first-step round
-            if (any) {
-                first = false;
-                coins = (uint64_t)src_deg * (r + 1);
-            } else if (++r >= a.retry_cap) {
-                failed = true;
-            } else if (r >= kThreadMaxRetries) {
-                handed = true;  // a rare source: the warp tier searches rounds in parallel
-            } else {
-                qc = q_first;
-                rowleft = true;
-            }
-        }
-        if (state == kRowWait || (state == kRun && !rowleft && !first && !failed && !handed)) {
-            // next row of the reverse BFS (Alg. 1 line 8: pop)
-            if (nx) {
-                ++head;
-                nx = false;
-                state = kRun;
-                coins += nxr.deg;
-                if (nxr.deg > a.max_deg) {
-                    handed = true;
-                } else if (nxr.deg > 0) {
-                    lo = (uint32_t)nxr.off;
-                    hi = lo + nxr.deg;
-                    tau_row = nxr.tau;
-                    q_first = lo >> 2;
-                    q_last = (hi - 1) >> 2;
-                    qc = q_first;
-                    rowleft = true;
-                }
-            } else if (head < len) {
-                nxr = a.rows[mq[head][lane]];
-                nx = true;
-                state = kRowWait;  // read next iteration
-            } else {
-                done = true;
-            }
-        }
-
-        // one edge quad of the current row: coins of lines 4-6 (first step,
-        // round r) or of line 9 (reverse BFS)
-        if (state == kRun && rowleft && !handed && !failed) {
-            const uint4 x = coin_block(a.seed, qc, first ? r : 0u, first ? kDomFirst : kDomBfs, j);
-            const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_row, tau_row, tau_row, tau_row);
-            const uint32_t e0 = qc << 2;
-            uint32_t inrow = 0xFu;
-            if (e0 < lo) inrow &= 0xFu << (lo - e0);
-            if (e0 + 4 > hi) inrow &= 0xFu >> (e0 + 4 - hi);
-            uint32_t live = (coin_live(x.x, t4.x) ? 1u : 0u) | (coin_live(x.y, t4.y) ? 2u : 0u) |
-                            (coin_live(x.z, t4.z) ? 4u : 0u) | (coin_live(x.w, t4.w) ? 8u : 0u);
-            live &= inrow;
-            if (live) {
-                any = true;
-                const int4 s4 = __ldg(src4 + qc);
-                const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
+        if (busy) {
+            // one edge quad of the current row: coins of lines 4-6 (first
+            // step, round r) or of line 9 (reverse BFS)
+            if (rowleft) {
+                const uint4 x = coin_block(a.seed, qc, first ? r : 0u, first ? kDomFirst : kDomBfs, j);
+                const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_row, tau_row, tau_row, tau_row);
+                const uint64_t e0 = qc << 2;
+                unsigned live = 0;
+                live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
+                live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
+                live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
+                live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
+                if (live) {
+                    any = true;
+                    const int4 s4 = __ldg(src4 + qc);
+                    const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (!((live >> k) & 1u) || handed) continue;
-                    const int32_t u = cand[k];
-                    bool seen = false;
-                    for (uint32_t i = 0; i < len; ++i)
-                        if (mq[i][lane] == u) { seen = true; break; }
-                    if (seen) continue;
-                    if (len == (uint32_t)kThreadQ) handed = true;
-                    else mq[len++][lane] = u;
+                    for (int k = 0; k < 4; ++k) {
+                        if (!((live >> k) & 1u) || handed) continue;
+                        const int32_t u = cand[k];
+                        bool seen = false;
+                        for (uint32_t i = 0; i < len; ++i)
+                            if (mq[i][lane] == u) { seen = true; break; }
+                        if (seen) continue;
+                        if (len == (uint32_t)kThreadQ) handed = true;
+                        else mq[len++][lane] = u;
+                    }
+                }
+                ++qc;
+                rowleft = qc <= q_last;
+                // a sample with much work is finished faster by a whole warp
+                if (++steps > a.max_steps) handed = true;
+            }
+            if (!handed && !rowleft) {
+                if (first) {  // end of a first-step round: accept it or redraw
+                    if (any || a.ris) {
+                        first = false;
+                        coins = (uint64_t)src_deg * (r + 1);
+                    } else if (++r >= a.retry_cap) {
+                        failed = true;
+                    } else if (r >= kThreadMaxRetries) {
+                        handed = true;  // a rare source: the warp tier searches rounds in parallel
+                    } else {
+                        qc = q_first;
+                        rowleft = true;
+                    }
+                }
+                if (!first && !failed && !handed) {  // pop the next queued vertex
+                    if (head < len) {
+                        const RowInfo rw = a.rows[mq[head][lane]];
+                        ++head;
+                        coins += rw.deg;
+                        if (rw.deg > a.max_deg) {
+                            handed = true;
+                        } else if (rw.deg > 0) {
+                            lo = rw.off;
+                            hi = rw.off + rw.deg;
+                            tau_row = rw.tau;
+                            q_first = lo >> 2;
+                            q_last = (hi - 1) >> 2;
+                            qc = q_first;
+                            rowleft = true;
+                        }
+                    } else {
+                        done = true;
+                    }
                 }
             }
-            ++qc;
-            rowleft = qc <= q_last;
-            // a sample with much work is finished faster by a whole warp
-            if (++steps > a.max_steps) handed = true;
+            if (handed) hand_on(a, j);
+            if (failed) record_retry_failure(a, j, v, r, src_deg);
+            if (handed || failed) busy = false;
         }
-        // prefetch the row of the next queued vertex while this row runs
-        if (state == kRun && !nx && (any || !first) && head < len && !handed && !failed) {
-            nxr = a.rows[mq[head][lane]];
-            nx = true;
-        }
-        if (handed) hand_on(a, j);
-        if (failed) record_retry_failure(a, j, v, r, src_deg);
-        if (handed || failed) state = kIdle;
 
         // finished samples: one arena reservation for the warp's batch
         const unsigned dm = __ballot_sync(kFull, done);
@@ -520,7 +500,7 @@ __global__ void __launch_bounds__(kThreadBlock, 5) k_iis_thread(SampleArgs a) {
                 } else {
                     arena_overflow(a, j);
                 }
-                state = kIdle;
+                busy = false;
             }
             if (fits) chunk_pos += total;
         }
@@ -672,7 +652,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
             for (;;) {
                 const bool any_w = expand_rows(a, j, kDomFirst, r, a_lo, lane == 0 ? sub_deg : 0u, rv.tau, ins);
                 const int any = __syncthreads_or(any_w ? 1 : 0);
-                if (any) break;
+                if (any || a.ris) break;
                 if (++r >= a.retry_cap) { failed = true; break; }
             }
         }
@@ -830,7 +810,7 @@ static int occupancy_grid(const void* kernel, int threads, int override_blocks, 
 
 int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* err) {
     const skis_graph* g = s->g;
-    if (g->W == 0) {
+    if (g->W == 0 && !s->ris) {
         *err = "skis_sample: Gamma = 0, the graph has no non-singular sample";
         return SKIS_EINVAL;
     }
@@ -857,6 +837,7 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.retry_cap = s->retry_cap;
     base.max_deg = s->thread_max_deg;
     base.max_steps = s->thread_max_steps;
+    base.ris = s->ris;
     base.ids = nullptr;
     base.first_id = s->T;
     base.count = count;
@@ -984,6 +965,7 @@ int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* can
     tmp.g = s->g;
     tmp.seed = s->seed;
     tmp.retry_cap = s->retry_cap;
+    tmp.ris = s->ris;
     tmp.cta_slots = s->cta_slots;
     tmp.warp_blocks = s->warp_blocks;
     tmp.thread_blocks = s->thread_blocks;

@@ -221,7 +221,7 @@ static int launch_batch(skis_server* srv, Slot& sl) {
     SV_CUDA(coverage_by_index(s, sl.d_off, sl.d_seeds, 0, q, 0, (int64_t)used, sl.d_chunk_cnt, sl.d_chunk_off,
                               sl.d_smask, sl.d_qcov, st));
     k_estimate<<<wb, 256, 0, st>>>(sl.d_off, sl.d_seeds, 0, q, g->n, g->w, g->f, g->W, s->T, sl.d_qcov, sl.d_cov,
-                                   sl.d_est); note_launch();
+                                   sl.d_est, s->ris); note_launch();
     SV_CUDA(cudaGetLastError());
     SV_CUDA(cudaMemcpyAsync(sl.h_cov, sl.d_cov, (size_t)q * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     SV_CUDA(cudaMemcpyAsync(sl.h_est, sl.d_est, (size_t)q * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -225,6 +225,7 @@ struct skis_sketch {
     uint32_t* inv = nullptr;             // sample ids, vertex after vertex
     uint64_t inv_T = 0;                  // T when the index was built (0 = none)
     int query_index = 0;                 // 0 auto (use the index if built), 1 always, 2 never
+    int ris = 0;                         // plain RIS samples (uniform source, n Cov / T estimator)
     // query / greedy scratch (allocated on first use)
     uint64_t* smask = nullptr;           // T per-sample query bits (inverted-index path)
     uint64_t smask_cap = 0;
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(256) k_coverage(const uint64_t* __restrict__ h
 __global__ void k_estimate(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
                            int32_t qn, int64_t n, const uint64_t* __restrict__ w, int f, uint64_t W, uint64_t T,
                            const unsigned long long* __restrict__ cov, int64_t* __restrict__ cov_out,
-                           double* __restrict__ est_out);
+                           double* __restrict__ est_out, int ris);
 
 // Builds every device structure of g from device edge arrays. Returns a
 // skis_status code; *err receives a message on failure.

@@ -317,3 +317,37 @@ def test_autotuned_split_gives_the_same_samples(er_small):
     ora = o.sample_ids(seed, np.arange(30_000, dtype=np.uint64))
     assert_samples_equal(dev, ora)
     s.close()
+
+
+@pytest.mark.parametrize("model", ["wc", "p"])
+def test_ris_variant_matches_oracle(model):
+    # plain RIS: uniform sources (isolated and zero-in-degree vertices too),
+    # one unconditioned round, n Cov / T, coverage-only greedy
+    n = 30_000
+    src, dst = synth.chunglu(n - 1000, 200_000, 2.1, 61)  # vertices >= n - 1000 have no edges
+    w = synth.tri(200_000, 61) if model == "p" else None
+    g, o = _pair(n, src, dst, model, w)
+    seed, T = 0x515, 200_000
+    s = skis.skis_sketch_create(g, seed)
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_SAMPLER, 1)
+    skis.skis_sample(s, T)
+    with pytest.raises(skis.SkisError):
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_SAMPLER, 0)  # fixed once samples exist
+    dev = skis.skis_sketch_export(s, 0, T)
+    osk = oracle.OracleSketch(o, seed, T, ris=True)
+    a = osk.arrays()
+    ora = dict(src=a["src"], retries=a["retries"], len=np.diff(a["off"]), coins=a["coins"],
+               member_off=a["off"], members=a["mem"])
+    assert_samples_equal(dev, ora)
+    assert (dev["len"] == 1).any()  # singular samples
+    off, seeds = synth.seed_sets(n, [1, 10, 100] * 30, 62)
+    cov, est = skis.skis_estimate(s, off, seeds)
+    ocov, oest = osk.coverage(off, seeds)
+    assert np.array_equal(cov, ocov)
+    np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
+    sd, sc, se = skis.skis_greedy_maxcover(s, 20)
+    od, oc, oe = osk.greedy(20)
+    assert np.array_equal(sd, od) and np.array_equal(sc, oc)
+    np.testing.assert_allclose(se, oe, rtol=REL, atol=0)
+    s.close()
+    g.close()
