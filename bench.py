@@ -51,6 +51,9 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help=f"{WORKLOAD} (the benchmark line) or rmat-2^25-wc (bounded-sample rates)")
+    ap.add_argument("--samples", type=int, default=200_000, help="samples of the bounded R-MAT run")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step and exit (the command profiled with ncu)")
     return ap.parse_args()
@@ -140,9 +143,9 @@ def _peaks():
 
 
 def _traffic_per_sample():
-    """Measured DRAM bytes per sample of the warp-tier sampler from the
+    """Measured DRAM bytes per sample of the sampling tiers from the
     committed ncu summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "iis_warp_dram.json")
+    path = os.path.join(ROOT, "profiles", "iis_sampler_dram.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
@@ -274,12 +277,77 @@ def serving_benchmark(skis, torch, dev, stream):
     }
 
 
+# ----------------------------------------------------------- R-MAT run
+def rmat_run(args):
+    """The R-MAT workload (2^25 vertices, 2^30 edges, weighted cascade) on a
+    bounded number of samples: weighted cascade on R-MAT reaches its hubs'
+    huge in-rows (about 10^6 coins per sample), so 10^8 samples are about
+    10^14 coin flips; the rates measured here set the time of any count."""
+    import torch
+
+    import paper_1709_03565_gb300 as skis
+    import synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    spec, src, dst, _ = synth.workload("rmat-2^25-wc")
+    t_gen = time.perf_counter() - t0
+    n, m = spec["n"], spec["m"]
+    d_src, d_dst = torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev)
+    del src, dst
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g = skis.skis_load_graph(n, d_src, d_dst, None, skis.SKIS_W_WC, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    load_ms = e0.elapsed_time(e1)
+    del d_src, d_dst
+    torch.cuda.empty_cache()
+    info = skis.skis_graph_get_info(g)
+    s = skis.skis_sketch_create(g, SKETCH_SEED + 3, args.samples * 64, stream=stream)
+    tune = skis.skis_sketch_autotune(s, max(2000, args.samples // 20), stream=stream)
+    skis.skis_sample(s, args.samples, stream=stream)
+    st = skis.skis_sketch_stats(s)
+    e0.record(stream)
+    seeds, cov, est = skis.skis_greedy_maxcover(s, 100, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    greedy_ms = e0.elapsed_time(e1)
+    free1, _ = torch.cuda.mem_get_info(dev)
+    sample_s = st["last_sample_ms"] / 1e3
+    line = {
+        "metric": METRIC, "value": args.samples / sample_s, "unit": "RR sets/s", "n_gpus": 1, "steps": 1,
+        "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "rmat-2^25-wc", "graph": "R-MAT (0.57, 0.19, 0.19, 0.05), weighted cascade",
+                   "n": n, "m": m, "samples": args.samples, "bounded_run": True},
+        "sampled_edges_per_s": st["coins"] / sample_s,
+        "per_sample": {"members": st["entries"] / args.samples, "coins": st["coins"] / args.samples},
+        "seconds_for_1e8_samples": 1e8 / (args.samples / sample_s),
+        "graph_load_ms": load_ms, "generate_s": t_gen, "Gamma": info["Gamma"],
+        "tiers_ms": {"thread": st["last_thread_ms"], "warp": st["last_warp_ms"], "cta": st["last_cta_ms"]},
+        "to_warp_tier": st["to_warp"], "to_cta_tier": st["deferred"], "autotune": tune,
+        "greedy_k100_ms": greedy_ms, "greedy_coverage": int(cov[-1]), "greedy_estimate": float(est[-1]),
+        "device_memory_used_gb": (free0 - free1) / 1e9,
+    }
+    s.close()
+    g.close()
+    print(json.dumps(line))
+
+
 # ----------------------------------------------------------------- ours
 def main():
     args = _args()
     rank, world, local = _dist()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != WORKLOAD:
+        if args.workload != "rmat-2^25-wc":
+            raise SystemExit(f"unknown workload {args.workload}")
+        return rmat_run(args)
 
     import torch
 

@@ -88,18 +88,20 @@ typedef struct skis_stats {
     uint64_t arena_reserved; /* entries reserved so far (>= entries) */
     uint64_t to_warp;        /* samples of the last skis_sample call handed to the warp tier */
     uint64_t deferred;       /* samples of the last skis_sample call that ran on the CTA tier */
-    double last_thread_ms;   /* device time of the last thread-tier sampling launch(es) */
+    double last_thread_ms;   /* device time of the last first-tier sampling launch(es) */
     double last_warp_ms;     /* device time of the last warp-tier sampling launch(es) */
     double last_cta_ms;      /* device time of the last CTA-tier sampling launch(es) */
     double last_sample_ms;   /* device time of all sampling launches of the last skis_sample call */
     uint64_t last_passes;    /* sampling passes of the last call (> 1: the arena grew and reran) */
 } skis_stats;
 
-/* Sampling runs in three tiers chained by sample id: one lane per sample
- * (up to 16 members, in-rows up to THREAD_MAX_DEG edges, up to
- * THREAD_MAX_STEPS edge quads, up to 8 rejected rounds), one warp per
- * sample (up to 256 members), one CTA per sample (any size). Options tune
- * the split; they never change the samples. */
+/* Sampling runs in three tiers chained by sample id: a packed first tier
+ * in which a warp holds 32 samples and shares its lanes among their edge
+ * quads (up to 32 members, in-rows up to THREAD_MAX_DEG edges, up to
+ * THREAD_MAX_STEPS edge quads, up to 8 rejected rounds; the "thread" names
+ * below refer to this tier), one warp per sample (up to 256 members), one
+ * CTA per sample (any size). Options tune the split; they never change the
+ * samples. */
 typedef enum skis_option {
     SKIS_OPT_RETRY_CAP = 0,      /* cap on rejected first-step rounds (default 2^24) */
     SKIS_OPT_CTA_SLOTS = 1,      /* CTAs of the CTA tier (default 2 per SM) */
@@ -183,6 +185,19 @@ int skis_sketch_autotune(skis_sketch *s, uint64_t pilot_samples, uint32_t *chose
  * W = 0 (no non-singular sample exists). Synchronises the stream.
  * next_sample_id_out (nullable) receives the new T. */
 int skis_sample(skis_sketch *s, uint64_t count, uint64_t *next_sample_id_out, void *cuda_stream);
+
+/* Stop-at-size sampling (the experiments' rule, Sec. VI "Algorithms
+ * compared": samples are generated until their total size reaches h n log n,
+ * the target here given in entries). Appends samples T, T+1, ... exactly as
+ * skis_sample does and stops at the first one that brings
+ * sum_{j < T'} |R_j| (over the whole sketch) to target_entries or more, or
+ * after max_count samples. Samples are drawn in batches; those of the last
+ * batch after the stopping one are dropped (the next call regenerates the
+ * same ids). appended_out / next_sample_id_out (nullable) receive the number
+ * appended and the new T. Errors as skis_sample; target_entries = 0 is
+ * SKIS_EINVAL. Synchronises the stream. */
+int skis_sample_to_size(skis_sketch *s, uint64_t target_entries, uint64_t max_count, uint64_t *appended_out,
+                        uint64_t *next_sample_id_out, void *cuda_stream);
 
 /* Influence queries (Alg. 2 line 2, Eq. 21): for each seed set S_b, b <
  * num_queries, given as CSR (seed_offsets int64[q+1], seeds int32[...]):

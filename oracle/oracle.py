@@ -48,6 +48,9 @@ def _lib():
         lib.orc_philox4x32_10.restype = None
         lib.orc_graph_build.argtypes = [i64, i64, P, P, P, ctypes.c_int, u64, ctypes.POINTER(P)]
         lib.orc_graph_build.restype = ctypes.c_int
+        lib.orc_graph_build_model.argtypes = [i64, i64, P, P, P, ctypes.c_int, u64, ctypes.c_int,
+                                              ctypes.POINTER(P)]
+        lib.orc_graph_build_model.restype = ctypes.c_int
         lib.orc_graph_free.argtypes = [P]
         lib.orc_graph_free.restype = None
         lib.orc_graph_scalars.argtypes = [P, P, P, P, P]
@@ -58,6 +61,10 @@ def _lib():
         lib.orc_sample_ids.restype = ctypes.c_int
         lib.orc_sketch_build.argtypes = [P, u64, i64, u32, ctypes.c_int, ctypes.POINTER(P)]
         lib.orc_sketch_build.restype = ctypes.c_int
+        lib.orc_sketch_build_to_size.argtypes = [P, u64, i64, i64, u32, ctypes.c_int, ctypes.POINTER(P)]
+        lib.orc_sketch_build_to_size.restype = ctypes.c_int
+        lib.orc_sketch_count.argtypes = [P]
+        lib.orc_sketch_count.restype = i64
         lib.orc_sketch_free.argtypes = [P]
         lib.orc_sketch_free.restype = None
         lib.orc_sketch_entries.argtypes = [P]
@@ -87,9 +94,10 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 class OracleGraph:
     """G = (V, E, w) with canonical in-CSR, thresholds, fixed-point gamma and
-    the alias table of the source law."""
+    the alias table of the source law; lt=True reads the weights under the
+    Linear Threshold model (gamma_v = the row's weight sum)."""
 
-    def __init__(self, n, src, dst, weights=None, model=W_WC, weight_seed=0):
+    def __init__(self, n, src, dst, weights=None, model=W_WC, weight_seed=0, lt=False):
         src = np.ascontiguousarray(src, dtype=np.int32)
         dst = np.ascontiguousarray(dst, dtype=np.int32)
         m = int(src.shape[0])
@@ -100,8 +108,8 @@ class OracleGraph:
         else:
             weights = None
         h = ctypes.c_void_p()
-        rc = _lib().orc_graph_build(n, m, _p(src), _p(dst), _p(weights), model, weight_seed,
-                                    ctypes.byref(h))
+        rc = _lib().orc_graph_build_model(n, m, _p(src), _p(dst), _p(weights), model, weight_seed,
+                                          1 if lt else 0, ctypes.byref(h))
         if rc != ORC_OK:
             raise OracleError(rc, "orc_graph_build")
         self._h = h
@@ -156,14 +164,21 @@ class OracleSketch:
     """The SKIS sketch R = {R_1..R_T} (sample ids 0..T-1) with Eq. 21 queries
     and Alg. 3 greedy."""
 
-    def __init__(self, graph: OracleGraph, seed: int, T: int, retry_cap: int = 1 << 24, ris: bool = False):
+    def __init__(self, graph: OracleGraph, seed: int, T: int, retry_cap: int = 1 << 24, ris: bool = False,
+                 stop_entries: int = 0):
+        """T samples; with stop_entries > 0, the first samples whose total
+        size reaches stop_entries (T bounds the count)."""
         h = ctypes.c_void_p()
-        rc = _lib().orc_sketch_build(graph._h, seed, T, retry_cap, 1 if ris else 0, ctypes.byref(h))
+        if stop_entries > 0:
+            rc = _lib().orc_sketch_build_to_size(graph._h, seed, stop_entries, T, retry_cap, 1 if ris else 0,
+                                                 ctypes.byref(h))
+        else:
+            rc = _lib().orc_sketch_build(graph._h, seed, T, retry_cap, 1 if ris else 0, ctypes.byref(h))
         if rc != ORC_OK:
             raise OracleError(rc, "orc_sketch_build")
         self._h = h
         self.graph = graph
-        self.T = T
+        self.T = int(_lib().orc_sketch_count(h))
         self.seed = seed
 
     def __del__(self):

@@ -51,6 +51,27 @@
  *      not depend on the order of the queue.
  *   R8 Self-loops are rejected; parallel edges are independent coins.
  *
+ * Variant (graph flag `lt`): the Linear Threshold model (Sec. "Extensions to
+ * other diffusion models"). Thresholds as R1/R2, read as edge weights with
+ * w' = tau / 2^32 (2^32 for the sentinel); every row must satisfy
+ * sum tau' <= 2^32 (the model's sum_u w(u,v) <= 1).
+ *   L1 gamma_v = sum of the row's tau' over 2^32, exactly: w_v = sum tau',
+ *      f = 32, W = sum w_v; the source law and alias table are as R4.
+ *   L2 In a live-edge world of LT each vertex keeps at most one in-edge: the
+ *      edge i of its row (canonical order) with P_{i-1} <= y < P_i, where P
+ *      is the running sum of tau', or none if y >= P_d, for a uniform y.
+ *   L3 An LT IIS sample: source v by Eq. probu with these gamma; the first
+ *      step picks exactly one in-neighbour with probability tau'_i / w_v
+ *      (z = floor(U w_v / 2^64) for the 64-bit word U of step 0, then the
+ *      row position as L2); then the reverse walk of RIS for LT: from the
+ *      last member x, word y of step t picks x's in-edge as L2 (t = 1, 2,
+ *      ...); the walk stops when none is picked or the picked vertex is
+ *      already in R_j. Step t uses the Philox block (q = t, retry 0,
+ *      domain LT = 5, sample j).
+ *   L4 Work counter coins = the sum of d_in over all members (each member's
+ *      row is examined once); retries = 0.
+ *   With `ris`, the source is uniform and step 0 is an ordinary walk step.
+ *
  * Variant (flag `ris`): plain reverse influence sampling (RIS, Borgs et al.;
  * Sec. II-C): the source is uniform (the column draw alone), the source's
  * in-edges get one unconditioned round (FIRST coins, round 0), so a sample
@@ -71,7 +92,7 @@ typedef unsigned __int128 u128;
 #define ORC_SENT 0xFFFFFFFFu
 
 enum { ORC_W_P = 0, ORC_W_TAU = 1, ORC_W_WC = 2, ORC_W_TRI = 3 };
-enum { DOM_SRC = 1, DOM_FIRST = 2, DOM_BFS = 3, DOM_WEIGHT = 4 };
+enum { DOM_SRC = 1, DOM_FIRST = 2, DOM_BFS = 3, DOM_WEIGHT = 4, DOM_LT = 5 };
 
 /* ------------------------------------------------------------ Philox -- */
 
@@ -141,6 +162,7 @@ static uint32_t tau_of_p(double p)
 
 typedef struct orc_graph {
     int64_t n, m;
+    int lt;          /* Linear Threshold model (L1-L4) instead of IC */
     int64_t *off;    /* n+1 row offsets of the in-CSR (rows = destinations) */
     int32_t *src;    /* m sources in CSR order */
     uint32_t *tau;   /* m thresholds in CSR order */
@@ -237,8 +259,8 @@ done:
  * thresholds (R1, R2), gamma in fixed point (R3, Eq. gamma_v) and the alias
  * table of the source law (R4, Eq. probu).
  *   weights: double p[m] (ORC_W_P), uint32 tau[m] (ORC_W_TAU), or NULL. */
-int orc_graph_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
-                    const void *weights, int model, uint64_t weight_seed, orc_graph **out)
+int orc_graph_build_model(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                          const void *weights, int model, uint64_t weight_seed, int lt, orc_graph **out)
 {
     *out = NULL;
     if (n < 1 || n > ((int64_t)1 << 31) || m < 0) return ORC_EINVAL;
@@ -254,7 +276,7 @@ int orc_graph_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst
     }
     orc_graph *g = (orc_graph *)calloc(1, sizeof(orc_graph));
     if (!g) return ORC_ENOMEM;
-    g->n = n; g->m = m;
+    g->n = n; g->m = m; g->lt = lt ? 1 : 0;
     size_t mm = (size_t)(m > 0 ? m : 1);
     g->off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
     g->src = (int32_t *)malloc(mm * sizeof(int32_t));
@@ -296,6 +318,26 @@ int orc_graph_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst
         }
     }
 
+    if (g->lt) {
+        /* L1: gamma_v = sum of the row's weights, exactly; rows above 1 are
+         * not an LT instance */
+        g->s = 0;
+        g->f = 32;
+        g->W = 0;
+        for (int64_t v = 0; v < n; v++) {
+            uint64_t S = 0;
+            for (int64_t e = g->off[v]; e < g->off[v + 1]; e++)
+                S += g->tau[e] == ORC_SENT ? ((uint64_t)1 << 32) : (uint64_t)g->tau[e];
+            if (S > ((uint64_t)1 << 32)) { orc_graph_free(g); return ORC_EINVAL; }
+            g->w[v] = S;
+            g->W += S;
+        }
+        int rc_lt = alias_sweep(g);
+        if (rc_lt != 0) { orc_graph_free(g); return rc_lt == -2 ? ORC_ENOMEM : ORC_EINVAL; }
+        *out = g;
+        return ORC_OK;
+    }
+
     /* gamma in fixed point (R3, Eq. gamma_v) */
     g->s = ceil_log2(n) + 1;
     g->f = 62 - g->s;
@@ -315,6 +357,12 @@ int orc_graph_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst
     if (rc != 0) { orc_graph_free(g); return rc == -2 ? ORC_ENOMEM : ORC_EINVAL; }
     *out = g;
     return ORC_OK;
+}
+
+int orc_graph_build(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                    const void *weights, int model, uint64_t weight_seed, orc_graph **out)
+{
+    return orc_graph_build_model(n, m, src, dst, weights, model, weight_seed, 0, out);
 }
 
 void orc_graph_scalars(const orc_graph *g, int64_t *n, int64_t *m, uint64_t *W, int32_t *f)
@@ -421,6 +469,61 @@ static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t re
     return ORC_OK;
 }
 
+/* L2: the in-edge of row [b, e_end) that a draw y in [0, sum tau') picks:
+ * the first position whose running sum of tau' exceeds y. */
+static int64_t lt_pick(const orc_graph *g, int64_t b, int64_t e_end, uint64_t y)
+{
+    uint64_t P = 0;
+    for (int64_t e = b; e < e_end; e++) {
+        P += g->tau[e] == ORC_SENT ? ((uint64_t)1 << 32) : (uint64_t)g->tau[e];
+        if (P > y) return e;
+    }
+    return -1;
+}
+
+/* One LT IIS sample (L3): the source, its one conditioned in-neighbour, then
+ * the reverse walk until no in-edge is picked or the walk meets R_j again.
+ * With ris: uniform source, and step 0 is an ordinary walk step. */
+static int sample_one_lt(const orc_graph *g, uint64_t seed, uint64_t j, int ris, char *visited,
+                         int32_t *members, int64_t *len_out, int32_t *src_out, uint32_t *retries_out,
+                         uint64_t *coins_out)
+{
+    int64_t v = ris ? draw_source_uniform(g, seed, j) : draw_source(g, seed, j);
+    *src_out = (int32_t)v;
+    *retries_out = 0;
+    int64_t len = 0;
+    visited[v] = 1;
+    members[len++] = (int32_t)v;
+    uint64_t coins = 0;
+    int64_t x = v;
+    for (uint64_t t = 0;; t++) {
+        int64_t b = g->off[x], e_end = g->off[x + 1];
+        coins += (uint64_t)(e_end - b);
+        if (e_end == b) break;
+        uint32_t blk[4];
+        philox_block(seed, t, 0, DOM_LT, j, blk);
+        uint64_t S = g->w[x];
+        uint64_t y;
+        if (t == 0 && !ris) {  /* Pr[u] = w(u, v) / gamma_v */
+            uint64_t U = (uint64_t)blk[0] | ((uint64_t)blk[1] << 32);
+            y = (uint64_t)(((u128)U * (u128)S) >> 64);
+        } else {
+            y = blk[0];
+            if (y >= S) break;  /* no in-edge kept: the walk ends */
+        }
+        int64_t e = lt_pick(g, b, e_end, y);
+        int32_t u = g->src[e];
+        if (visited[u]) break;  /* the walk closes on R_j */
+        visited[u] = 1;
+        members[len++] = u;
+        x = u;
+    }
+    for (int64_t i = 0; i < len; i++) visited[members[i]] = 0;
+    *len_out = len;
+    *coins_out = coins;
+    return ORC_OK;
+}
+
 /* Samples for an explicit list of sample ids. Per sample: src, retries, len,
  * coins, status; members are concatenated (insertion order) into members_out,
  * whose capacity is members_cap; *members_used receives the total. Returns
@@ -438,8 +541,12 @@ int orc_sample_ids(const orc_graph *g, uint64_t seed, const uint64_t *ids, int64
     int rc = ORC_OK;
     for (int64_t t = 0; t < count; t++) {
         int64_t len;
-        status_out[t] = sample_one(g, seed, ids[t], retry_cap, ris, visited, buf, &len, &src_out[t],
-                                   &retries_out[t], &coins_out[t]);
+        if (g->lt)
+            status_out[t] = sample_one_lt(g, seed, ids[t], ris, visited, buf, &len, &src_out[t],
+                                          &retries_out[t], &coins_out[t]);
+        else
+            status_out[t] = sample_one(g, seed, ids[t], retry_cap, ris, visited, buf, &len, &src_out[t],
+                                       &retries_out[t], &coins_out[t]);
         len_out[t] = len;
         if (used + len > members_cap) { rc = ORC_ENOMEM; break; }
         memcpy(members_out + used, buf, (size_t)len * sizeof(int32_t));
@@ -472,8 +579,12 @@ void orc_sketch_free(orc_sketch *s)
     free(s);
 }
 
-int orc_sketch_build(const orc_graph *g, uint64_t seed, int64_t T, uint32_t retry_cap, int ris,
-                     orc_sketch **out)
+/* Samples j = 0, 1, ... up to T; with stop_entries > 0, the sketch ends at
+ * the first sample that brings the total size sum_j |R_j| to stop_entries
+ * or more (the stop-at-size rule of the experiments, Sec. VI "Algorithms
+ * compared": sample until the total size reaches a target), T bounding it. */
+static int sketch_build(const orc_graph *g, uint64_t seed, int64_t T, int64_t stop_entries,
+                        uint32_t retry_cap, int ris, orc_sketch **out)
 {
     *out = NULL;
     if (T < 1 || (g->W == 0 && !ris)) return ORC_EINVAL;
@@ -494,8 +605,10 @@ int orc_sketch_build(const orc_graph *g, uint64_t seed, int64_t T, uint32_t retr
     s->off[0] = 0;
     for (int64_t j = 0; j < T; j++) {
         int64_t len;
-        int rc = sample_one(g, seed, (uint64_t)j, retry_cap, ris, visited, buf, &len, &s->src[j],
-                            &s->retries[j], &s->coins[j]);
+        int rc = g->lt ? sample_one_lt(g, seed, (uint64_t)j, ris, visited, buf, &len, &s->src[j],
+                                       &s->retries[j], &s->coins[j])
+                       : sample_one(g, seed, (uint64_t)j, retry_cap, ris, visited, buf, &len, &s->src[j],
+                                    &s->retries[j], &s->coins[j]);
         if (rc != ORC_OK) { free(visited); free(buf); orc_sketch_free(s); return rc; }
         if (s->off[j] + len > cap) {
             while (s->off[j] + len > cap) cap *= 2;
@@ -505,11 +618,32 @@ int orc_sketch_build(const orc_graph *g, uint64_t seed, int64_t T, uint32_t retr
         }
         memcpy(s->mem + s->off[j], buf, (size_t)len * sizeof(int32_t));
         s->off[j + 1] = s->off[j] + len;
+        if (stop_entries > 0 && s->off[j + 1] >= stop_entries) {
+            s->T = j + 1;
+            break;
+        }
     }
     free(visited); free(buf);
     *out = s;
     return ORC_OK;
 }
+
+int orc_sketch_build(const orc_graph *g, uint64_t seed, int64_t T, uint32_t retry_cap, int ris,
+                     orc_sketch **out)
+{
+    return sketch_build(g, seed, T, 0, retry_cap, ris, out);
+}
+
+/* Stop-at-size sketch: samples until sum_j |R_j| >= target_entries (at most
+ * T_max samples); the sample count is orc_sketch_count. */
+int orc_sketch_build_to_size(const orc_graph *g, uint64_t seed, int64_t target_entries, int64_t T_max,
+                             uint32_t retry_cap, int ris, orc_sketch **out)
+{
+    if (target_entries < 1) return ORC_EINVAL;
+    return sketch_build(g, seed, T_max, target_entries, retry_cap, ris, out);
+}
+
+int64_t orc_sketch_count(const orc_sketch *s) { return s->T; }
 
 int64_t orc_sketch_entries(const orc_sketch *s) { return s->off[s->T]; }
 

@@ -65,6 +65,7 @@ _SIGNATURES = [
     ("skis_sketch_set_option", _INT, [_P, _INT, _U64]),
     ("skis_sketch_autotune", _INT, [_P, _U64, _P, _P, _P, _I32, _P, _P]),
     ("skis_sample", _INT, [_P, _U64, _P, _P]),
+    ("skis_sample_to_size", _INT, [_P, _U64, _U64, _P, _P, _P]),
     ("skis_estimate", _INT, [_P, _I32, _P, _P, _P, _P, _INT, _P]),
     ("skis_greedy_maxcover", _INT, [_P, _I32, _P, _P, _P, _P]),
     ("skis_sketch_stats", _INT, [_P, _P]),
@@ -249,6 +250,15 @@ def skis_sample(s: Sketch, count: int, stream=None) -> int:
     nxt = ctypes.c_uint64()
     _check(lib().skis_sample(s.ptr, int(count), ctypes.byref(nxt), _stream(stream)))
     return nxt.value
+
+
+def skis_sample_to_size(s: Sketch, target_entries: int, max_count: int = 1 << 40, stream=None):
+    """Append samples until their total size reaches target_entries; returns
+    (samples appended, new T)."""
+    app, nxt = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().skis_sample_to_size(s.ptr, int(target_entries), int(max_count), ctypes.byref(app),
+                                     ctypes.byref(nxt), _stream(stream)))
+    return app.value, nxt.value
 
 
 def skis_estimate(s: Sketch, seed_offsets, seeds, coverage_out=None, estimate_out=None, stream=None):

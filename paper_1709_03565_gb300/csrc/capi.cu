@@ -230,6 +230,24 @@ extern "C" int skis_sample(skis_sketch* s, uint64_t count, uint64_t* next_sample
     API_CATCH
 }
 
+extern "C" int skis_sample_to_size(skis_sketch* s, uint64_t target_entries, uint64_t max_count,
+                                   uint64_t* appended_out, uint64_t* next_sample_id_out, void* cuda_stream) {
+    API_TRY
+    if (!s) return fail(SKIS_EINVAL, "skis_sample_to_size: NULL sketch");
+    if (target_entries < 1) return fail(SKIS_EINVAL, "skis_sample_to_size: target_entries must be >= 1");
+    if (max_count > (1ull << 40)) return fail(SKIS_EINVAL, "skis_sample_to_size: max_count too large");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s->stream = st;
+    std::string err;
+    uint64_t appended = 0;
+    const int rc = sketch_sample_to_size(s, target_entries, max_count, st, &appended, &err);
+    if (appended_out) *appended_out = appended;
+    if (next_sample_id_out) *next_sample_id_out = s->T;
+    if (rc != SKIS_OK) return fail(rc, err);
+    return SKIS_OK;
+    API_CATCH
+}
+
 extern "C" int skis_sketch_autotune(skis_sketch* s, uint64_t pilot_samples, uint32_t* chosen_max_deg,
                                     uint32_t* chosen_max_steps, double* candidate_ms, int32_t candidate_cap,
                                     int32_t* candidates_out, void* cuda_stream) {

@@ -108,7 +108,19 @@ __global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __rest
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const RowInfo r = rows[v];
         uint64_t Q = one62;
-        for (uint32_t k = 0; k < r.deg && Q != 0; ++k) {
+        uint32_t k = 0;
+        // thresholds are loaded 8 at a time ahead of the (sequential) product
+        for (; k + 8 <= r.deg && Q != 0; k += 8) {
+            uint32_t t[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) t[i] = csr_tau ? csr_tau[r.off + k + i] : r.tau;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (t[i] == kSentinel) Q = 0;
+                else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t[i])) >> 32);
+            }
+        }
+        for (; k < r.deg && Q != 0; ++k) {
             const uint32_t t = csr_tau ? csr_tau[r.off + k] : r.tau;
             if (t == kSentinel) Q = 0;
             else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t)) >> 32);

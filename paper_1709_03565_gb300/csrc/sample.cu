@@ -1,15 +1,14 @@
 // Importance Influence Sampling (Sec. III, Alg. 1) on the device, in three
 // tiers chained by sample id.
 //
-// Thread tier: one lane per sample. Lanes are persistent: a lane that
-// finishes claims the next id while its neighbours carry on, so a warp keeps
-// 32 independent samples in flight and one warp instruction advances 32 of
-// them by one edge quad (one Philox block = the 4 coins of a quad). The member
-// list (which is also Alg. 1's FIFO queue Q = members[head .. len)) holds up to
-// 16 vertices per lane in shared memory, laid out so that entry k of lane l is
-// word 32 k + l (no bank conflicts whatever k each lane uses). A sample whose
-// member list outgrows it, or that meets an in-row longer than the degree
-// threshold, is handed by id to the warp tier.
+// Packed tier (first): a warp holds 32 samples, one per lane, and each step
+// spreads the edge quads still to be drawn in their current rows over its
+// 32 lanes (one Philox block = the 4 coins of a quad), so the lanes draw
+// coins together whatever the mix of row lengths. Member lists (which are
+// also Alg. 1's FIFO queues Q = members[head .. len)) hold up to 32 vertices
+// per sample in shared memory. A sample whose list outgrows it, that meets an
+// in-row longer than the degree threshold or that uses up its step budget is
+// handed by id to the warp tier.
 //
 // Warp tier: one warp per sample. The member list (256 entries) and an
 // open-addressing hash set (the visited set R_j) live in shared memory. Edges
@@ -36,11 +35,13 @@ constexpr int kHCap = 512;         // warp-tier hash slots (load <= 1/2 + one in
 constexpr int kHashBits = 9;
 constexpr int kIdBatch = 16;       // sample ids taken per work-cursor atomic
 constexpr uint32_t kArenaChunk = 2048;        // entries reserved per arena atomic (warp tier)
-constexpr uint32_t kThreadArenaChunk = 512;   // entries reserved per arena atomic (thread tier)
+constexpr uint32_t kPackArenaChunk = 512;     // entries reserved per arena atomic (packed tier)
 constexpr int kCtaThreads = 512;
-constexpr int kThreadQ = 16;       // thread-tier member capacity per lane
-constexpr uint32_t kThreadMaxRetries = 8;  // rejected rounds before the warp tier takes over
-constexpr int kThreadBlock = 256;
+constexpr int kCtaWin = 2 * kCtaThreads;  // queued vertices per load-balanced CTA-tier window
+constexpr int kPackQ = 32;                 // packed-tier member capacity per sample
+constexpr int kPackStride = kPackQ + 1;    // shared-memory row stride of a slot's member list
+constexpr uint32_t kPackMaxRetries = 8;    // rejected rounds before the warp tier takes over
+constexpr int kPackBlock = 256;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 struct SampleArgs {
@@ -320,153 +321,161 @@ __global__ void k_sources(SampleArgs a, uint4* __restrict__ rec) {
     }
 }
 
-// ----------------------------------------------------------- thread tier
-__global__ void __launch_bounds__(kThreadBlock, 5) k_iis_thread(SampleArgs a) {
-    __shared__ int32_t s_q[kThreadBlock / 32][kThreadQ][32];
+// ----------------------------------------------------------- packed tier
+// A warp holds 32 samples, one slot per lane (the slot's state lives in its
+// lane's registers). Each step the edge quads still to be drawn in the slots'
+// current rows are laid end to end and the warp's 32 lanes take the first 32:
+// lane i works on the quad at position i (slot found by a binary search over
+// the slots' inclusive prefix of remaining quads), so every lane draws a
+// Philox block whenever the warp holds that much work. Live coins then join
+// their sample's member list one at a time in lane order, which is the
+// sample's own edge order, with the visited check done by all lanes against
+// up to 32 members at once.
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
+    const uint32_t lo = __shfl_sync(kFull, (uint32_t)v, src);
+    const uint32_t hi = __shfl_sync(kFull, (uint32_t)(v >> 32), src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__global__ void __launch_bounds__(kPackBlock, 4) k_iis_pack(SampleArgs a) {
+    // member k of slot s at mq[s * kPackStride + k]: a row stride of 33 words
+    // keeps both "one slot, all members" and "all slots, one member each"
+    // accesses free of bank conflicts
+    __shared__ int32_t s_q[kPackBlock / 32][32 * kPackStride];
+    __shared__ uint32_t s_len[kPackBlock / 32][32];
     const int lane = threadIdx.x & 31;
-    int32_t(*const mq)[32] = s_q[threadIdx.x >> 5];  // mq[k][lane]: member k of this lane's sample
+    int32_t* const mq = s_q[threadIdx.x >> 5];
+    uint32_t* const mlen = s_len[threadIdx.x >> 5];
+    int32_t* const mine = mq + lane * kPackStride;
     const uint64_t count = input_count(a);
     const uint4* __restrict__ tau4 = reinterpret_cast<const uint4*>(a.tau);
     const int4* __restrict__ src4 = reinterpret_cast<const int4*>(a.src);
 
-    // per-lane sample state
-    bool busy = false, first = true, any = false, rowleft = false;
-    uint64_t j = 0, qc = 0, q_first = 0, q_last = 0, lo = 0, hi = 0, coins = 0;
-    uint32_t v = 0, r = 0, len = 0, head = 0, src_deg = 0, tau_row = 0, steps = 0;
+    // state of this lane's slot; rows are [lo, hi) in edge positions (the
+    // graph holds fewer than 2^32 - 8 edges), qn the next quad to hand out
+    bool busy = false, first = false, any = false;
+    uint64_t j = 0, coins = 0;
+    uint32_t v = 0, r = 0, head = 0, src_deg = 0, tau_row = 0, steps = 0;
+    uint32_t lo = 0, hi = 0, qn = 0;
+    bool pf_ok = false;                     // the row of the next pop, loaded ahead
+    uint32_t pf_off = 0, pf_deg = 0, pf_tau = 0;
     bool exhausted = false;                 // warp-uniform: no ids left to claim
+    uint64_t pool_base = 0;                 // warp-uniform input pool [pool_base, + pool_n)
+    uint32_t pool_n = 0, pool_used = 0;
+    uint4 rec = make_uint4(0, 0, 0, 0);     // source record of pool entry `lane`
     uint64_t chunk_pos = 0, chunk_end = 0;  // this warp's arena reservation
 
     for (;;) {
-        // idle lanes claim the next ids together (one atomic per warp)
-        const unsigned idle = __ballot_sync(kFull, !busy);
-        if (idle && !exhausted) {
-            const int leader = __ffs(idle) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(idle));
-            base = __shfl_sync(kFull, base, leader);
-            if (base + __popc(idle) >= count) exhausted = true;
-            if (!busy) {
-                const uint64_t t = base + __popc(idle & lanemask_lt());
-                if (t < count) {
-                    j = input_id(a, t);
-                    RowInfo rv;
-                    if (a.srcrec) {  // Alg. 1 line 1, drawn by k_sources
-                        const uint4 sr = __ldg(a.srcrec + t);
-                        v = sr.x;
-                        rv.deg = sr.y;
-                        rv.off = sr.z;
-                        rv.tau = sr.w;
-                    } else {
-                        v = draw_source(a, j);  // Alg. 1 line 1
-                        rv = a.rows[v];
-                    }
-                    if (rv.deg > a.max_deg) {
-                        hand_on(a, j);
-                    } else {
-                        busy = true;
-                        first = true;
-                        any = false;
-                        r = 0;
-                        mq[0][lane] = (int32_t)v;
-                        len = 1;
-                        head = 1;
-                        src_deg = rv.deg;
-                        tau_row = rv.tau;
-                        lo = rv.off;
-                        hi = rv.off + rv.deg;
-                        q_first = lo >> 2;
-                        q_last = hi > lo ? (hi - 1) >> 2 : q_first;
-                        qc = q_first;
-                        rowleft = hi > lo;  // a RIS source may have no in-edges
-                        coins = 0;
-                        steps = 0;
-                    }
+        __syncwarp();  // the previous step's shared-memory reads are done before slots are reused
+        // (1) idle slots take the next inputs from the warp's pool of 32,
+        // whose source records (k_sources) lane i holds for pool entry i;
+        // the pool is refilled with one atomic per 32 inputs
+        unsigned idle = __ballot_sync(kFull, !busy);
+        while (idle && !exhausted) {
+            if (pool_used == pool_n) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.work, 32ull);
+                base = __shfl_sync(kFull, base, 0);
+                if (base >= count) {
+                    exhausted = true;
+                    break;
+                }
+                pool_base = base;
+                pool_n = (uint32_t)min(32ull, count - base);
+                pool_used = 0;
+                if ((uint32_t)lane < pool_n) rec = __ldg(a.srcrec + base + lane);
+            }
+            const uint32_t take = min((uint32_t)__popc(idle), pool_n - pool_used);
+            const uint32_t rank = __popc(idle & lanemask_lt());
+            const int from = (int)min(pool_used + rank, 31u);
+            const uint32_t rv_src = __shfl_sync(kFull, rec.x, from);
+            const uint32_t rv_deg = __shfl_sync(kFull, rec.y, from);
+            const uint32_t rv_off = __shfl_sync(kFull, rec.z, from);
+            const uint32_t rv_tau = __shfl_sync(kFull, rec.w, from);
+            if (!busy && rank < take) {
+                j = input_id(a, pool_base + pool_used + rank);
+                v = rv_src;  // Alg. 1 line 1, drawn by k_sources
+                if (rv_deg > a.max_deg) {
+                    hand_on(a, j);
+                } else {
+                    busy = true;
+                    first = true;
+                    any = false;
+                    pf_ok = false;
+                    r = 0;
+                    mine[0] = (int32_t)v;
+                    mlen[lane] = 1;
+                    head = 1;
+                    src_deg = rv_deg;
+                    tau_row = rv_tau;
+                    lo = rv_off;
+                    hi = lo + rv_deg;  // a RIS source may have no in-edges
+                    qn = lo >> 2;
+                    coins = 0;
+                    steps = 0;
                 }
             }
+            pool_used += take;
+            idle = __ballot_sync(kFull, !busy);
         }
         if (!__any_sync(kFull, busy)) {
             if (exhausted) break;
             continue;
         }
+        __syncwarp();
 
+        // (2) slots whose current row is used up: the end of a first-step
+        // round (Alg. 1 lines 2-6: accept it or redraw), or the next pop of
+        // the reverse BFS (lines 7-8)
         bool done = false, handed = false, failed = false;
-        if (busy) {
-            // one edge quad of the current row: coins of lines 4-6 (first
-            // step, round r) or of line 9 (reverse BFS)
-            if (rowleft) {
-                const uint4 x = coin_block(a.seed, qc, first ? r : 0u, first ? kDomFirst : kDomBfs, j);
-                const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_row, tau_row, tau_row, tau_row);
-                const uint64_t e0 = qc << 2;
-                unsigned live = 0;
-                live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
-                live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
-                live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
-                live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
-                if (live) {
-                    any = true;
-                    const int4 s4 = __ldg(src4 + qc);
-                    const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (!((live >> k) & 1u) || handed) continue;
-                        const int32_t u = cand[k];
-                        bool seen = false;
-                        for (uint32_t i = 0; i < len; ++i)
-                            if (mq[i][lane] == u) { seen = true; break; }
-                        if (seen) continue;
-                        if (len == (uint32_t)kThreadQ) handed = true;
-                        else mq[len++][lane] = u;
-                    }
-                }
-                ++qc;
-                rowleft = qc <= q_last;
-                // a sample with much work is finished faster by a whole warp
-                if (++steps > a.max_steps) handed = true;
-            }
-            if (!handed && !rowleft) {
-                if (first) {  // end of a first-step round: accept it or redraw
-                    if (any || a.ris) {
-                        first = false;
-                        coins = (uint64_t)src_deg * (r + 1);
-                    } else if (++r >= a.retry_cap) {
-                        failed = true;
-                    } else if (r >= kThreadMaxRetries) {
-                        handed = true;  // a rare source: the warp tier searches rounds in parallel
-                    } else {
-                        qc = q_first;
-                        rowleft = true;
-                    }
-                }
-                if (!first && !failed && !handed) {  // pop the next queued vertex
-                    if (head < len) {
-                        const RowInfo rw = a.rows[mq[head][lane]];
-                        ++head;
-                        coins += rw.deg;
-                        if (rw.deg > a.max_deg) {
-                            handed = true;
-                        } else if (rw.deg > 0) {
-                            lo = rw.off;
-                            hi = rw.off + rw.deg;
-                            tau_row = rw.tau;
-                            q_first = lo >> 2;
-                            q_last = (hi - 1) >> 2;
-                            qc = q_first;
-                            rowleft = true;
-                        }
-                    } else {
-                        done = true;
-                    }
+        if (busy && (hi <= lo || qn > ((hi - 1) >> 2))) {
+            if (first) {
+                if (any || a.ris) {
+                    first = false;
+                    coins = (uint64_t)src_deg * (r + 1);
+                } else if (++r >= a.retry_cap) {
+                    failed = true;
+                } else if (r >= kPackMaxRetries) {
+                    handed = true;  // a rare source: the warp tier searches rounds in parallel
+                } else {
+                    qn = lo >> 2;
                 }
             }
-            if (handed) hand_on(a, j);
-            if (failed) record_retry_failure(a, j, v, r, src_deg);
-            if (handed || failed) busy = false;
+            if (!first && !failed && !handed) {
+                if (head < mlen[lane]) {
+                    if (!pf_ok) {
+                        const RowInfo rw = a.rows[mine[head]];
+                        pf_off = (uint32_t)rw.off;
+                        pf_deg = rw.deg;
+                        pf_tau = rw.tau;
+                    }
+                    pf_ok = false;
+                    ++head;
+                    coins += pf_deg;
+                    if (pf_deg > a.max_deg) {
+                        handed = true;
+                    } else {
+                        lo = pf_off;
+                        hi = pf_off + pf_deg;
+                        tau_row = pf_tau;
+                        qn = lo >> 2;
+                    }
+                } else {
+                    done = true;
+                }
+            }
         }
+        // a sample with much work is finished faster by a whole warp
+        if (busy && !done && steps > a.max_steps) handed = true;
+        if (handed) hand_on(a, j);
+        if (failed) record_retry_failure(a, j, v, r, src_deg);
+        if (handed || failed) busy = false;
 
-        // finished samples: one arena reservation for the warp's batch
-        const unsigned dm = __ballot_sync(kFull, done);
+        // (3) finished samples: one arena reservation for the warp's batch;
+        // each list is copied by the whole warp (coalesced)
+        unsigned dm = __ballot_sync(kFull, done);
         if (dm) {
-            const uint32_t mylen = done ? len : 0u;
+            const uint32_t mylen = done ? mlen[lane] : 0u;
             uint32_t incl = mylen;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -476,7 +485,7 @@ __global__ void __launch_bounds__(kThreadBlock, 5) k_iis_thread(SampleArgs a) {
             const uint32_t total = __shfl_sync(kFull, incl, 31);
             bool fits = true;
             if (chunk_end - chunk_pos < total) {
-                const uint64_t size = max((uint64_t)kThreadArenaChunk, (uint64_t)total);
+                const uint64_t size = max((uint64_t)kPackArenaChunk, (uint64_t)total);
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(a.arena_cursor, (unsigned long long)size);
                 base = __shfl_sync(kFull, base, 0);
@@ -488,12 +497,11 @@ __global__ void __launch_bounds__(kThreadBlock, 5) k_iis_thread(SampleArgs a) {
                     chunk_end = base + size;
                 }
             }
+            const uint64_t at = chunk_pos + (incl - mylen);
             if (done) {
                 if (fits) {
-                    const uint64_t at = chunk_pos + (incl - mylen);
-                    for (uint32_t i = 0; i < len; ++i) a.arena[at + i] = mq[i][lane];
                     a.h_off[j] = at;
-                    a.h_len[j] = len;
+                    a.h_len[j] = mylen;
                     a.h_src[j] = v;
                     a.h_retries[j] = r;
                     a.h_coins[j] = coins;
@@ -502,7 +510,111 @@ __global__ void __launch_bounds__(kThreadBlock, 5) k_iis_thread(SampleArgs a) {
                 }
                 busy = false;
             }
-            if (fits) chunk_pos += total;
+            if (fits) {
+                while (dm) {
+                    const int sl = __ffs(dm) - 1;
+                    dm &= dm - 1;
+                    const uint64_t at_s = shfl_u64(at, sl);
+                    const uint32_t len_s = mlen[sl];
+                    for (uint32_t k = lane; k < len_s; k += 32) a.arena[at_s + k] = mq[sl * kPackStride + k];
+                }
+                chunk_pos += total;
+            }
+        }
+
+        // (4) hand out the slots' remaining quads to the lanes
+        const uint32_t rem = (busy && hi > lo && qn <= ((hi - 1) >> 2)) ? ((hi - 1) >> 2) - qn + 1 : 0u;
+        uint32_t incl = rem;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        int sl = 0;  // the slot of this lane's quad: the number of slots with incl <= lane
+#pragma unroll
+        for (int b = 16; b; b >>= 1) {
+            const uint32_t x = __shfl_sync(kFull, incl, sl + b - 1);
+            if (x <= (uint32_t)lane) sl += b;
+        }
+        const uint32_t excl_s = __shfl_sync(kFull, incl - rem, sl);
+        const uint32_t qc = __shfl_sync(kFull, qn, sl) + ((uint32_t)lane - excl_s);
+        const uint32_t lo_s = __shfl_sync(kFull, lo, sl);
+        const uint32_t hi_s = __shfl_sync(kFull, hi, sl);
+        const uint32_t tau_s = __shfl_sync(kFull, tau_row, sl);
+        const uint32_t round_s = __shfl_sync(kFull, first ? r : kEmpty, sl);  // kEmpty: BFS coins
+        const uint64_t j_s = shfl_u64(j, sl);
+        // (5) each slot advances past the quads it was given; a BFS slot
+        // whose row is now fully handed out loads the row of its next pop
+        // ahead, while the coins of this step are drawn
+        if (rem) {
+            const uint32_t excl = incl - rem;
+            const uint32_t taken = excl >= 32u ? 0u : min(rem, 32u - excl);
+            qn += taken;
+            steps += taken;
+            if (!first && !pf_ok && qn > ((hi - 1) >> 2) && head < mlen[lane]) {
+                const RowInfo rw = a.rows[mine[head]];
+                pf_off = (uint32_t)rw.off;
+                pf_deg = rw.deg;
+                pf_tau = rw.tau;
+                pf_ok = true;
+            }
+        }
+        unsigned live = 0;
+        int4 s4 = make_int4(0, 0, 0, 0);
+        if ((uint32_t)lane < total) {
+            // one edge quad: coins of lines 4-6 (first step, round r) or of
+            // line 9 (reverse BFS); its sources are loaded with its
+            // thresholds rather than after the coins
+            const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_s, tau_s, tau_s, tau_s);
+            s4 = __ldg(src4 + qc);
+            const bool fs = round_s != kEmpty;
+            const uint4 x = coin_block(a.seed, qc, fs ? round_s : 0u, fs ? kDomFirst : kDomBfs, j_s);
+            const uint32_t e0 = qc << 2;
+            live |= (e0 + 0 >= lo_s && e0 + 0 < hi_s && coin_live(x.x, t4.x)) ? 1u : 0u;
+            live |= (e0 + 1 >= lo_s && e0 + 1 < hi_s && coin_live(x.y, t4.y)) ? 2u : 0u;
+            live |= (e0 + 2 >= lo_s && e0 + 2 < hi_s && coin_live(x.z, t4.z)) ? 4u : 0u;
+            live |= (e0 + 3 >= lo_s && e0 + 3 < hi_s && coin_live(x.w, t4.w)) ? 8u : 0u;
+        }
+
+        // (6) live coins join their samples in lane order (Alg. 1 lines 5
+        // and 10-11; an in-neighbour already in R_j is skipped)
+        unsigned lm = __ballot_sync(kFull, live != 0);
+        unsigned hit = 0, over = 0;
+        while (lm) {
+            const int L = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int sL = __shfl_sync(kFull, sl, L);
+            unsigned bits = __shfl_sync(kFull, live, L);
+            const int32_t c0 = __shfl_sync(kFull, s4.x, L);
+            const int32_t c1 = __shfl_sync(kFull, s4.y, L);
+            const int32_t c2 = __shfl_sync(kFull, s4.z, L);
+            const int32_t c3 = __shfl_sync(kFull, s4.w, L);
+            hit |= 1u << sL;
+            int32_t* const q = mq + sL * kPackStride;
+            while (bits && !((over >> sL) & 1u)) {
+                const int k = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int32_t u = k == 0 ? c0 : k == 1 ? c1 : k == 2 ? c2 : c3;
+                const uint32_t len = mlen[sL];
+                const bool seen = (uint32_t)lane < len && q[lane] == u;
+                if (__ballot_sync(kFull, seen)) continue;
+                if (len == (uint32_t)kPackQ) {
+                    over |= 1u << sL;  // outgrew the list: the warp tier takes it
+                } else {
+                    if (lane == 0) {
+                        q[len] = u;
+                        mlen[sL] = len + 1;
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        any = any || ((hit >> lane) & 1u);
+        if (busy && ((over >> lane) & 1u)) {
+            hand_on(a, j);
+            busy = false;
         }
     }
 }
@@ -599,8 +711,11 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
     __shared__ unsigned long long s_coins;
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_r, s_failed;
+    __shared__ uint32_t s_pre[kCtaWin], s_lo[kCtaWin], s_hi[kCtaWin], s_tau[kCtaWin];
+    __shared__ uint32_t s_wsum[kCtaThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int kWarps = kCtaThreads / 32;
+    static_assert(kCtaWin == 2 * kCtaThreads, "two window rows per thread");
     uint32_t* bitmap = a.bitmaps + (uint64_t)blockIdx.x * a.bitmap_words;
     int32_t* queue = a.queues + (uint64_t)blockIdx.x * a.n;
     const uint64_t count = input_count(a);
@@ -665,8 +780,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
             continue;
         }
 
-        // reverse BFS, level by level: the window [head, tail) is split over
-        // the warps, 32 vertices per warp step
+        // reverse BFS, level by level. A level [head, tail) is taken in
+        // windows of up to kCtaWin queued vertices; the edge quads of a
+        // window's rows are laid end to end and dealt to the warps 32 at a
+        // time, so one long in-row (a hub) is shared by every warp.
         uint64_t coins = 0;
         uint32_t head = 1;
         for (;;) {
@@ -674,13 +791,83 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
             const uint32_t tail = s_qlen;
             __syncthreads();
             if (head >= tail) break;
-            for (uint32_t base = head + 32u * wid; base < tail; base += 32u * kWarps) {
-                const uint32_t idx = base + lane;
-                RowInfo rw;
-                rw.off = 0; rw.deg = 0; rw.tau = 0;
-                if (idx < tail) rw = a.rows[queue[idx]];
-                coins += rw.deg;
-                expand_rows(a, j, kDomBfs, 0, rw.off, rw.deg, rw.tau, ins);
+            for (uint32_t w0 = head; w0 < tail; w0 += kCtaWin) {
+                const uint32_t nw = min((uint32_t)kCtaWin, tail - w0);
+                uint32_t nq2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t i = 2u * threadIdx.x + h;
+                    nq2[h] = 0;
+                    if (i < nw) {
+                        const RowInfo rw = a.rows[queue[w0 + i]];
+                        coins += rw.deg;
+                        const uint32_t lo = (uint32_t)rw.off, hi = lo + rw.deg;
+                        s_lo[i] = lo;
+                        s_hi[i] = hi;
+                        s_tau[i] = rw.tau;
+                        nq2[h] = rw.deg ? ((hi - 1) >> 2) - (lo >> 2) + 1 : 0u;
+                    }
+                }
+                // block-wide inclusive prefix of the quad counts
+                const uint32_t pair = nq2[0] + nq2[1];
+                uint32_t x = pair;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, x, d);
+                    if (lane >= d) x += y;
+                }
+                if (lane == 31) s_wsum[wid] = x;
+                __syncthreads();
+                if (wid == 0) {
+                    uint32_t w = lane < kWarps ? s_wsum[lane] : 0u;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t y = __shfl_up_sync(kFull, w, d);
+                        if (lane >= d) w += y;
+                    }
+                    if (lane < kWarps) s_wsum[lane] = w;
+                }
+                __syncthreads();
+                const uint32_t before = (wid ? s_wsum[wid - 1] : 0u) + x - pair;
+                if (2u * threadIdx.x < nw) s_pre[2u * threadIdx.x] = before + nq2[0];
+                if (2u * threadIdx.x + 1 < nw) s_pre[2u * threadIdx.x + 1] = before + pair;
+                __syncthreads();
+                const uint32_t total = s_pre[nw - 1];
+                for (uint32_t c = wid; c * 32u < total; c += kWarps) {
+                    const uint32_t g = c * 32u + lane;
+                    int32_t c0 = -1, c1 = -1, c2 = -1, c3 = -1;
+                    if (g < total) {
+                        uint32_t i = 0;  // the row of quad g: entries with prefix <= g
+#pragma unroll
+                        for (uint32_t b = kCtaWin / 2; b; b >>= 1)
+                            if (i + b - 1 < nw && s_pre[i + b - 1] <= g) i += b;
+                        const uint32_t lo = s_lo[i], hi = s_hi[i], tr = s_tau[i];
+                        const uint32_t q = (lo >> 2) + (g - (i ? s_pre[i - 1] : 0u));
+                        const uint4 xq = coin_block(a.seed, q, 0, kDomBfs, j);
+                        const uint4 t4 = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q)
+                                               : make_uint4(tr, tr, tr, tr);
+                        const uint32_t e0 = q << 2;
+                        unsigned live = 0;
+                        live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(xq.x, t4.x)) ? 1u : 0u;
+                        live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(xq.y, t4.y)) ? 2u : 0u;
+                        live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(xq.z, t4.z)) ? 4u : 0u;
+                        live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(xq.w, t4.w)) ? 8u : 0u;
+                        if (live) {
+                            const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
+                            if (live & 1u) c0 = s4.x;
+                            if (live & 2u) c1 = s4.y;
+                            if (live & 4u) c2 = s4.z;
+                            if (live & 8u) c3 = s4.w;
+                        }
+                    }
+                    if (__any_sync(kFull, (c0 >= 0) | (c1 >= 0) | (c2 >= 0) | (c3 >= 0))) {
+                        if (__any_sync(kFull, c0 >= 0)) ins.insert(c0);
+                        if (__any_sync(kFull, c1 >= 0)) ins.insert(c1);
+                        if (__any_sync(kFull, c2 >= 0)) ins.insert(c2);
+                        if (__any_sync(kFull, c3 >= 0)) ins.insert(c3);
+                    }
+                }
+                __syncthreads();  // the window's shared arrays are reused
             }
             head = tail;
         }
@@ -819,8 +1006,8 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     if (rc != SKIS_OK) return rc;
     const bool thread_tier = s->thread_max_deg > 0;
     int thread_blocks = 0, warp_blocks = 0;
-    rc = occupancy_grid((const void*)k_iis_thread, kThreadBlock, s->thread_blocks,
-                        (count + kThreadBlock - 1) / kThreadBlock, err, &thread_blocks);
+    rc = occupancy_grid((const void*)k_iis_pack, kPackBlock, s->thread_blocks,
+                        (count + kPackBlock - 1) / kPackBlock, err, &thread_blocks);
     if (rc != SKIS_OK) return rc;
     rc = occupancy_grid((const void*)k_iis_warp, kWarpThreads, s->warp_blocks,
                         thread_tier ? UINT64_MAX : (count + kIdBatch - 1) / kIdBatch, err, &warp_blocks);
@@ -895,7 +1082,7 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
             k_sources<<<(int)std::max<uint64_t>(1, std::min<uint64_t>((in_count + 255) / 256, (uint64_t)sm_count() * 16)),
                         256, 0, st>>>(at, s->srcrec); note_launch();
             at.srcrec = s->srcrec;
-            k_iis_thread<<<thread_blocks, kThreadBlock, 0, st>>>(at); note_launch();
+            k_iis_pack<<<thread_blocks, kPackBlock, 0, st>>>(at); note_launch();
             SK_CUDA(cudaGetLastError());
         }
         SK_CUDA(cudaEventRecord(s->ev[1], st));
@@ -924,7 +1111,7 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
         // completed sample, all of which lie below the old capacity) and
         // rerun exactly the samples that failed
         const uint64_t old_cap = s->arena_cap;
-        const uint64_t new_cap = old_cap * 2 + (uint64_t)kThreadArenaChunk * thread_blocks * (kThreadBlock / 32) +
+        const uint64_t new_cap = old_cap * 2 + (uint64_t)kPackArenaChunk * thread_blocks * (kPackBlock / 32) +
                                  (uint64_t)kArenaChunk * warp_blocks * (kWarpThreads / 32);
         rc = [&]() -> int {
             SK_CUDA(grow_copy(&s->arena, old_cap, new_cap, st));
@@ -949,6 +1136,71 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
         *err = "skis_sample: a conditioned first step reached the retry cap (" + std::to_string(s->retry_cap) +
                " rounds) at sample id " + std::to_string(hst.first_bad) + "; failed samples are empty";
         return SKIS_ERR_RETRY_LIMIT;
+    }
+    return SKIS_OK;
+}
+
+// The one batch sample whose inclusive prefix of sizes first reaches need:
+// pre is the exclusive scan with the total appended, so the index i with
+// pre[i] < need <= pre[i + 1] is unique when pre[count] >= need.
+__global__ void k_first_reach(const uint64_t* __restrict__ pre, uint64_t count, uint64_t need,
+                              unsigned long long* __restrict__ out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+        if (pre[i] < need && pre[i + 1] >= need) *out = i;
+}
+
+int sketch_sample_to_size(skis_sketch* s, uint64_t target, uint64_t max_count, cudaStream_t st, uint64_t* appended,
+                          std::string* err) {
+    *appended = 0;
+    uint64_t cur = 0;  // sum of |R_j| over the samples already in the sketch
+    if (s->T > 0) {
+        uint64_t* pre = nullptr;
+        SK_CUDA(dev_alloc_t(&pre, (size_t)s->T + 1, st));
+        SK_CUDA(scan_u32_to_u64(s->h_len, pre, (int64_t)s->T, st));
+        SK_CUDA(cudaMemcpyAsync(&cur, pre + s->T, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        SK_CUDA(cudaStreamSynchronize(st));
+        dev_free(pre, st);
+    }
+    while (cur < target && *appended < max_count) {
+        const uint64_t need = target - cur;
+        // batch: the expected count to reach the target at the sizes seen
+        // so far, plus 5 %, within [2^16, what is left of max_count]
+        uint64_t batch = 1u << 16;
+        if (s->T > 0 && cur > 0) {
+            const double mean = (double)cur / (double)s->T;
+            batch = std::max<uint64_t>(batch, (uint64_t)((double)need / mean * 1.05) + 1024);
+        }
+        batch = std::min<uint64_t>(batch, max_count - *appended);
+        const uint64_t T0 = s->T;
+        int rc = sketch_sample(s, batch, st, err);
+        if (rc != SKIS_OK) return rc;
+        uint64_t* pre = nullptr;
+        unsigned long long* d_at = nullptr;
+        SK_CUDA(dev_alloc_t(&pre, (size_t)batch + 1, st));
+        SK_CUDA(dev_alloc_t(&d_at, 1, st));
+        SK_CUDA(scan_u32_to_u64(s->h_len + T0, pre, (int64_t)batch, st));
+        SK_CUDA(cudaMemsetAsync(d_at, 0xFF, sizeof(unsigned long long), st));
+        k_first_reach<<<(int)std::max<uint64_t>(1, std::min<uint64_t>((batch + 255) / 256, (uint64_t)sm_count() * 8)), 256, 0,
+                        st>>>(pre, batch, need, d_at); note_launch();
+        SK_CUDA(cudaGetLastError());
+        uint64_t tot = 0;
+        unsigned long long at = 0;
+        SK_CUDA(cudaMemcpyAsync(&tot, pre + batch, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        SK_CUDA(cudaMemcpyAsync(&at, d_at, sizeof(at), cudaMemcpyDeviceToHost, st));
+        SK_CUDA(cudaStreamSynchronize(st));
+        if (tot >= need) {
+            uint64_t upto = 0;  // sizes of batch samples 0 .. at
+            SK_CUDA(cudaMemcpyAsync(&upto, pre + at + 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+            SK_CUDA(cudaStreamSynchronize(st));
+            s->T = T0 + at + 1;  // later samples of the batch are dropped
+            *appended += at + 1;
+            cur += upto;
+        } else {
+            *appended += batch;
+            cur += tot;
+        }
+        dev_free(pre, st);
+        dev_free(d_at, st);
     }
     return SKIS_OK;
 }

@@ -237,6 +237,8 @@ struct skis_sketch {
 
 namespace skis {
 int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* err);
+int sketch_sample_to_size(skis_sketch* s, uint64_t target, uint64_t max_count, cudaStream_t st, uint64_t* appended,
+                          std::string* err);
 int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds, const int64_t* h_off,
                     int64_t* d_cov, double* d_est, cudaStream_t st, std::string* err);
 int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, double* h_est, cudaStream_t st,

@@ -93,3 +93,75 @@ def iis_law(n, src, dst, probs, w, W):
                 continue
             out[(v, R)] = Fraction(int(w[v]), int(W)) * pr / gam[v]
     return out
+
+
+# ------------------------------------------------------ Linear Threshold --
+def lt_worlds(n, dst, probs):
+    """Live-edge worlds of the Linear Threshold model (Kempe et al.): every
+    vertex keeps at most one in-edge, edge e with probability w_e and none
+    with probability 1 - sum of its row. Yields (kept edge per vertex or
+    None, probability)."""
+    import itertools
+
+    options = []
+    for v in range(n):
+        row = [e for e in range(len(dst)) if dst[e] == v]
+        rest = 1 - sum((probs[e] for e in row), Fraction(0))
+        assert rest >= 0, "row weights above 1"
+        options.append([(e, probs[e]) for e in row] + [(None, rest)])
+    for combo in itertools.product(*options):
+        pr = Fraction(1)
+        for _, p in combo:
+            pr *= p
+        if pr:
+            yield tuple(c for c, _ in combo), pr
+
+
+def _lt_rr(src, kept, v):
+    """Vertices that reach v in an LT world: the chain of kept in-edges back
+    from v (each vertex keeps at most one), up to a repeat."""
+    R = [v]
+    x = v
+    while kept[x] is not None:
+        u = src[kept[x]]
+        if u in R:
+            break
+        R.append(u)
+        x = u
+    return frozenset(R)
+
+
+def lt_rr_law(n, src, dst, probs):
+    """{v: {R: Pr[the LT reverse-reachable set of v is R]}}."""
+    law = {v: {} for v in range(n)}
+    for kept, pr in lt_worlds(n, dst, probs):
+        for v in range(n):
+            R = _lt_rr(src, kept, v)
+            law[v][R] = law[v].get(R, Fraction(0)) + pr
+    return law
+
+
+def lt_iis_law(n, src, dst, probs, w, W):
+    """Law of an LT importance sample: source v with probability w_v / W, then
+    the reverse-reachable set of v conditioned on v keeping an in-edge
+    (gamma_v = its row's weight sum): {(v, R): probability}."""
+    law = {}
+    gam = [sum((probs[e] for e in range(len(dst)) if dst[e] == v), Fraction(0)) for v in range(n)]
+    rr = lt_rr_law(n, src, dst, probs)
+    for v in range(n):
+        if w[v] == 0:
+            continue
+        for R, pr in rr[v].items():
+            if len(R) >= 2:
+                law[(v, R)] = Fraction(int(w[v]), int(W)) * pr / gam[v]
+    return law
+
+
+def lt_influence(n, src, dst, probs, S) -> Fraction:
+    """I(S) under LT: expected number of vertices whose reverse-reachable set
+    meets S."""
+    S = set(S)
+    tot = Fraction(0)
+    for kept, pr in lt_worlds(n, dst, probs):
+        tot += pr * sum(1 for x in range(n) if _lt_rr(src, kept, x) & S)
+    return tot

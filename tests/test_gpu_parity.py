@@ -351,3 +351,35 @@ def test_ris_variant_matches_oracle(model):
     np.testing.assert_allclose(se, oe, rtol=REL, atol=0)
     s.close()
     g.close()
+
+
+def test_stop_at_size_matches_oracle(er_small):
+    # sample until the total size reaches h n ln n (h = 1 here): the same
+    # sample count and samples as the oracle's sequential stop rule
+    spec, src, dst, g, o, osk, seed, T = er_small
+    n = spec["n"]
+    target = int(1.0 * n * np.log(n))
+    s = skis.skis_sketch_create(g, seed)
+    appended, T1 = skis.skis_sample_to_size(s, target)
+    ref = oracle.OracleSketch(o, seed, 10 * target, stop_entries=target)
+    assert appended == T1 == ref.T
+    st = skis.skis_sketch_stats(s)
+    a = ref.arrays()
+    assert st["entries"] == int(a["off"][-1]) >= target > int(a["off"][-2])
+    dev = skis.skis_sketch_export(s, 0, T1)
+    ora = dict(src=a["src"], retries=a["retries"], len=np.diff(a["off"]), coins=a["coins"],
+               member_off=a["off"], members=a["mem"])
+    assert_samples_equal(dev, ora)
+    off, seeds = synth.seed_sets(n, [10] * 20, 71)
+    cov, est = skis.skis_estimate(s, off, seeds)
+    ocov, oest = ref.coverage(off, seeds)
+    assert np.array_equal(cov, ocov)
+    np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
+    # a larger target continues from the truncated sketch with the same ids
+    appended2, T2 = skis.skis_sample_to_size(s, 2 * target)
+    ref2 = oracle.OracleSketch(o, seed, 10 * target, stop_entries=2 * target)
+    assert T2 == ref2.T and appended2 == T2 - T1
+    # a reached target appends nothing; max_count bounds a call
+    assert skis.skis_sample_to_size(s, target) == (0, T2)
+    assert skis.skis_sample_to_size(s, 100 * target, max_count=1000) == (1000, T2 + 1000)
+    s.close()
