@@ -71,12 +71,17 @@ typedef enum skis_weight_model {
 
 typedef enum skis_mem_space { SKIS_MEM_HOST = 0, SKIS_MEM_DEVICE = 1 } skis_mem_space;
 
+/* Diffusion model of a loaded graph. */
+typedef enum skis_diffusion { SKIS_DIFF_IC = 0, SKIS_DIFF_LT = 1 } skis_diffusion;
+
 typedef struct skis_graph_info {
     int64_t n, m;
     uint64_t W;        /* Gamma in fixed point: Gamma~ = W / 2^f */
-    int32_t f;         /* fractional bits: gamma~_v = w_v / 2^f, f = 61 - ceil(log2 n) */
+    int32_t f;         /* fractional bits: gamma~_v = w_v / 2^f, f = 61 - ceil(log2 n) (IC), 32 (LT) */
     int32_t row_uniform_tau; /* 1 when every in-row has one threshold (WC) */
     double Gamma;      /* W / 2^f as binary64 (informational) */
+    int32_t diffusion; /* skis_diffusion */
+    int32_t reserved;
 } skis_graph_info;
 
 typedef struct skis_stats {
@@ -113,11 +118,23 @@ typedef enum skis_option {
                                     1 = build it if needed and walk it; 2 = always scan */
     SKIS_OPT_THREAD_MAX_STEPS = 6, /* edge quads a sample may take in the thread tier before the warp
                                       tier takes it over (default 256) */
-    SKIS_OPT_SAMPLER = 7          /* 0 = IIS samples (Alg. 1, default); 1 = plain RIS samples (Sec. II-C,
+    SKIS_OPT_SAMPLER = 7,         /* 0 = IIS samples (Alg. 1, default); 1 = plain RIS samples (Sec. II-C,
                                      Borgs et al.): uniform source (the column draw alone), one
                                      unconditioned round of the source's in-edges (singular samples
                                      occur), estimator n Cov / T (Lemma 1), greedy key Delta alone.
                                      Set before the first skis_sample. */
+    SKIS_OPT_THREAD_MAX_RETRIES = 8, /* rejected first-step rounds a sample may take in the thread tier
+                                        before the warp tier (rounds searched in parallel) takes it
+                                        over (default 32) */
+    SKIS_OPT_FIRST_STEP = 9        /* 0 = conditioned first step by rejection (default); 1 = bucket form
+                                      (Eq. probn, no retries): the bucket of the source's row, "in-edges
+                                      before i dead, edge i live", is drawn with mass Q_{i-1} - Q_i of the
+                                      fixed-point gamma chain (total 2^62 - Q_d) by z = floor(U (2^62 -
+                                      Q_d) / 2^64), U the 64-bit word of the Philox block (q 0, retry 0,
+                                      domain BUCKET = 6, sample j); the first e with 2^62 - Q_e > z is
+                                      live and the in-edges after it get their FIRST coins of round 0.
+                                      IC graphs, IIS sampler; set before the first skis_sample; builds
+                                      the graph's per-edge chain (8 bytes an edge) on first use. */
 } skis_option;
 
 /* Load G = (V, E, w) (Sec. II-A) and build the device structures every later
@@ -137,6 +154,21 @@ typedef enum skis_option {
 int skis_load_graph(skis_graph **out, int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                     const void *weights, int weight_model, uint64_t weight_seed, int mem_space,
                     void *cuda_stream);
+
+/* Load G under the Linear Threshold model (Sec. "Extensions to other
+ * diffusion models", LT): the same inputs, CSR and thresholds as
+ * skis_load_graph, read as edge weights w = tau / 2^32 (1 for the sentinel),
+ * and
+ *   - gamma_v = sum over in-edges of w(u,v), exactly: w_v = the row's sum of
+ *     tau' (tau' = tau, 2^32 for the sentinel), f = 32;
+ *   - the alias table of Pr[src = v] = w_v / W as above.
+ * Every in-row must satisfy sum tau' <= 2^32 (the model's sum of in-weights
+ * at most 1): otherwise SKIS_EINVAL naming the first such vertex; other
+ * errors as skis_load_graph. Sketches of this graph draw LT samples (see
+ * skis_sample); queries, greedy and the server are unchanged. */
+int skis_load_graph_lt(skis_graph **out, int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                       const void *weights, int weight_model, uint64_t weight_seed, int mem_space,
+                       void *cuda_stream);
 
 int skis_graph_get_info(const skis_graph *g, skis_graph_info *info);
 
@@ -160,8 +192,8 @@ int skis_sketch_set_option(skis_sketch *s, int option, uint64_t value);
 
 /* Autotuner of the sampling tiers: times pilot sampling of ids
  * [0, pilot_samples) on a scratch sketch under each candidate split
- * (SKIS_OPT_THREAD_MAX_DEG in {0, 32, 64, 128, 256, 1024} x
- * SKIS_OPT_THREAD_MAX_STEPS in {64, 128, 256}), keeps the fastest on s and
+ * (SKIS_OPT_THREAD_MAX_DEG in {0, 64, 128, 256, 512, 1024} x
+ * SKIS_OPT_THREAD_MAX_STEPS in {128, 256, 1024}), keeps the fastest on s and
  * reports it (outputs nullable; candidate_ms receives up to candidate_cap
  * pilot times in that order, candidates_out their number). The pilot samples
  * are discarded; the samples of s never depend on the split. */

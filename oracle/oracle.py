@@ -79,6 +79,11 @@ def _lib():
     return _handle
 
 
+def _flags(ris: bool, bucket: bool) -> int:
+    """Sampler flags: 1 = plain RIS, 2 = bucket first step."""
+    return (1 if ris else 0) | (2 if bucket else 0)
+
+
 def _p(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
@@ -134,7 +139,7 @@ class OracleGraph:
                                 _p(a["w"]), _p(a["prob"]), _p(a["alias"]))
         return a
 
-    def sample_ids(self, seed, ids, retry_cap=1 << 24, members_cap=None, ris=False):
+    def sample_ids(self, seed, ids, retry_cap=1 << 24, members_cap=None, ris=False, bucket=False):
         """Samples for explicit ids: dict of per-sample arrays plus the
         concatenated members (insertion order) and their offsets."""
         ids = np.ascontiguousarray(ids, dtype=np.uint64)
@@ -146,7 +151,7 @@ class OracleGraph:
                        status=np.empty(c, np.int32))
             mem = np.empty(cap, np.int32)
             used = ctypes.c_int64()
-            rc = _lib().orc_sample_ids(self._h, seed, _p(ids), c, retry_cap, 1 if ris else 0, _p(out["src"]),
+            rc = _lib().orc_sample_ids(self._h, seed, _p(ids), c, retry_cap, _flags(ris, bucket), _p(out["src"]),
                                        _p(out["retries"]), _p(out["len"]), _p(out["coins"]),
                                        _p(out["status"]), _p(mem), cap, ctypes.byref(used))
             if rc == ORC_ENOMEM and members_cap is None:
@@ -165,15 +170,15 @@ class OracleSketch:
     and Alg. 3 greedy."""
 
     def __init__(self, graph: OracleGraph, seed: int, T: int, retry_cap: int = 1 << 24, ris: bool = False,
-                 stop_entries: int = 0):
+                 stop_entries: int = 0, bucket: bool = False):
         """T samples; with stop_entries > 0, the first samples whose total
         size reaches stop_entries (T bounds the count)."""
         h = ctypes.c_void_p()
         if stop_entries > 0:
-            rc = _lib().orc_sketch_build_to_size(graph._h, seed, stop_entries, T, retry_cap, 1 if ris else 0,
+            rc = _lib().orc_sketch_build_to_size(graph._h, seed, stop_entries, T, retry_cap, _flags(ris, bucket),
                                                  ctypes.byref(h))
         else:
-            rc = _lib().orc_sketch_build(graph._h, seed, T, retry_cap, 1 if ris else 0, ctypes.byref(h))
+            rc = _lib().orc_sketch_build(graph._h, seed, T, retry_cap, _flags(ris, bucket), ctypes.byref(h))
         if rc != ORC_OK:
             raise OracleError(rc, "orc_sketch_build")
         self._h = h

@@ -72,6 +72,17 @@
  *      row is examined once); retries = 0.
  *   With `ris`, the source is uniform and step 0 is an ordinary walk step.
  *
+ * Variant (flag ORC_F_BUCKET): the first step of Alg. 1 in its bucket form
+ * (Eq. probn) instead of rejection (R5):
+ *   B1 bucket i of the source's row (canonical order) is "in-edges before i
+ *      dead, edge i live"; its mass is Q_{i-1} - Q_i in the fixed-point
+ *      chain of R3 (Q_0 = 2^62), which is w_i prod_{t<i} (1 - w_t) 2^62 up to
+ *      the chain's floors, of total 2^62 - Q_d. z = floor(U (2^62 - Q_d) /
+ *      2^64) for the 64-bit word U of the Philox block (q = 0, retry 0,
+ *      domain BUCKET = 6, sample j) picks the first i with 2^62 - Q_i > z;
+ *      u_i joins R_j and the in-edges after i get their FIRST coins of round
+ *      0; retries = 0.
+ *
  * Variant (flag `ris`): plain reverse influence sampling (RIS, Borgs et al.;
  * Sec. II-C): the source is uniform (the column draw alone), the source's
  * in-edges get one unconditioned round (FIRST coins, round 0), so a sample
@@ -92,7 +103,8 @@ typedef unsigned __int128 u128;
 #define ORC_SENT 0xFFFFFFFFu
 
 enum { ORC_W_P = 0, ORC_W_TAU = 1, ORC_W_WC = 2, ORC_W_TRI = 3 };
-enum { DOM_SRC = 1, DOM_FIRST = 2, DOM_BFS = 3, DOM_WEIGHT = 4, DOM_LT = 5 };
+enum { DOM_SRC = 1, DOM_FIRST = 2, DOM_BFS = 3, DOM_WEIGHT = 4, DOM_LT = 5, DOM_BUCKET = 6 };
+enum { ORC_F_RIS = 1, ORC_F_BUCKET = 2 };  /* sampler flags */
 
 /* ------------------------------------------------------------ Philox -- */
 
@@ -411,10 +423,35 @@ static int64_t draw_source_uniform(const orc_graph *g, uint64_t seed, uint64_t j
     return (int64_t)(((u128)u1 * (u128)(uint64_t)g->n) >> 64);
 }
 
-static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t retry_cap, int ris,
+/* B1: the bucket (in-edge position in [b, e_end)) of the source's row. */
+static int64_t bucket_pick(const orc_graph *g, uint64_t seed, uint64_t j, int64_t b, int64_t e_end)
+{
+    const uint64_t one62 = (uint64_t)1 << 62;
+    uint64_t Q = one62;
+    for (int64_t e = b; e < e_end; e++) {
+        if (g->tau[e] == ORC_SENT) Q = 0;
+        else Q = (uint64_t)(((u128)Q * (u128)(((uint64_t)1 << 32) - g->tau[e])) >> 32);
+    }
+    uint64_t G = one62 - Q;
+    uint32_t x[4];
+    philox_block(seed, 0, 0, DOM_BUCKET, j, x);
+    uint64_t U = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+    uint64_t z = (uint64_t)(((u128)U * (u128)G) >> 64);
+    Q = one62;
+    for (int64_t e = b; e < e_end; e++) {
+        if (g->tau[e] == ORC_SENT) Q = 0;
+        else Q = (uint64_t)(((u128)Q * (u128)(((uint64_t)1 << 32) - g->tau[e])) >> 32);
+        if (one62 - Q > z) return e;
+    }
+    return e_end - 1; /* not reached: z < G = 2^62 - Q_d */
+}
+
+static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t retry_cap, int flags,
                       char *visited, int32_t *members, int64_t *len_out, int32_t *src_out,
                       uint32_t *retries_out, uint64_t *coins_out)
 {
+    const int ris = flags & ORC_F_RIS;
+    const int bucket = (flags & ORC_F_BUCKET) && !ris;
     /* line 1: the source, Eq. probu (RIS: uniform) */
     int64_t v = ris ? draw_source_uniform(g, seed, j) : draw_source(g, seed, j);
     int64_t b = g->off[v], e_end = g->off[v + 1];
@@ -423,8 +460,10 @@ static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t re
     /* lines 2-6 in rejection form (R5): round r flips every in-edge of v
      * (RIS: round 0 only, accepted whatever its coins) */
     uint32_t r = 0;
+    int64_t picked = -1; /* B1: the bucket's live in-edge */
+    if (bucket) picked = bucket_pick(g, seed, j, b, e_end);
     for (;; r++) {
-        if (ris) break;
+        if (ris || bucket) break;
         if (r >= retry_cap) {
             *retries_out = r;
             *len_out = 0;
@@ -443,8 +482,8 @@ static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t re
     int64_t len = 0;
     visited[v] = 1;
     members[len++] = (int32_t)v;
-    for (int64_t e = b; e < e_end; e++) {
-        if (!is_live(coin_word(seed, DOM_FIRST, r, j, (uint64_t)e), g->tau[e])) continue;
+    for (int64_t e = (bucket ? picked : b); e < e_end; e++) {
+        if (e != picked && !is_live(coin_word(seed, DOM_FIRST, r, j, (uint64_t)e), g->tau[e])) continue;
         int32_t u = g->src[e];
         if (!visited[u]) { visited[u] = 1; members[len++] = u; }
     }
@@ -529,10 +568,11 @@ static int sample_one_lt(const orc_graph *g, uint64_t seed, uint64_t j, int ris,
  * whose capacity is members_cap; *members_used receives the total. Returns
  * ORC_OK, or ORC_ENOMEM if members_cap is too small (outputs then partial). */
 int orc_sample_ids(const orc_graph *g, uint64_t seed, const uint64_t *ids, int64_t count,
-                   uint32_t retry_cap, int ris, int32_t *src_out, uint32_t *retries_out,
+                   uint32_t retry_cap, int flags, int32_t *src_out, uint32_t *retries_out,
                    int64_t *len_out, uint64_t *coins_out, int32_t *status_out, int32_t *members_out,
                    int64_t members_cap, int64_t *members_used)
 {
+    const int ris = flags & ORC_F_RIS;
     if (g->W == 0 && !ris) return ORC_EINVAL;
     char *visited = (char *)calloc((size_t)g->n, 1);
     int32_t *buf = (int32_t *)malloc((size_t)g->n * sizeof(int32_t));
@@ -545,7 +585,7 @@ int orc_sample_ids(const orc_graph *g, uint64_t seed, const uint64_t *ids, int64
             status_out[t] = sample_one_lt(g, seed, ids[t], ris, visited, buf, &len, &src_out[t],
                                           &retries_out[t], &coins_out[t]);
         else
-            status_out[t] = sample_one(g, seed, ids[t], retry_cap, ris, visited, buf, &len, &src_out[t],
+            status_out[t] = sample_one(g, seed, ids[t], retry_cap, flags, visited, buf, &len, &src_out[t],
                                        &retries_out[t], &coins_out[t]);
         len_out[t] = len;
         if (used + len > members_cap) { rc = ORC_ENOMEM; break; }
@@ -584,8 +624,9 @@ void orc_sketch_free(orc_sketch *s)
  * or more (the stop-at-size rule of the experiments, Sec. VI "Algorithms
  * compared": sample until the total size reaches a target), T bounding it. */
 static int sketch_build(const orc_graph *g, uint64_t seed, int64_t T, int64_t stop_entries,
-                        uint32_t retry_cap, int ris, orc_sketch **out)
+                        uint32_t retry_cap, int flags, orc_sketch **out)
 {
+    const int ris = flags & ORC_F_RIS;
     *out = NULL;
     if (T < 1 || (g->W == 0 && !ris)) return ORC_EINVAL;
     orc_sketch *s = (orc_sketch *)calloc(1, sizeof(orc_sketch));
@@ -607,7 +648,7 @@ static int sketch_build(const orc_graph *g, uint64_t seed, int64_t T, int64_t st
         int64_t len;
         int rc = g->lt ? sample_one_lt(g, seed, (uint64_t)j, ris, visited, buf, &len, &s->src[j],
                                        &s->retries[j], &s->coins[j])
-                       : sample_one(g, seed, (uint64_t)j, retry_cap, ris, visited, buf, &len, &s->src[j],
+                       : sample_one(g, seed, (uint64_t)j, retry_cap, flags, visited, buf, &len, &s->src[j],
                                     &s->retries[j], &s->coins[j]);
         if (rc != ORC_OK) { free(visited); free(buf); orc_sketch_free(s); return rc; }
         if (s->off[j] + len > cap) {
@@ -628,19 +669,19 @@ static int sketch_build(const orc_graph *g, uint64_t seed, int64_t T, int64_t st
     return ORC_OK;
 }
 
-int orc_sketch_build(const orc_graph *g, uint64_t seed, int64_t T, uint32_t retry_cap, int ris,
+int orc_sketch_build(const orc_graph *g, uint64_t seed, int64_t T, uint32_t retry_cap, int flags,
                      orc_sketch **out)
 {
-    return sketch_build(g, seed, T, 0, retry_cap, ris, out);
+    return sketch_build(g, seed, T, 0, retry_cap, flags, out);
 }
 
 /* Stop-at-size sketch: samples until sum_j |R_j| >= target_entries (at most
  * T_max samples); the sample count is orc_sketch_count. */
 int orc_sketch_build_to_size(const orc_graph *g, uint64_t seed, int64_t target_entries, int64_t T_max,
-                             uint32_t retry_cap, int ris, orc_sketch **out)
+                             uint32_t retry_cap, int flags, orc_sketch **out)
 {
     if (target_entries < 1) return ORC_EINVAL;
-    return sketch_build(g, seed, T_max, target_entries, retry_cap, ris, out);
+    return sketch_build(g, seed, T_max, target_entries, retry_cap, flags, out);
 }
 
 int64_t orc_sketch_count(const orc_sketch *s) { return s->T; }

@@ -19,7 +19,8 @@ SKIS_W_EXPLICIT_P, SKIS_W_EXPLICIT_TAU, SKIS_W_WC, SKIS_W_TRI = 0, 1, 2, 3
 SKIS_MEM_HOST, SKIS_MEM_DEVICE = 0, 1
 SKIS_OPT_RETRY_CAP, SKIS_OPT_CTA_SLOTS, SKIS_OPT_WARP_BLOCKS = 0, 1, 2
 SKIS_OPT_THREAD_MAX_DEG, SKIS_OPT_THREAD_BLOCKS, SKIS_OPT_QUERY_INDEX, SKIS_OPT_THREAD_MAX_STEPS = 3, 4, 5, 6
-SKIS_OPT_SAMPLER = 7
+SKIS_OPT_SAMPLER, SKIS_OPT_THREAD_MAX_RETRIES, SKIS_OPT_FIRST_STEP = 7, 8, 9
+SKIS_DIFF_IC, SKIS_DIFF_LT = 0, 1
 
 
 class SkisError(RuntimeError):
@@ -30,7 +31,8 @@ class SkisError(RuntimeError):
 
 class skis_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("W", ctypes.c_uint64), ("f", ctypes.c_int32),
-                ("row_uniform_tau", ctypes.c_int32), ("Gamma", ctypes.c_double)]
+                ("row_uniform_tau", ctypes.c_int32), ("Gamma", ctypes.c_double), ("diffusion", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class skis_stats(ctypes.Structure):
@@ -58,6 +60,7 @@ _lib = None
 _P, _I64, _U64, _I32, _INT = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int
 _SIGNATURES = [
     ("skis_load_graph", _INT, [_P, _I64, _I64, _P, _P, _P, _INT, _U64, _INT, _P]),
+    ("skis_load_graph_lt", _INT, [_P, _I64, _I64, _P, _P, _P, _INT, _U64, _INT, _P]),
     ("skis_graph_get_info", _INT, [_P, _P]),
     ("skis_graph_export", _INT, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     ("skis_graph_free", None, [_P]),
@@ -192,16 +195,25 @@ class Server(_Handle):
 
 
 # ------------------------------------------------------------ entry points
-def skis_load_graph(n, src, dst, weights=None, weight_model=SKIS_W_WC, weight_seed=0, stream=None) -> Graph:
+def _load(fn, n, src, dst, weights, weight_model, weight_seed, stream) -> Graph:
     ps, ss = _ptr(src, np.int32)
     pd, sd = _ptr(dst, np.int32)
     wdt = np.float64 if weight_model == SKIS_W_EXPLICIT_P else np.uint32
     pw, sw = _ptr(weights, wdt) if weight_model in (SKIS_W_EXPLICIT_P, SKIS_W_EXPLICIT_TAU) else (None, None)
     out = ctypes.c_void_p()
     m = int(src.shape[0])
-    _check(lib().skis_load_graph(ctypes.byref(out), int(n), m, ps, pd, pw, int(weight_model), int(weight_seed),
-                                 _space(ss, sd, sw), _stream(stream)))
+    _check(fn(ctypes.byref(out), int(n), m, ps, pd, pw, int(weight_model), int(weight_seed), _space(ss, sd, sw),
+              _stream(stream)))
     return Graph(out)
+
+
+def skis_load_graph(n, src, dst, weights=None, weight_model=SKIS_W_WC, weight_seed=0, stream=None) -> Graph:
+    return _load(lib().skis_load_graph, n, src, dst, weights, weight_model, weight_seed, stream)
+
+
+def skis_load_graph_lt(n, src, dst, weights=None, weight_model=SKIS_W_WC, weight_seed=0, stream=None) -> Graph:
+    """The graph under the Linear Threshold model."""
+    return _load(lib().skis_load_graph_lt, n, src, dst, weights, weight_model, weight_seed, stream)
 
 
 def skis_graph_get_info(g: Graph) -> dict:

@@ -41,9 +41,9 @@ static int cuda_fail(const char* where, cudaError_t e) {
     } while (0)
 
 // ------------------------------------------------------------------ graph
-extern "C" int skis_load_graph(skis_graph** out, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
-                               const void* weights, int weight_model, uint64_t weight_seed, int mem_space,
-                               void* cuda_stream) {
+static int load_graph(skis_graph** out, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                      const void* weights, int weight_model, uint64_t weight_seed, int mem_space, int lt,
+                      void* cuda_stream) {
     API_TRY
     if (!out) return fail(SKIS_EINVAL, "skis_load_graph: out is NULL");
     *out = nullptr;
@@ -82,7 +82,7 @@ extern "C" int skis_load_graph(skis_graph** out, int64_t n, int64_t m, const int
     g->m = m;
     g->stream = st;
     std::string err;
-    const int rc = graph_build(g, d_src, d_dst, d_w, weight_model, weight_seed, st, &err);
+    const int rc = graph_build(g, d_src, d_dst, d_w, weight_model, weight_seed, lt, st, &err);
     dev_free(t_src, st);
     dev_free(t_dst, st);
     dev_free(t_w, st);
@@ -95,6 +95,18 @@ extern "C" int skis_load_graph(skis_graph** out, int64_t n, int64_t m, const int
     API_CATCH
 }
 
+extern "C" int skis_load_graph(skis_graph** out, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                               const void* weights, int weight_model, uint64_t weight_seed, int mem_space,
+                               void* cuda_stream) {
+    return load_graph(out, n, m, src, dst, weights, weight_model, weight_seed, mem_space, 0, cuda_stream);
+}
+
+extern "C" int skis_load_graph_lt(skis_graph** out, int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                                  const void* weights, int weight_model, uint64_t weight_seed, int mem_space,
+                                  void* cuda_stream) {
+    return load_graph(out, n, m, src, dst, weights, weight_model, weight_seed, mem_space, 1, cuda_stream);
+}
+
 extern "C" int skis_graph_get_info(const skis_graph* g, skis_graph_info* info) {
     if (!g || !info) return fail(SKIS_EINVAL, "skis_graph_get_info: NULL argument");
     info->n = g->n;
@@ -103,6 +115,7 @@ extern "C" int skis_graph_get_info(const skis_graph* g, skis_graph_info* info) {
     info->f = g->f;
     info->row_uniform_tau = g->row_uniform;
     info->Gamma = (double)g->W / (double)(1ull << g->f);
+    info->diffusion = g->lt ? SKIS_DIFF_LT : SKIS_DIFF_IC;
     return SKIS_OK;
 }
 
@@ -197,6 +210,15 @@ extern "C" int skis_sketch_set_option(skis_sketch* s, int option, uint64_t value
         case SKIS_OPT_THREAD_MAX_STEPS:
             if (value < 1 || value > (1u << 30)) return fail(SKIS_EINVAL, "thread-tier step budget must be in [1, 2^30]");
             s->thread_max_steps = (uint32_t)value;
+            return SKIS_OK;
+        case SKIS_OPT_FIRST_STEP:
+            if (value > 1) return fail(SKIS_EINVAL, "first step must be 0 (rejection) or 1 (bucket)");
+            if (s->T != 0) return fail(SKIS_EINVAL, "the first-step form is chosen before the first sample");
+            s->bucket = (int)value;
+            return SKIS_OK;
+        case SKIS_OPT_THREAD_MAX_RETRIES:
+            if (value < 1 || value > (1u << 24)) return fail(SKIS_EINVAL, "thread-tier retry limit must be in [1, 2^24]");
+            s->thread_max_retries = (uint32_t)value;
             return SKIS_OK;
         case SKIS_OPT_SAMPLER:
             if (value > 1) return fail(SKIS_EINVAL, "sampler must be 0 (IIS) or 1 (RIS)");

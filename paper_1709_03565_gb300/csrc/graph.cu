@@ -129,6 +129,53 @@ __global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __rest
     }
 }
 
+// The gamma chain of every row kept edge by edge, for the bucket form of the
+// first step (Eq. probn): chain[e] = Q after in-edge e of its row, with the
+// same arithmetic as k_gamma, so that chain[last edge] >> s gives w_v back.
+__global__ void k_chain(const RowInfo* __restrict__ rows, const uint32_t* __restrict__ csr_tau, int64_t n,
+                        uint64_t* __restrict__ chain) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const RowInfo r = rows[v];
+        uint64_t Q = 1ull << 62;
+        for (uint32_t k = 0; k < r.deg; ++k) {
+            const uint32_t t = csr_tau ? csr_tau[r.off + k] : r.tau;
+            if (t == kSentinel) Q = 0;
+            else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t)) >> 32);
+            chain[r.off + k] = Q;
+        }
+    }
+}
+
+// Linear Threshold model (Sec. "Extensions to other diffusion models"):
+// gamma_v = the sum of the row's weights, exactly, as w_v = sum tau' with
+// f = 32 (tau' = tau, or 2^32 for the always-live sentinel). A row above 1
+// is not an LT instance and flags the input as invalid.
+__device__ __forceinline__ uint64_t lt_weight(uint32_t tau) { return tau == kSentinel ? (1ull << 32) : tau; }
+
+__global__ void k_gamma_lt(const RowInfo* __restrict__ rows, const uint32_t* __restrict__ csr_tau, int64_t n,
+                           uint64_t* __restrict__ w, DevStatus* status) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const RowInfo r = rows[v];
+        uint64_t S = 0;
+        if (csr_tau) {
+            for (uint32_t k = 0; k < r.deg; ++k) S += lt_weight(csr_tau[r.off + k]);
+        } else {
+            S = (uint64_t)r.deg * lt_weight(r.tau);
+        }
+        if (S > (1ull << 32)) {
+            atomicOr(&status->flags, kStInval);
+            atomicMin(&status->first_bad, (unsigned long long)v);
+            S = 0;
+        }
+        w[v] = S;
+    }
+}
+
+__global__ void k_lt_weights(const uint32_t* __restrict__ csr_tau, int64_t m, uint64_t* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = lt_weight(csr_tau[e]);
+}
+
 // ------------------------------------------------------------- alias table
 // Parallel form of the sweeping alias construction (Huebschle-Schneider and
 // Sanders, "Parallel Weighted Random Sampling", ESA 2019) in integers.
@@ -238,12 +285,34 @@ void graph_release(skis_graph* g) {
     dev_free(g->perm, st);
     dev_free(g->w, st);
     dev_free(g->alias, st);
+    dev_free(g->lt_cum, st);
+    dev_free(g->chain, st);
     g->off = nullptr; g->rows = nullptr; g->src = nullptr; g->tau = nullptr;
-    g->perm = nullptr; g->w = nullptr; g->alias = nullptr;
+    g->perm = nullptr; g->w = nullptr; g->alias = nullptr; g->lt_cum = nullptr; g->chain = nullptr;
+}
+
+// The chain is a cache of the graph built by the first sketch that needs it
+// (the graph is otherwise immutable after loading).
+int graph_ensure_chain(const skis_graph* gc, cudaStream_t st, std::string* err) {
+    skis_graph* g = const_cast<skis_graph*>(gc);
+    if (g->chain || g->m == 0) return SKIS_OK;
+    uint64_t* chain = nullptr;
+    cudaError_t e = dev_alloc_t(&chain, (size_t)g->m, st);
+    if (e == cudaSuccess) {
+        k_chain<<<sm_count() * 8, 256, 0, st>>>(g->rows, g->row_uniform ? nullptr : g->tau, g->n, chain); note_launch();
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        dev_free(chain, st);
+        *err = std::string("CUDA error building the gamma chain: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SKIS_ENOMEM : SKIS_ERR_CUDA;
+    }
+    g->chain = chain;
+    return SKIS_OK;
 }
 
 int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const void* d_weights, int model,
-                uint64_t weight_seed, cudaStream_t st, std::string* err) {
+                uint64_t weight_seed, int lt, cudaStream_t st, std::string* err) {
     int rc = SKIS_OK;
     const int64_t n = g->n, m = g->m;
     const int grid = sm_count() * 8, block = 256;
@@ -260,9 +329,11 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     DevStatus h_status;
     uint64_t nl = 0, nh = 0;
 
-    g->s = bits_for(n) + 1;  // ceil(log2 n) + 1
-    g->f = 62 - g->s;
+    g->lt = lt ? 1 : 0;
+    g->s = g->lt ? 0 : bits_for(n) + 1;  // ceil(log2 n) + 1
+    g->f = g->lt ? 32 : 62 - g->s;
     g->row_uniform = (model == SKIS_W_WC);
+    uint64_t* lt_w = nullptr;
     g->m_pad = ((m + 3) / 4) * 4 + 4;
 
     GB_CUDA(dev_alloc_t(&d_status, 1, st));
@@ -316,8 +387,28 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     GB_CUDA(cudaGetLastError());
 
     // gamma in fixed point and W
-    k_gamma<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->s, g->w); note_launch();
-    GB_CUDA(cudaGetLastError());
+    if (g->lt) {
+        k_gamma_lt<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->w, d_status); note_launch();
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaMemcpyAsync(&h_status, d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        if (h_status.flags & kStInval) {
+            *err = "skis_load_graph_lt: the in-edge weights of vertex " + std::to_string(h_status.first_bad) +
+                   " sum above 1 (not a Linear Threshold instance)";
+            rc = SKIS_EINVAL;
+            goto cleanup;
+        }
+        if (!g->row_uniform && m > 0) {  // running sums for the walk's edge choice
+            GB_CUDA(dev_alloc_t(&lt_w, (size_t)m, st));
+            GB_CUDA(dev_alloc_t(&g->lt_cum, (size_t)m + 1, st));
+            k_lt_weights<<<grid, block, 0, st>>>(g->tau, m, lt_w); note_launch();
+            GB_CUDA(cudaGetLastError());
+            GB_CUDA(scan_u64(lt_w, g->lt_cum, m, st));
+        }
+    } else {
+        k_gamma<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->s, g->w); note_launch();
+        GB_CUDA(cudaGetLastError());
+    }
     GB_CUDA(sum_u64(g->w, n, d_W, st));
 
     // alias table
@@ -355,6 +446,7 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     GB_CUDA(cudaStreamSynchronize(st));
 
 cleanup:
+    dev_free(lt_w, st);
     dev_free(d_status, st);
     dev_free(d_W, st);
     dev_free(keys, st);

@@ -1,14 +1,14 @@
 // Importance Influence Sampling (Sec. III, Alg. 1) on the device, in three
 // tiers chained by sample id.
 //
-// Packed tier (first): a warp holds 32 samples, one per lane, and each step
-// spreads the edge quads still to be drawn in their current rows over its
-// 32 lanes (one Philox block = the 4 coins of a quad), so the lanes draw
-// coins together whatever the mix of row lengths. Member lists (which are
-// also Alg. 1's FIFO queues Q = members[head .. len)) hold up to 32 vertices
-// per sample in shared memory. A sample whose list outgrows it, that meets an
-// in-row longer than the degree threshold or that uses up its step budget is
-// handed by id to the warp tier.
+// Lane tier (first): one lane per sample; each step draws one edge quad of
+// the lane's current row (one Philox block = the 4 coins of a quad). Member
+// lists (which are also Alg. 1's FIFO queues Q = members[head .. len)) hold
+// up to 32 vertices per sample in shared memory; the row of the next pop is
+// loaded ahead; finished samples are written out and lanes refilled in
+// batches. A sample whose list outgrows it, that meets an in-row longer than
+// the degree threshold, or that uses up its step or retry budget is handed
+// by id to the warp tier.
 //
 // Warp tier: one warp per sample. The member list (256 entries) and an
 // open-addressing hash set (the visited set R_j) live in shared memory. Edges
@@ -35,13 +35,9 @@ constexpr int kHCap = 512;         // warp-tier hash slots (load <= 1/2 + one in
 constexpr int kHashBits = 9;
 constexpr int kIdBatch = 16;       // sample ids taken per work-cursor atomic
 constexpr uint32_t kArenaChunk = 2048;        // entries reserved per arena atomic (warp tier)
-constexpr uint32_t kPackArenaChunk = 512;     // entries reserved per arena atomic (packed tier)
+constexpr uint32_t kLaneArenaChunk = 512;     // entries reserved per arena atomic (lane tiers)
 constexpr int kCtaThreads = 512;
 constexpr int kCtaWin = 2 * kCtaThreads;  // queued vertices per load-balanced CTA-tier window
-constexpr int kPackQ = 32;                 // packed-tier member capacity per sample
-constexpr int kPackStride = kPackQ + 1;    // shared-memory row stride of a slot's member list
-constexpr uint32_t kPackMaxRetries = 8;    // rejected rounds before the warp tier takes over
-constexpr int kPackBlock = 256;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 struct SampleArgs {
@@ -53,6 +49,7 @@ struct SampleArgs {
     uint32_t retry_cap;
     uint32_t max_deg;                  // thread tier: longest in-row it expands
     uint32_t max_steps;                // thread tier: edge quads per sample before handing it on
+    uint32_t max_retries;              // thread tier: rejected rounds before handing it on
     int ris;                           // plain RIS: uniform source, one unconditioned round
     // input ids: first_id + t (ids == nullptr) or ids[t], t < count (or
     // t < *count_dev when the list was filled by the previous tier)
@@ -76,7 +73,9 @@ struct SampleArgs {
     uint32_t* bitmaps;
     int32_t* queues;
     uint64_t bitmap_words;
-    const uint4* srcrec;  // thread tier: source record per input t (k_sources), or nullptr
+    const uint4* srcrec;  // lane tier: source record per input t (k_sources)
+    const uint64_t* lt_cum;  // LT graphs with per-edge thresholds: running weight sums, else nullptr
+    const uint64_t* chain;   // bucket first step: the gamma chain per in-edge, else nullptr
 };
 
 __device__ __forceinline__ uint64_t input_count(const SampleArgs& a) {
@@ -109,6 +108,27 @@ __device__ __forceinline__ uint32_t draw_source(const SampleArgs& a, uint64_t j)
     const uint64_t y = __umul64hi(u2, a.W);
     const AliasEntry e = a.alias[col];
     return y < e.prob ? (uint32_t)col : e.alias;
+}
+
+// The bucket form of Alg. 1 lines 2-6 (Eq. probn): bucket i of the source's
+// row is "in-edges before i dead, edge i live", of mass Q_{i-1} - Q_i in the
+// gamma chain (total 2^62 - Q_d); z = floor(U (2^62 - Q_d) / 2^64) from the
+// BUCKET-domain block of sample j picks the first edge e with
+// 2^62 - Q_e > z, i.e. Q_e < 2^62 - z (the chain does not increase).
+// Returns the edge position; the edges after it get FIRST coins of round 0.
+__device__ __forceinline__ uint64_t bucket_pick(const SampleArgs& a, uint64_t j, uint64_t off, uint32_t deg) {
+    const uint64_t one62 = 1ull << 62;
+    const uint64_t G = one62 - a.chain[off + deg - 1];
+    const uint4 x = coin_block(a.seed, 0, 0, kDomBucket, j);
+    const uint64_t z = __umul64hi((uint64_t)x.x | ((uint64_t)x.y << 32), G);
+    const uint64_t lim = one62 - z;
+    uint32_t lo = 0, hi = deg - 1;  // the answer exists: Q_d = 2^62 - G < lim
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a.chain[off + mid] < lim) hi = mid;
+        else lo = mid + 1;
+    }
+    return off + lo;
 }
 
 // ----------------------------------------------------------- inserters
@@ -241,6 +261,19 @@ __device__ __forceinline__ uint32_t first_step_warp(const SampleArgs& a, uint64_
                                                     bool* failed) {
     const int lane = threadIdx.x & 31;
     *failed = false;
+    if (a.chain) {  // bucket form: the picked in-edge, then round-0 coins after it
+        int32_t u = -1;
+        uint64_t e = 0;
+        if (lane == 0) {
+            e = bucket_pick(a, j, rv.off, rv.deg);
+            u = a.src[e];
+        }
+        e = __shfl_sync(kFull, e, 0);
+        ins.insert(u);
+        const uint64_t rest = rv.off + rv.deg - (e + 1);
+        expand_rows(a, j, kDomFirst, 0, e + 1, lane == 0 ? (uint32_t)rest : 0u, rv.tau, ins);
+        return 0;
+    }
     if (a.ris) {  // RIS: round 0, accepted whatever its coins
         expand_rows(a, j, kDomFirst, 0, rv.off, lane == 0 ? rv.deg : 0u, rv.tau, ins);
         return 0;
@@ -321,128 +354,214 @@ __global__ void k_sources(SampleArgs a, uint4* __restrict__ rec) {
     }
 }
 
-// ----------------------------------------------------------- packed tier
-// A warp holds 32 samples, one slot per lane (the slot's state lives in its
-// lane's registers). Each step the edge quads still to be drawn in the slots'
-// current rows are laid end to end and the warp's 32 lanes take the first 32:
-// lane i works on the quad at position i (slot found by a binary search over
-// the slots' inclusive prefix of remaining quads), so every lane draws a
-// Philox block whenever the warp holds that much work. Live coins then join
-// their sample's member list one at a time in lane order, which is the
-// sample's own edge order, with the visited check done by all lanes against
-// up to 32 members at once.
 __device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
     const uint32_t lo = __shfl_sync(kFull, (uint32_t)v, src);
     const uint32_t hi = __shfl_sync(kFull, (uint32_t)(v >> 32), src);
     return ((uint64_t)hi << 32) | lo;
 }
 
-__global__ void __launch_bounds__(kPackBlock, 4) k_iis_pack(SampleArgs a) {
-    // member k of slot s at mq[s * kPackStride + k]: a row stride of 33 words
-    // keeps both "one slot, all members" and "all slots, one member each"
-    // accesses free of bank conflicts
-    __shared__ int32_t s_q[kPackBlock / 32][32 * kPackStride];
-    __shared__ uint32_t s_len[kPackBlock / 32][32];
+// ------------------------------------------------------------- lane tier
+// One lane per sample with a lean inner step: one edge quad of the lane's
+// current row (Philox block, thresholds, four compares); live coins join the
+// member list at once (visited check by scanning it); at the end of a row
+// the next queued member's row, loaded ahead, takes over. Finished samples
+// are written out, and idle lanes refilled, in batches: when at least
+// kLaneRefill lanes are idle or nothing else is left.
+constexpr int kLaneBlock = 256;
+constexpr int kLaneQ = 32;
+constexpr int kLaneStride = kLaneQ + 1;  // odd: conflict-free by lane and by member
+constexpr int kLaneRefill = 8;
+
+__global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
+    __shared__ int32_t s_q[kLaneBlock / 32][32 * kLaneStride];
     const int lane = threadIdx.x & 31;
     int32_t* const mq = s_q[threadIdx.x >> 5];
-    uint32_t* const mlen = s_len[threadIdx.x >> 5];
-    int32_t* const mine = mq + lane * kPackStride;
+    int32_t* const mine = mq + lane * kLaneStride;
     const uint64_t count = input_count(a);
     const uint4* __restrict__ tau4 = reinterpret_cast<const uint4*>(a.tau);
     const int4* __restrict__ src4 = reinterpret_cast<const int4*>(a.src);
 
-    // state of this lane's slot; rows are [lo, hi) in edge positions (the
-    // graph holds fewer than 2^32 - 8 edges), qn the next quad to hand out
-    bool busy = false, first = false, any = false;
+    bool busy = false, done = false, first = false, any = false, pf_ok = false;
     uint64_t j = 0, coins = 0;
-    uint32_t v = 0, r = 0, head = 0, src_deg = 0, tau_row = 0, steps = 0;
-    uint32_t lo = 0, hi = 0, qn = 0;
-    bool pf_ok = false;                     // the row of the next pop, loaded ahead
+    uint32_t v = 0, r = 0, len = 0, head = 0, src_deg = 0, tau_row = 0, steps = 0;
+    uint32_t lo = 0, hi = 0, qc = 0, q_last = 0;
     uint32_t pf_off = 0, pf_deg = 0, pf_tau = 0;
-    bool exhausted = false;                 // warp-uniform: no ids left to claim
-    uint64_t pool_base = 0;                 // warp-uniform input pool [pool_base, + pool_n)
+    bool exhausted = false;
+    uint64_t pool_base = 0;
     uint32_t pool_n = 0, pool_used = 0;
-    uint4 rec = make_uint4(0, 0, 0, 0);     // source record of pool entry `lane`
-    uint64_t chunk_pos = 0, chunk_end = 0;  // this warp's arena reservation
+    uint4 rec = make_uint4(0, 0, 0, 0);
+    uint64_t chunk_pos = 0, chunk_end = 0;
 
     for (;;) {
-        __syncwarp();  // the previous step's shared-memory reads are done before slots are reused
-        // (1) idle slots take the next inputs from the warp's pool of 32,
-        // whose source records (k_sources) lane i holds for pool entry i;
-        // the pool is refilled with one atomic per 32 inputs
-        unsigned idle = __ballot_sync(kFull, !busy);
-        while (idle && !exhausted) {
-            if (pool_used == pool_n) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(a.work, 32ull);
-                base = __shfl_sync(kFull, base, 0);
-                if (base >= count) {
-                    exhausted = true;
-                    break;
+        // ---- batched maintenance: write out finished samples, refill
+        const unsigned dn = __ballot_sync(kFull, done);
+        const unsigned free_l = __ballot_sync(kFull, !busy || done);
+        const bool all_free = free_l == kFull;
+        if (__popc(free_l) >= kLaneRefill || all_free) {
+            if (dn) {
+                const uint32_t mylen = done ? len : 0u;
+                uint32_t incl = mylen;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, incl, d);
+                    if (lane >= d) incl += y;
                 }
-                pool_base = base;
-                pool_n = (uint32_t)min(32ull, count - base);
-                pool_used = 0;
-                if ((uint32_t)lane < pool_n) rec = __ldg(a.srcrec + base + lane);
-            }
-            const uint32_t take = min((uint32_t)__popc(idle), pool_n - pool_used);
-            const uint32_t rank = __popc(idle & lanemask_lt());
-            const int from = (int)min(pool_used + rank, 31u);
-            const uint32_t rv_src = __shfl_sync(kFull, rec.x, from);
-            const uint32_t rv_deg = __shfl_sync(kFull, rec.y, from);
-            const uint32_t rv_off = __shfl_sync(kFull, rec.z, from);
-            const uint32_t rv_tau = __shfl_sync(kFull, rec.w, from);
-            if (!busy && rank < take) {
-                j = input_id(a, pool_base + pool_used + rank);
-                v = rv_src;  // Alg. 1 line 1, drawn by k_sources
-                if (rv_deg > a.max_deg) {
-                    hand_on(a, j);
-                } else {
-                    busy = true;
-                    first = true;
-                    any = false;
-                    pf_ok = false;
-                    r = 0;
-                    mine[0] = (int32_t)v;
-                    mlen[lane] = 1;
-                    head = 1;
-                    src_deg = rv_deg;
-                    tau_row = rv_tau;
-                    lo = rv_off;
-                    hi = lo + rv_deg;  // a RIS source may have no in-edges
-                    qn = lo >> 2;
-                    coins = 0;
-                    steps = 0;
+                const uint32_t total = __shfl_sync(kFull, incl, 31);
+                bool fits = true;
+                if (chunk_end - chunk_pos < total) {
+                    const uint64_t size = max((uint64_t)kLaneArenaChunk, (uint64_t)total);
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(a.arena_cursor, (unsigned long long)size);
+                    base = __shfl_sync(kFull, base, 0);
+                    if (base + size > a.arena_cap) {
+                        fits = false;
+                        chunk_pos = chunk_end = 0;
+                    } else {
+                        chunk_pos = base;
+                        chunk_end = base + size;
+                    }
+                }
+                const uint64_t at = chunk_pos + (incl - mylen);
+                if (done) {
+                    if (fits) {
+                        a.h_off[j] = at;
+                        a.h_len[j] = len;
+                        a.h_src[j] = v;
+                        a.h_retries[j] = r;
+                        a.h_coins[j] = coins;
+                    } else {
+                        arena_overflow(a, j);
+                    }
+                }
+                __syncwarp();
+                if (fits) {
+                    unsigned m = dn;
+                    while (m) {
+                        const int sl = __ffs(m) - 1;
+                        m &= m - 1;
+                        const uint64_t at_s = shfl_u64(at, sl);
+                        const uint32_t len_s = __shfl_sync(kFull, len, sl);
+                        if ((uint32_t)lane < len_s) a.arena[at_s + lane] = mq[sl * kLaneStride + lane];
+                    }
+                    chunk_pos += total;
+                }
+                __syncwarp();
+                if (done) {
+                    done = false;
+                    busy = false;
                 }
             }
-            pool_used += take;
-            idle = __ballot_sync(kFull, !busy);
+            unsigned idle = __ballot_sync(kFull, !busy);
+            while (idle && !exhausted) {
+                if (pool_used == pool_n) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(a.work, 32ull);
+                    base = __shfl_sync(kFull, base, 0);
+                    if (base >= count) {
+                        exhausted = true;
+                        break;
+                    }
+                    pool_base = base;
+                    pool_n = (uint32_t)min(32ull, count - base);
+                    pool_used = 0;
+                    if ((uint32_t)lane < pool_n) rec = __ldg(a.srcrec + base + lane);
+                }
+                const uint32_t take = min((uint32_t)__popc(idle), pool_n - pool_used);
+                const uint32_t rank = __popc(idle & lanemask_lt());
+                const int from = (int)min(pool_used + rank, 31u);
+                const uint32_t rv_src = __shfl_sync(kFull, rec.x, from);
+                const uint32_t rv_deg = __shfl_sync(kFull, rec.y, from);
+                const uint32_t rv_off = __shfl_sync(kFull, rec.z, from);
+                const uint32_t rv_tau = __shfl_sync(kFull, rec.w, from);
+                if (!busy && rank < take) {
+                    j = input_id(a, pool_base + pool_used + rank);
+                    v = rv_src;  // Alg. 1 line 1, drawn by k_sources
+                    if (rv_deg > a.max_deg) {
+                        hand_on(a, j);
+                    } else {
+                        busy = true;
+                        first = true;
+                        any = false;
+                        pf_ok = false;
+                        r = 0;
+                        mine[0] = (int32_t)v;
+                        len = 1;
+                        head = 1;
+                        src_deg = rv_deg;
+                        tau_row = rv_tau;
+                        lo = rv_off;
+                        hi = rv_off + rv_deg;
+                        q_last = hi > lo ? (hi - 1) >> 2 : lo >> 2;
+                        if (a.chain) {  // bucket form: the picked in-edge, round-0 coins after it
+                            const uint32_t e = (uint32_t)bucket_pick(a, j, rv_off, rv_deg);
+                            mine[1] = a.src[e];
+                            len = 2;
+                            lo = e + 1;
+                            any = true;
+                        }
+                        qc = lo >> 2;
+                        coins = 0;
+                        steps = 0;
+                    }
+                }
+                pool_used += take;
+                idle = __ballot_sync(kFull, !busy);
+            }
+            if (!__any_sync(kFull, busy)) {
+                if (exhausted) break;
+                continue;
+            }
         }
-        if (!__any_sync(kFull, busy)) {
-            if (exhausted) break;
-            continue;
-        }
-        __syncwarp();
+        if (!busy || done) continue;  // the lane waits for the next batch
 
-        // (2) slots whose current row is used up: the end of a first-step
-        // round (Alg. 1 lines 2-6: accept it or redraw), or the next pop of
-        // the reverse BFS (lines 7-8)
-        bool done = false, handed = false, failed = false;
-        if (busy && (hi <= lo || qn > ((hi - 1) >> 2))) {
+        // ---- one edge quad: coins of lines 4-6 (first step, round r) or
+        // of line 9 (reverse BFS); a RIS source may have no in-edges
+        bool handed = false, failed = false;
+        if (hi > lo) {
+            const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_row, tau_row, tau_row, tau_row);
+            const uint4 x = coin_block(a.seed, qc, first ? r : 0u, first ? kDomFirst : kDomBfs, j);
+            const uint32_t e0 = qc << 2;
+            unsigned live = 0;
+            live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
+            live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
+            live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
+            live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
+            if (live) {
+                any = true;
+                const int4 s4 = __ldg(src4 + qc);
+                const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (!((live >> k) & 1u) || handed) continue;
+                    const int32_t u = cand[k];
+                    bool seen = false;
+                    for (uint32_t i = 0; i < len; ++i)
+                        if (mine[i] == u) { seen = true; break; }
+                    if (seen) continue;
+                    if (len == (uint32_t)kLaneQ) handed = true;  // the warp tier takes it
+                    else mine[len++] = u;
+                }
+            }
+            ++steps;
+        }
+        if (!handed && (hi <= lo || qc >= q_last)) {  // the row is used up
             if (first) {
                 if (any || a.ris) {
                     first = false;
                     coins = (uint64_t)src_deg * (r + 1);
                 } else if (++r >= a.retry_cap) {
                     failed = true;
-                } else if (r >= kPackMaxRetries) {
+                } else if (r >= a.max_retries) {
                     handed = true;  // a rare source: the warp tier searches rounds in parallel
                 } else {
-                    qn = lo >> 2;
+                    qc = lo >> 2;  // next round over the same row
                 }
             }
             if (!first && !failed && !handed) {
-                if (head < mlen[lane]) {
+                // Alg. 1 lines 7-8: pop the next queued members until one
+                // has in-edges (the first one's row was loaded ahead)
+                bool row = false;
+                while (!row && head < len) {
                     if (!pf_ok) {
                         const RowInfo rw = a.rows[mine[head]];
                         pf_off = (uint32_t)rw.off;
@@ -454,167 +573,33 @@ __global__ void __launch_bounds__(kPackBlock, 4) k_iis_pack(SampleArgs a) {
                     coins += pf_deg;
                     if (pf_deg > a.max_deg) {
                         handed = true;
-                    } else {
+                        break;
+                    }
+                    if (pf_deg > 0) {
+                        row = true;
                         lo = pf_off;
                         hi = pf_off + pf_deg;
                         tau_row = pf_tau;
-                        qn = lo >> 2;
+                        qc = lo >> 2;
+                        q_last = (hi - 1) >> 2;
                     }
-                } else {
-                    done = true;
                 }
+                if (!row && !handed) done = true;
             }
+        } else if (!handed) {
+            ++qc;
         }
-        // a sample with much work is finished faster by a whole warp
-        if (busy && !done && steps > a.max_steps) handed = true;
+        if (!done && !handed && steps > a.max_steps) handed = true;
         if (handed) hand_on(a, j);
         if (failed) record_retry_failure(a, j, v, r, src_deg);
         if (handed || failed) busy = false;
-
-        // (3) finished samples: one arena reservation for the warp's batch;
-        // each list is copied by the whole warp (coalesced)
-        unsigned dm = __ballot_sync(kFull, done);
-        if (dm) {
-            const uint32_t mylen = done ? mlen[lane] : 0u;
-            uint32_t incl = mylen;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, incl, d);
-                if (lane >= d) incl += y;
-            }
-            const uint32_t total = __shfl_sync(kFull, incl, 31);
-            bool fits = true;
-            if (chunk_end - chunk_pos < total) {
-                const uint64_t size = max((uint64_t)kPackArenaChunk, (uint64_t)total);
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(a.arena_cursor, (unsigned long long)size);
-                base = __shfl_sync(kFull, base, 0);
-                if (base + size > a.arena_cap) {
-                    fits = false;
-                    chunk_pos = chunk_end = 0;
-                } else {
-                    chunk_pos = base;
-                    chunk_end = base + size;
-                }
-            }
-            const uint64_t at = chunk_pos + (incl - mylen);
-            if (done) {
-                if (fits) {
-                    a.h_off[j] = at;
-                    a.h_len[j] = mylen;
-                    a.h_src[j] = v;
-                    a.h_retries[j] = r;
-                    a.h_coins[j] = coins;
-                } else {
-                    arena_overflow(a, j);
-                }
-                busy = false;
-            }
-            if (fits) {
-                while (dm) {
-                    const int sl = __ffs(dm) - 1;
-                    dm &= dm - 1;
-                    const uint64_t at_s = shfl_u64(at, sl);
-                    const uint32_t len_s = mlen[sl];
-                    for (uint32_t k = lane; k < len_s; k += 32) a.arena[at_s + k] = mq[sl * kPackStride + k];
-                }
-                chunk_pos += total;
-            }
-        }
-
-        // (4) hand out the slots' remaining quads to the lanes
-        const uint32_t rem = (busy && hi > lo && qn <= ((hi - 1) >> 2)) ? ((hi - 1) >> 2) - qn + 1 : 0u;
-        uint32_t incl = rem;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, incl, d);
-            if (lane >= d) incl += y;
-        }
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        if (total == 0) continue;
-        int sl = 0;  // the slot of this lane's quad: the number of slots with incl <= lane
-#pragma unroll
-        for (int b = 16; b; b >>= 1) {
-            const uint32_t x = __shfl_sync(kFull, incl, sl + b - 1);
-            if (x <= (uint32_t)lane) sl += b;
-        }
-        const uint32_t excl_s = __shfl_sync(kFull, incl - rem, sl);
-        const uint32_t qc = __shfl_sync(kFull, qn, sl) + ((uint32_t)lane - excl_s);
-        const uint32_t lo_s = __shfl_sync(kFull, lo, sl);
-        const uint32_t hi_s = __shfl_sync(kFull, hi, sl);
-        const uint32_t tau_s = __shfl_sync(kFull, tau_row, sl);
-        const uint32_t round_s = __shfl_sync(kFull, first ? r : kEmpty, sl);  // kEmpty: BFS coins
-        const uint64_t j_s = shfl_u64(j, sl);
-        // (5) each slot advances past the quads it was given; a BFS slot
-        // whose row is now fully handed out loads the row of its next pop
-        // ahead, while the coins of this step are drawn
-        if (rem) {
-            const uint32_t excl = incl - rem;
-            const uint32_t taken = excl >= 32u ? 0u : min(rem, 32u - excl);
-            qn += taken;
-            steps += taken;
-            if (!first && !pf_ok && qn > ((hi - 1) >> 2) && head < mlen[lane]) {
-                const RowInfo rw = a.rows[mine[head]];
-                pf_off = (uint32_t)rw.off;
-                pf_deg = rw.deg;
-                pf_tau = rw.tau;
-                pf_ok = true;
-            }
-        }
-        unsigned live = 0;
-        int4 s4 = make_int4(0, 0, 0, 0);
-        if ((uint32_t)lane < total) {
-            // one edge quad: coins of lines 4-6 (first step, round r) or of
-            // line 9 (reverse BFS); its sources are loaded with its
-            // thresholds rather than after the coins
-            const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_s, tau_s, tau_s, tau_s);
-            s4 = __ldg(src4 + qc);
-            const bool fs = round_s != kEmpty;
-            const uint4 x = coin_block(a.seed, qc, fs ? round_s : 0u, fs ? kDomFirst : kDomBfs, j_s);
-            const uint32_t e0 = qc << 2;
-            live |= (e0 + 0 >= lo_s && e0 + 0 < hi_s && coin_live(x.x, t4.x)) ? 1u : 0u;
-            live |= (e0 + 1 >= lo_s && e0 + 1 < hi_s && coin_live(x.y, t4.y)) ? 2u : 0u;
-            live |= (e0 + 2 >= lo_s && e0 + 2 < hi_s && coin_live(x.z, t4.z)) ? 4u : 0u;
-            live |= (e0 + 3 >= lo_s && e0 + 3 < hi_s && coin_live(x.w, t4.w)) ? 8u : 0u;
-        }
-
-        // (6) live coins join their samples in lane order (Alg. 1 lines 5
-        // and 10-11; an in-neighbour already in R_j is skipped)
-        unsigned lm = __ballot_sync(kFull, live != 0);
-        unsigned hit = 0, over = 0;
-        while (lm) {
-            const int L = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int sL = __shfl_sync(kFull, sl, L);
-            unsigned bits = __shfl_sync(kFull, live, L);
-            const int32_t c0 = __shfl_sync(kFull, s4.x, L);
-            const int32_t c1 = __shfl_sync(kFull, s4.y, L);
-            const int32_t c2 = __shfl_sync(kFull, s4.z, L);
-            const int32_t c3 = __shfl_sync(kFull, s4.w, L);
-            hit |= 1u << sL;
-            int32_t* const q = mq + sL * kPackStride;
-            while (bits && !((over >> sL) & 1u)) {
-                const int k = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int32_t u = k == 0 ? c0 : k == 1 ? c1 : k == 2 ? c2 : c3;
-                const uint32_t len = mlen[sL];
-                const bool seen = (uint32_t)lane < len && q[lane] == u;
-                if (__ballot_sync(kFull, seen)) continue;
-                if (len == (uint32_t)kPackQ) {
-                    over |= 1u << sL;  // outgrew the list: the warp tier takes it
-                } else {
-                    if (lane == 0) {
-                        q[len] = u;
-                        mlen[sL] = len + 1;
-                    }
-                    __syncwarp();
-                }
-            }
-        }
-        any = any || ((hit >> lane) & 1u);
-        if (busy && ((over >> lane) & 1u)) {
-            hand_on(a, j);
-            busy = false;
+        // load the next pop's row ahead while this row's last quads are drawn
+        if (busy && !done && !first && !pf_ok && head < len && q_last - qc <= 1u) {
+            const RowInfo rw = a.rows[mine[head]];
+            pf_off = (uint32_t)rw.off;
+            pf_deg = rw.deg;
+            pf_tau = rw.tau;
+            pf_ok = true;
         }
     }
 }
@@ -745,7 +730,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
         uint32_t r = 0;
         bool failed = false;
         const uint64_t nq_src = ((rv.off + rv.deg - 1) >> 2) - (rv.off >> 2) + 1;
-        if (nq_src <= 16) {
+        if (nq_src <= 16 || a.chain) {
             if (wid == 0) {
                 bool f = false;
                 const uint32_t rr = first_step_warp(a, j, rv, ins, &f);
@@ -900,6 +885,217 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
     }
 }
 
+// --------------------------------------------------------------- LT walks
+// Linear Threshold samples (Sec. "Extensions to other diffusion models",
+// LT): the source by Eq. probu with gamma_v = the row's weight sum, exactly
+// one in-neighbour picked with probability w(u,v) / gamma_v, then the
+// reverse walk of RIS for LT: from the last member x, one draw picks at most
+// one in-edge of x (edge i when P_{i-1} <= y < P_i for the running weight
+// sums P, none when y >= P_d); the walk ends when none is picked or the
+// picked vertex is already in R_j. Step t of sample j draws the Philox block
+// (q = t, domain LT, sample j): step 0 conditioned (64-bit U, y = floor(U S
+// / 2^64)), later steps y = its word 0. Two tiers: one lane per sample with
+// up to kLtQ members in shared memory, then one warp per CTA-tier slot with
+// the slot's global visited bitmap and queue.
+constexpr int kLtBlock = 256;
+constexpr int kLtQ = 48;
+
+__device__ __forceinline__ uint64_t lt_weight(uint32_t tau) { return tau == kSentinel ? (1ull << 32) : (uint64_t)tau; }
+
+// one walk step from a vertex with in-row rw: the picked in-neighbour, or -1
+// when the walk ends there
+__device__ __forceinline__ int32_t lt_step(const SampleArgs& a, uint64_t j, uint32_t t, const RowInfo& rw) {
+    if (rw.deg == 0) return -1;
+    const uint64_t base = a.lt_cum ? a.lt_cum[rw.off] : 0;
+    const uint64_t S = a.lt_cum ? a.lt_cum[rw.off + rw.deg] - base : (uint64_t)rw.deg * lt_weight(rw.tau);
+    const uint4 b = coin_block(a.seed, t, 0, kDomLt, j);
+    uint64_t y;
+    if (t == 0 && !a.ris) {
+        y = __umul64hi((uint64_t)b.x | ((uint64_t)b.y << 32), S);  // Pr[u] = w(u, v) / gamma_v
+    } else {
+        y = b.x;
+        if (y >= S) return -1;  // no in-edge kept
+    }
+    uint32_t i;
+    if (!a.lt_cum) {
+        i = (uint32_t)(y / lt_weight(rw.tau));
+    } else {  // the first position whose running sum exceeds y
+        uint32_t lo = 0, hi = rw.deg - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.lt_cum[rw.off + mid + 1] - base > y) hi = mid;
+            else lo = mid + 1;
+        }
+        i = lo;
+    }
+    return a.src[rw.off + i];
+}
+
+__global__ void __launch_bounds__(kLtBlock) k_lt_walk(SampleArgs a) {
+    __shared__ int32_t s_q[kLtBlock / 32][kLtQ][32];
+    const int lane = threadIdx.x & 31;
+    int32_t(*const mq)[32] = s_q[threadIdx.x >> 5];  // mq[k][lane]: member k of this lane's sample
+    const uint64_t count = input_count(a);
+    bool busy = false, exhausted = false;
+    uint64_t j = 0, coins = 0;
+    uint32_t v = 0, len = 0, t = 0;
+    int32_t x = 0;
+    uint64_t chunk_pos = 0, chunk_end = 0;
+
+    for (;;) {
+        const unsigned idle = __ballot_sync(kFull, !busy);
+        if (idle && !exhausted) {
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.work, (unsigned long long)__popc(idle));
+            base = __shfl_sync(kFull, base, leader);
+            if (base + __popc(idle) >= count) exhausted = true;
+            if (!busy) {
+                const uint64_t ti = base + __popc(idle & lanemask_lt());
+                if (ti < count) {
+                    j = input_id(a, ti);
+                    v = draw_source(a, j);
+                    x = (int32_t)v;
+                    mq[0][lane] = x;
+                    len = 1;
+                    t = 0;
+                    coins = 0;
+                    busy = true;
+                }
+            }
+        }
+        if (!__any_sync(kFull, busy)) {
+            if (exhausted) break;
+            continue;
+        }
+        bool done = false;
+        if (busy) {
+            const RowInfo rw = a.rows[x];
+            coins += rw.deg;
+            const int32_t u = lt_step(a, j, t, rw);
+            ++t;
+            if (u < 0) {
+                done = true;
+            } else {
+                bool seen = false;
+                for (uint32_t i = 0; i < len; ++i)
+                    if (mq[i][lane] == u) { seen = true; break; }
+                if (seen) {
+                    done = true;  // the walk closes on R_j
+                } else if (len == (uint32_t)kLtQ) {
+                    hand_on(a, j);  // a long walk: the slot tier redraws it
+                    busy = false;
+                } else {
+                    mq[len++][lane] = u;
+                    x = u;
+                }
+            }
+        }
+        const unsigned dm = __ballot_sync(kFull, done);
+        if (dm) {
+            const uint32_t mylen = done ? len : 0u;
+            uint32_t incl = mylen;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, d);
+                if (lane >= d) incl += y;
+            }
+            const uint32_t total = __shfl_sync(kFull, incl, 31);
+            bool fits = true;
+            if (chunk_end - chunk_pos < total) {
+                const uint64_t size = max((uint64_t)kLaneArenaChunk, (uint64_t)total);
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(a.arena_cursor, (unsigned long long)size);
+                base = __shfl_sync(kFull, base, 0);
+                if (base + size > a.arena_cap) {
+                    fits = false;
+                    chunk_pos = chunk_end = 0;
+                } else {
+                    chunk_pos = base;
+                    chunk_end = base + size;
+                }
+            }
+            if (done) {
+                if (fits) {
+                    const uint64_t at = chunk_pos + (incl - mylen);
+                    for (uint32_t i = 0; i < len; ++i) a.arena[at + i] = mq[i][lane];
+                    a.h_off[j] = at;
+                    a.h_len[j] = len;
+                    a.h_src[j] = v;
+                    a.h_retries[j] = 0;
+                    a.h_coins[j] = coins;
+                } else {
+                    arena_overflow(a, j);
+                }
+                busy = false;
+            }
+            if (fits) chunk_pos += total;
+        }
+    }
+}
+
+// Long LT walks: one warp per slot; lane 0 walks with the slot's global
+// visited bitmap and queue, the warp copies the members out and clears the
+// bitmap.
+__global__ void __launch_bounds__(32) k_lt_long(SampleArgs a) {
+    const int lane = threadIdx.x & 31;
+    uint32_t* bitmap = a.bitmaps + (uint64_t)blockIdx.x * a.bitmap_words;
+    int32_t* queue = a.queues + (uint64_t)blockIdx.x * a.n;
+    const uint64_t count = input_count(a);
+    for (;;) {
+        unsigned long long ti = 0;
+        if (lane == 0) ti = atomicAdd(a.work, 1ull);
+        ti = __shfl_sync(kFull, ti, 0);
+        if (ti >= count) break;
+        const uint64_t j = input_id(a, ti);
+        uint32_t len = 0, v = 0;
+        uint64_t coins = 0;
+        if (lane == 0) {
+            v = draw_source(a, j);
+            bitmap[v >> 5] |= 1u << (v & 31);
+            queue[0] = (int32_t)v;
+            len = 1;
+            int32_t x = (int32_t)v;
+            for (uint32_t t = 0;; ++t) {  // at most n steps: each adds a new member
+                const RowInfo rw = a.rows[x];
+                coins += rw.deg;
+                const int32_t u = lt_step(a, j, t, rw);
+                if (u < 0) break;
+                const uint32_t bit = 1u << (u & 31);
+                if (bitmap[(uint32_t)u >> 5] & bit) break;
+                bitmap[(uint32_t)u >> 5] |= bit;
+                queue[len++] = u;
+                x = u;
+            }
+        }
+        __syncwarp();
+        len = __shfl_sync(kFull, len, 0);
+        v = __shfl_sync(kFull, v, 0);
+        coins = __shfl_sync(kFull, coins, 0);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.arena_cursor, (unsigned long long)len);
+        base = __shfl_sync(kFull, base, 0);
+        const bool fits = base + len <= a.arena_cap;
+        for (uint32_t i = lane; i < len; i += 32) {
+            const int32_t u = queue[i];
+            if (fits) a.arena[base + i] = u;
+            bitmap[(uint32_t)u >> 5] = 0;  // restore the all-zero bitmap
+        }
+        if (lane == 0) {
+            if (fits) {
+                a.h_off[j] = base;
+                a.h_len[j] = len;
+                a.h_src[j] = v;
+                a.h_retries[j] = 0;
+                a.h_coins[j] = coins;
+            } else {
+                arena_overflow(a, j);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------ host
 #define SK_CUDA(call)                                                                   \
     do {                                                                                \
@@ -1005,9 +1201,9 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     int rc = ensure_sample_buffers(s, count, st, err);
     if (rc != SKIS_OK) return rc;
     const bool thread_tier = s->thread_max_deg > 0;
-    int thread_blocks = 0, warp_blocks = 0;
-    rc = occupancy_grid((const void*)k_iis_pack, kPackBlock, s->thread_blocks,
-                        (count + kPackBlock - 1) / kPackBlock, err, &thread_blocks);
+    int warp_blocks = 0, lane_blocks = 0;
+    rc = occupancy_grid((const void*)k_iis_lane, kLaneBlock, s->thread_blocks,
+                        (count + kLaneBlock - 1) / kLaneBlock, err, &lane_blocks);
     if (rc != SKIS_OK) return rc;
     rc = occupancy_grid((const void*)k_iis_warp, kWarpThreads, s->warp_blocks,
                         thread_tier ? UINT64_MAX : (count + kIdBatch - 1) / kIdBatch, err, &warp_blocks);
@@ -1024,6 +1220,7 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.retry_cap = s->retry_cap;
     base.max_deg = s->thread_max_deg;
     base.max_steps = s->thread_max_steps;
+    base.max_retries = s->thread_max_retries;
     base.ris = s->ris;
     base.ids = nullptr;
     base.first_id = s->T;
@@ -1043,6 +1240,19 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.queues = s->queues;
     base.bitmap_words = s->bitmap_words;
     base.srcrec = nullptr;
+    base.lt_cum = g->lt_cum;
+    base.chain = nullptr;
+    if (s->bucket && !s->ris && !g->lt) {
+        rc = graph_ensure_chain(g, st, err);
+        if (rc != SKIS_OK) return rc;
+        base.chain = g->chain;
+    }
+    int lt_blocks = 0;
+    if (g->lt) {
+        rc = occupancy_grid((const void*)k_lt_walk, kLtBlock, s->thread_blocks, (count + kLtBlock - 1) / kLtBlock,
+                            err, &lt_blocks);
+        if (rc != SKIS_OK) return rc;
+    }
 
     DevStatus hst;
     SampleCounters hc;
@@ -1077,21 +1287,33 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
         ac.out_count = nullptr;
 
         SK_CUDA(cudaEventRecord(s->ev[0], st));
-        if (thread_tier) {
-            const uint64_t in_count = base.count;
-            k_sources<<<(int)std::max<uint64_t>(1, std::min<uint64_t>((in_count + 255) / 256, (uint64_t)sm_count() * 16)),
-                        256, 0, st>>>(at, s->srcrec); note_launch();
-            at.srcrec = s->srcrec;
-            k_iis_pack<<<thread_blocks, kPackBlock, 0, st>>>(at); note_launch();
+        if (g->lt) {  // LT: lane-per-sample walks, then long walks on the CTA-tier slots
+            aw.ids = s->to_warp_ids;
+            aw.count_dev = &s->ctr->n_to_warp;
+            k_lt_walk<<<lt_blocks, kLtBlock, 0, st>>>(at); note_launch();
             SK_CUDA(cudaGetLastError());
+            SK_CUDA(cudaEventRecord(s->ev[1], st));
+            k_lt_long<<<s->cta_slots_alloc, 32, 0, st>>>(aw); note_launch();
+            SK_CUDA(cudaGetLastError());
+            SK_CUDA(cudaEventRecord(s->ev[2], st));
+            SK_CUDA(cudaEventRecord(s->ev[3], st));
+        } else {
+            if (thread_tier) {
+                const uint64_t in_count = base.count;
+                k_sources<<<(int)std::max<uint64_t>(1, std::min<uint64_t>((in_count + 255) / 256, (uint64_t)sm_count() * 16)),
+                            256, 0, st>>>(at, s->srcrec); note_launch();
+                at.srcrec = s->srcrec;
+                k_iis_lane<<<lane_blocks, kLaneBlock, 0, st>>>(at); note_launch();
+                SK_CUDA(cudaGetLastError());
+            }
+            SK_CUDA(cudaEventRecord(s->ev[1], st));
+            k_iis_warp<<<warp_blocks, kWarpThreads, 0, st>>>(aw); note_launch();
+            SK_CUDA(cudaGetLastError());
+            SK_CUDA(cudaEventRecord(s->ev[2], st));
+            k_iis_cta<<<s->cta_slots_alloc, kCtaThreads, 0, st>>>(ac); note_launch();
+            SK_CUDA(cudaGetLastError());
+            SK_CUDA(cudaEventRecord(s->ev[3], st));
         }
-        SK_CUDA(cudaEventRecord(s->ev[1], st));
-        k_iis_warp<<<warp_blocks, kWarpThreads, 0, st>>>(aw); note_launch();
-        SK_CUDA(cudaGetLastError());
-        SK_CUDA(cudaEventRecord(s->ev[2], st));
-        k_iis_cta<<<s->cta_slots_alloc, kCtaThreads, 0, st>>>(ac); note_launch();
-        SK_CUDA(cudaGetLastError());
-        SK_CUDA(cudaEventRecord(s->ev[3], st));
         SK_CUDA(cudaMemcpyAsync(&hc, s->ctr, sizeof(SampleCounters), cudaMemcpyDeviceToHost, st));
         SK_CUDA(cudaMemcpyAsync(&hst, s->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
         SK_CUDA(cudaStreamSynchronize(st));
@@ -1103,7 +1325,7 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
         s->last_warp_ms += ms_w;
         s->last_cta_ms += ms_c;
         s->last_sample_ms += ms_t + ms_w + ms_c;
-        s->last_to_warp += thread_tier ? hc.n_to_warp : count;
+        s->last_to_warp += (thread_tier || g->lt) ? hc.n_to_warp : count;
         s->last_deferred += hc.n_to_cta;
         s->last_passes += 1;
         if (hc.novf == 0) break;
@@ -1111,7 +1333,8 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
         // completed sample, all of which lie below the old capacity) and
         // rerun exactly the samples that failed
         const uint64_t old_cap = s->arena_cap;
-        const uint64_t new_cap = old_cap * 2 + (uint64_t)kPackArenaChunk * thread_blocks * (kPackBlock / 32) +
+        const uint64_t new_cap = old_cap * 2 + (uint64_t)kLaneArenaChunk * lane_blocks * (kLaneBlock / 32) +
+                                 (uint64_t)kLaneArenaChunk * lt_blocks * (kLtBlock / 32) +
                                  (uint64_t)kArenaChunk * warp_blocks * (kWarpThreads / 32);
         rc = [&]() -> int {
             SK_CUDA(grow_copy(&s->arena, old_cap, new_cap, st));
@@ -1211,13 +1434,15 @@ int sketch_sample_to_size(skis_sketch* s, uint64_t target, uint64_t max_count, c
 // time is compared.
 int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* cand_ms, int cand_cap, int* ncand,
                     std::string* err) {
-    static const uint32_t kDeg[] = {0, 32, 64, 128, 256, 1024};
-    static const uint32_t kSteps[] = {64, 128, 256};
+    static const uint32_t kDeg[] = {0, 64, 128, 256, 512, 1024};
+    static const uint32_t kSteps[] = {128, 256, 1024};
     skis_sketch tmp;
     tmp.g = s->g;
     tmp.seed = s->seed;
     tmp.retry_cap = s->retry_cap;
     tmp.ris = s->ris;
+    tmp.bucket = s->bucket;
+    tmp.thread_max_retries = s->thread_max_retries;
     tmp.cta_slots = s->cta_slots;
     tmp.warp_blocks = s->warp_blocks;
     tmp.thread_blocks = s->thread_blocks;

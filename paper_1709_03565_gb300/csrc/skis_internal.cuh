@@ -16,7 +16,7 @@ constexpr uint32_t kSentinel = 0xFFFFFFFFu;  // threshold meaning "always live"
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Philox counter domains: one independent stream per use of randomness.
-enum : uint32_t { kDomSrc = 1, kDomFirst = 2, kDomBfs = 3, kDomWeight = 4 };
+enum : uint32_t { kDomSrc = 1, kDomFirst = 2, kDomBfs = 3, kDomWeight = 4, kDomLt = 5, kDomBucket = 6 };
 
 // Per-vertex in-row record, one 16-byte load on the hot path: CSR offset of
 // the row, its length d_in(v) and, for row-uniform models (WC), the row's
@@ -160,6 +160,11 @@ struct skis_graph {
     int32_t s = 0, f = 0;       // gamma~ = w / 2^f, s = 62 - f
     uint64_t W = 0;             // sum of w
     int row_uniform = 0;        // thresholds live in RowInfo.tau (WC)
+    int lt = 0;                 // Linear Threshold model: w_v = sum of the row's weights, f = 32
+    uint64_t* lt_cum = nullptr; // LT with per-edge thresholds: exclusive running sums of the
+                                // weights tau' (2^32 for the sentinel) in CSR order, m + 1
+    uint64_t* chain = nullptr;  // bucket first step: the fixed-point chain Q after each in-edge
+                                // of its row (m), built on first use
     uint64_t* off = nullptr;    // n+1 CSR offsets
     skis::RowInfo* rows = nullptr;     // n
     int32_t* src = nullptr;     // m_pad, CSR order, padding = 0
@@ -216,6 +221,7 @@ struct skis_sketch {
     int thread_blocks = 0;               // 0 = automatic
     uint32_t thread_max_deg = 256;       // longest in-row the thread tier expands (0 = tier off)
     uint32_t thread_max_steps = 256;     // edge quads per sample in the thread tier
+    uint32_t thread_max_retries = 32;    // rejected rounds in the thread tier before the warp tier
     // last-call statistics
     uint64_t last_to_warp = 0, last_deferred = 0, last_passes = 0;
     double last_thread_ms = 0, last_warp_ms = 0, last_cta_ms = 0, last_sample_ms = 0;
@@ -226,6 +232,7 @@ struct skis_sketch {
     uint64_t inv_T = 0;                  // T when the index was built (0 = none)
     int query_index = 0;                 // 0 auto (use the index if built), 1 always, 2 never
     int ris = 0;                         // plain RIS samples (uniform source, n Cov / T estimator)
+    int bucket = 0;                      // first step in bucket form (Eq. probn) instead of rejection
     // query / greedy scratch (allocated on first use)
     uint64_t* smask = nullptr;           // T per-sample query bits (inverted-index path)
     uint64_t smask_cap = 0;
@@ -274,6 +281,7 @@ __global__ void k_estimate(const int64_t* __restrict__ off, const int32_t* __res
 // Builds every device structure of g from device edge arrays. Returns a
 // skis_status code; *err receives a message on failure.
 int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const void* d_weights,
-                int model, uint64_t weight_seed, cudaStream_t st, std::string* err);
+                int model, uint64_t weight_seed, int lt, cudaStream_t st, std::string* err);
 void graph_release(skis_graph* g);
+int graph_ensure_chain(const skis_graph* g, cudaStream_t st, std::string* err);
 }  // namespace skis

@@ -310,7 +310,7 @@ def test_autotuned_split_gives_the_same_samples(er_small):
     spec, src, dst, g, o, osk, seed, T = er_small
     s = skis.skis_sketch_create(g, seed)
     tune = skis.skis_sketch_autotune(s, 20_000)
-    assert tune["max_deg"] in (0, 32, 64, 128, 256, 1024) and tune["max_steps"] in (64, 128, 256)
+    assert tune["max_deg"] in (0, 64, 128, 256, 512, 1024) and tune["max_steps"] in (128, 256, 1024)
     assert len(tune["candidate_ms"]) == 16 and all(x > 0 for x in tune["candidate_ms"])
     skis.skis_sample(s, 30_000)
     dev = skis.skis_sketch_export(s, 0, 30_000)
@@ -382,4 +382,47 @@ def test_stop_at_size_matches_oracle(er_small):
     # a reached target appends nothing; max_count bounds a call
     assert skis.skis_sample_to_size(s, target) == (0, T2)
     assert skis.skis_sample_to_size(s, 100 * target, max_count=1000) == (1000, T2 + 1000)
+    s.close()
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_bucket_first_step_matches_oracle(name):
+    # the bucket form of the first step (Eq. probn), on every tier
+    n, src, dst, model, w = GRAPHS[name]()
+    g, o = _pair(n, src, dst, model, w, weight_seed=5)
+    T = 20000
+    seed = 0xB0C0 + len(name)
+    for max_deg in (256, 0):  # with and without the lane tier
+        s = skis.skis_sketch_create(g, seed)
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, 1)
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_THREAD_MAX_DEG, max_deg)
+        skis.skis_sample(s, T)
+        with pytest.raises(skis.SkisError):
+            skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, 0)  # fixed once samples exist
+        dev = skis.skis_sketch_export(s, 0, T)
+        ora = o.sample_ids(seed, np.arange(T, dtype=np.uint64), bucket=True)
+        assert_samples_equal(dev, ora)
+        assert (dev["retries"] == 0).all()
+        s.close()
+    g.close()
+
+
+def test_bucket_first_step_full_er_workload(er_small):
+    spec, src, dst, g, o, osk, seed, T = er_small
+    s = skis.skis_sketch_create(g, seed)
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, 1)
+    skis.skis_sample(s, T)
+    st = skis.skis_sketch_stats(s)
+    assert st["deferred"] > 0 and st["retries"] == 0  # the CTA tier took part
+    ref = oracle.OracleSketch(o, seed, T, bucket=True)
+    a = ref.arrays()
+    dev = skis.skis_sketch_export(s, 0, T)
+    ora = dict(src=a["src"], retries=a["retries"], len=np.diff(a["off"]), coins=a["coins"],
+               member_off=a["off"], members=a["mem"])
+    assert_samples_equal(dev, ora)
+    off, seeds = synth.seed_sets(spec["n"], [10] * 50, 77)
+    cov, est = skis.skis_estimate(s, off, seeds)
+    ocov, oest = ref.coverage(off, seeds)
+    assert np.array_equal(cov, ocov)
+    np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
     s.close()

@@ -194,3 +194,47 @@ def test_bfs_coin_boundary_is_strict():
         assert res[0][1] == {0, 1} and res[1][1] == {0, 1, 2}
         checked += 1
     assert checked >= 20
+
+
+@pytest.mark.parametrize("kind", ["mixed", "wc", "tri"])
+def test_bucket_first_step_has_the_iis_law(kind):
+    """The bucket form of the first step (Eq. probn) draws from the same law
+    as rejection (Lemma 2), without retries."""
+    n, src, dst, p, model = _tiny_graph(kind)
+    g = oracle.OracleGraph(n, src, dst, weights=p, model=model, weight_seed=3)
+    a = g.arrays()
+    probs = [p_eff(t) for t in a["tau"]]
+    dst_csr = np.repeat(np.arange(n), np.diff(a["off"])).tolist()
+    law = iis_law(n, a["src"].tolist(), dst_csr, probs, a["w"].tolist(), g.W)
+    T = 300_000
+    out = g.sample_ids(0x4321 + len(kind), np.arange(T, dtype=np.uint64), bucket=True)
+    assert (out["retries"] == 0).all() and (out["status"] == 0).all()
+    deg = np.diff(a["off"])
+    mo, mem = out["member_off"], out["members"]
+    cnt = Counter()
+    for t in range(T):
+        cnt[(int(out["src"][t]), frozenset(mem[mo[t]:mo[t + 1]].tolist()))] += 1
+    assert all(len(R) >= 2 for (_, R) in cnt) and set(cnt) <= set(law)
+    for t in range(0, T, 1009):
+        assert out["coins"][t] == deg[mem[mo[t]:mo[t + 1]]].sum()
+    exp = {k: float(v) * T for k, v in law.items()}
+    big = [k for k in exp if exp[k] >= 20]
+    small = [k for k in exp if exp[k] < 20]
+    obs = [cnt.get(k, 0) for k in big] + [sum(cnt.get(k, 0) for k in small)]
+    ex = [exp[k] for k in big] + [sum(exp[k] for k in small)]
+    if ex[-1] == 0:
+        obs, ex = obs[:-1], ex[:-1]
+    obs, ex = np.array(obs, float), np.array(ex, float)
+    chi2 = ((obs - ex) ** 2 / ex).sum()
+    dof = len(ex) - 1
+    assert chi2 < dof + 5 * np.sqrt(2 * dof), (chi2, dof)
+
+
+def test_bucket_first_step_on_a_single_in_edge_row():
+    # a source with one in-edge: the bucket is that edge, whatever its weight
+    g = oracle.OracleGraph(3, [1, 2], [0, 1], weights=np.array([0.001, 0.5]), model=oracle.W_P)
+    out = g.sample_ids(5, np.arange(2000, dtype=np.uint64), bucket=True)
+    mo, mem = out["member_off"], out["members"]
+    for t in range(2000):
+        R = mem[mo[t]:mo[t + 1]].tolist()
+        assert R[:2] == [out["src"][t], out["src"][t] + 1]
