@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD,
                     help=f"{WORKLOAD} (the benchmark line) or rmat-2^25-wc (bounded-sample rates)")
     ap.add_argument("--samples", type=int, default=200_000, help="samples of the bounded R-MAT run")
+    ap.add_argument("--first-step", default="bucket", choices=["bucket", "rejection"],
+                    help="form of Alg. 1's conditioned first step (Eq. probn buckets, or rejection rounds)")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step and exit (the command profiled with ncu)")
     return ap.parse_args()
@@ -142,15 +144,16 @@ def _peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def _traffic_per_sample():
+def _traffic_per_sample(first_step: str):
     """Measured DRAM bytes per sample of the sampling tiers from the
-    committed ncu summary, if it was taken on the current kernel source."""
+    committed ncu summary, if it was taken on the current kernel source and
+    the same form of the first step."""
     path = os.path.join(ROOT, "profiles", "iis_sampler_dram.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     src = open(os.path.join(ROOT, "paper_1709_03565_gb300", "csrc", "sample.cu"), "rb").read()
-    if d.get("sample_cu_sha256") != hashlib.sha256(src).hexdigest():
+    if d.get("sample_cu_sha256") != hashlib.sha256(src).hexdigest() or d.get("first_step") != first_step:
         return None
     return float(d["dram_bytes_per_sample"])
 
@@ -181,7 +184,7 @@ def run_reference(args, rank, world):
         nonlocal nxt
         ids = np.arange(nxt, nxt + per_step, dtype=np.uint64)
         nxt += per_step
-        out = g.sample_ids(SKETCH_SEED, ids)
+        out = g.sample_ids(SKETCH_SEED, ids, bucket=args.first_step == "bucket")
         return int(out["coins"].sum())
 
     for _ in range(args.warmup):
@@ -197,7 +200,8 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": spec["n"], "m": spec["m"], "samples": spec["samples"],
-                   "k": spec["k"], "step": f"{per_step} consecutive sample ids of the workload"},
+                   "k": spec["k"], "step": f"{per_step} consecutive sample ids of the workload",
+                   "first_step": args.first_step},
         "sampled_edges_per_s": coins / dt,
         "cpu_baseline": {"value": value, "unit": "RR sets/s", "cores": 1, "kind": "oracle",
                          "sample": f"{per_step} sample ids per step, single-threaded C oracle"},
@@ -374,9 +378,12 @@ def main():
     arena_hint = int(T * 5.5)
     torch.cuda.synchronize()
 
+    first_step = 1 if args.first_step == "bucket" else 0
+
     def step():
         g = skis.skis_load_graph(n, d_src, d_dst, d_p, skis.SKIS_W_EXPLICIT_P, stream=stream)
         s = skis.skis_sketch_create(g, seed, arena_hint, stream=stream)
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, first_step)
         skis.skis_sample(s, T, stream=stream)
         sd, sc, se = skis.skis_greedy_maxcover(s, k, stream=stream)  # builds the inverted index
         skis.skis_estimate(s, d_off, d_seeds, d_cov, d_est, stream=stream)  # walks it
@@ -438,6 +445,7 @@ def main():
     def step_e2e():
         g = skis.skis_load_graph(n, h_src, h_dst, h_p, skis.SKIS_W_EXPLICIT_P, stream=stream)
         s = skis.skis_sketch_create(g, seed, arena_hint, stream=stream)
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, first_step)
         skis.skis_sample(s, T, stream=stream)
         out = skis.skis_greedy_maxcover(s, k, stream=stream)
         skis.skis_estimate(s, h_off, h_seeds, h_cov, h_est, stream=stream)
@@ -466,15 +474,15 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel (warp-tier IIS sampler)
+    # ---- roofline of the dominant kernels (the three IIS sampling tiers)
     peak, peak_kind = _peaks()
     # the three sampling launches of one skis_sample call (thread, warp and
     # CTA tiers) together produce the whole sketch
     alg = algorithmic_bytes(T, entries, coins, per_edge_tau=True)
     achieved = alg / (sample_ms / 1e3) / 1e9
-    tps = _traffic_per_sample()
+    tps = _traffic_per_sample(args.first_step)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tps * T if tps is not None else None), "kernel": "k_iis_thread + k_iis_warp + k_iis_cta",
+                "traffic": (tps * T if tps is not None else None), "kernel": "k_iis_lane + k_iis_warp + k_iis_cta",
                 "algorithmic_bytes": alg, "kernel_ms": sample_ms, "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
 
     # ---- influence-oracle serving (queries/s, p50/p99)
@@ -489,7 +497,7 @@ def main():
         og = oracle.OracleGraph(n, src, dst, weights=p, model=oracle.W_P)
         done, t0 = 0, time.perf_counter()
         while time.perf_counter() - t0 < args.cpu_seconds:
-            og.sample_ids(seed, np.arange(done, done + 50_000, dtype=np.uint64))
+            og.sample_ids(seed, np.arange(done, done + 50_000, dtype=np.uint64), bucket=args.first_step == "bucket")
             done += 50_000
         dt = time.perf_counter() - t0
         cpu = {"value": done / dt, "unit": "RR sets/s", "cores": 1, "kind": "oracle",
@@ -502,6 +510,7 @@ def main():
         "config": {"workload": WORKLOAD, "graph": "Chung-Lu directed, exponent 2.1, TRI probabilities",
                    "n": n, "m": m, "samples": T, "queries": QUERIES, "query_size": QUERY_SIZE, "k": k,
                    "l2": "inputs larger than L2 (edge arrays 160 MB, arena ~170 MB, rebuilt every step)",
+                   "first_step": args.first_step + (" (Eq. probn)" if args.first_step == "bucket" else " rounds"),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "sampled_edges_per_s": world * args.steps * coins / (elapsed_ms / 1e3),
         "sampling_only": {"rr_sets_per_s": T / (sample_ms / 1e3), "edges_per_s": coins / (sample_ms / 1e3),

@@ -63,6 +63,27 @@ __device__ __forceinline__ void add_aggregated(uint32_t* counter, int32_t u, int
     }
 }
 
+// Greedy's cover walk: a block-local table merges the decrements of vertices
+// that recur across the samples a seed covers (hubs), so that each such
+// vertex takes one global atomic per block and round instead of one per
+// warp step. A vertex that finds its slot held by another goes straight to
+// the global counter.
+constexpr int kHotBits = 10;
+constexpr int kHotSlots = 1 << kHotBits;
+constexpr uint32_t kHotEmpty = 0xFFFFFFFFu;
+
+__device__ __forceinline__ void sub_merged(uint32_t* counter, int32_t u, uint32_t* hkey, uint32_t* hcnt) {
+    const unsigned active = __activemask();
+    const unsigned peers = __match_any_sync(active, u);
+    if ((threadIdx.x & 31) != __ffs(peers) - 1) return;
+    const uint32_t c = (uint32_t)__popc(peers);
+    const uint32_t slot = ((uint32_t)u * 2654435761u) >> (32 - kHotBits);
+    uint32_t old = hkey[slot];
+    if (old == kHotEmpty) old = atomicCAS(&hkey[slot], kHotEmpty, (uint32_t)u);
+    if (old == kHotEmpty || old == (uint32_t)u) atomicAdd(&hcnt[slot], c);
+    else atomicSub(&counter[u], c);
+}
+
 // ------------------------------------------------------------- coverage
 __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
                             int32_t qn, int64_t n, uint64_t* __restrict__ qmask, DevStatus* st) {
@@ -380,17 +401,12 @@ __global__ void __launch_bounds__(kCovThreads) k_fill_inverted(const uint64_t* _
     }
 }
 
-struct GreedyState {
-    unsigned long long done;     // blocks finished in the current argmax round
-    unsigned long long cov;      // Cov_R(S)
-    unsigned long long sum_c;    // sum_{v in S} (2^f - w_v), < 2^61 for |S| <= n
-    unsigned long long pad;
-};
-
 struct KeyId {
     u128 key;
     uint32_t id;
     uint32_t valid;
+    uint32_t d;    // Delta of the vertex (carried with the key)
+    uint32_t pad;
 };
 
 __device__ __forceinline__ bool better(const KeyId& a, const KeyId& b) {
@@ -404,6 +420,8 @@ __device__ __forceinline__ KeyId shfl_down_keyid(const KeyId& x, int d) {
     y.key = shfl_down_u128(x.key, d);
     y.id = __shfl_down_sync(kFull, x.id, d);
     y.valid = __shfl_down_sync(kFull, x.valid, d);
+    y.d = __shfl_down_sync(kFull, x.d, d);
+    y.pad = 0;
     return y;
 }
 
@@ -427,14 +445,6 @@ __device__ KeyId block_best(KeyId b, KeyId* s_part) {
     return b;  // valid in thread 0
 }
 
-// All k rounds of Alg. 3 in one cooperative launch. Per round: every block
-// scans its share of the vertices for the exact key Delta_v W + T (2^f - w_v)
-// (v outside S, ties to the lowest id); the last block to finish commits the
-// winner; a grid barrier; every warp walks the winner's inverted list,
-// marking uncovered samples and decrementing their members' Delta; a grid
-// barrier. Every block executes the same sequence of barriers. Data that
-// other blocks change during the launch (Delta, S, the committed seed) is
-// read through L2 (ld.global.cg), never from a possibly stale L1 line.
 struct GreedyArgs {
     const uint64_t* w;
     uint8_t* inS;
@@ -450,12 +460,12 @@ struct GreedyArgs {
     const int32_t* arena;
     uint32_t* covered;
     KeyId* partial;
-    GreedyState* gs;
     int32_t* seeds;
     int64_t* cov_out;
     double* est_out;
     int ris;
 };
+
 
 __device__ __forceinline__ KeyId ldcg_keyid(const KeyId* p) {
     const unsigned long long* q = reinterpret_cast<const unsigned long long*>(p);
@@ -464,65 +474,83 @@ __device__ __forceinline__ KeyId ldcg_keyid(const KeyId* p) {
     const unsigned long long tail = __ldcg(q + 2);
     c.id = (uint32_t)tail;
     c.valid = (uint32_t)(tail >> 32);
+    c.d = (uint32_t)__ldcg(q + 3);
+    c.pad = 0;
     return c;
 }
 
-__global__ void __launch_bounds__(kCovThreads) k_greedy_rounds(GreedyArgs a) {
+// All k rounds of Alg. 3 in one cooperative launch, one block per SM. Per
+// round: every block scans its share of the vertices for the exact key
+// Delta_v W + T (2^f - w_v) (v outside S, ties to the lowest id) and writes
+// its best; a grid barrier; every block reduces all the blocks' bests itself
+// (the same winner everywhere, no atomic hand-off) and block 0 records it;
+// every warp walks the winner's inverted list, marking uncovered samples and
+// decrementing their members' Delta (hub decrements merged per block); a grid
+// barrier. Every block executes the same sequence of barriers. Data that
+// other blocks change during the launch (Delta, the block bests) is read
+// through L2 (ld.global.cg), never from a possibly stale L1 line.
+constexpr int kGreedyThreads = 1024;
+
+__global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs a) {
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
-    __shared__ KeyId s_part[kCovThreads / 32];
-    __shared__ bool s_last;
+    __shared__ KeyId s_part[kGreedyThreads / 32];
+    __shared__ KeyId s_win;
+    __shared__ uint32_t s_hkey[kHotSlots], s_hcnt[kHotSlots];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t one_f = 1ull << a.f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int i = threadIdx.x; i < kHotSlots; i += blockDim.x) {
+        s_hkey[i] = kHotEmpty;
+        s_hcnt[i] = 0;
+    }
+    uint64_t cov = 0, sum_c = 0;  // running totals, kept by block 0
+    __syncthreads();
     for (int32_t round = 0; round < a.k; ++round) {
         KeyId best{0, 0xFFFFFFFFu, 0};
         for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
-            if (__ldcg(a.inS + v)) continue;
-            const u128 dv = (u128)__ldcg(a.delta + v);
-            const KeyId c{a.ris ? dv : dv * a.W + (u128)a.T * (one_f - a.w[v]), (uint32_t)v, 1u};
+            if (a.inS[v]) continue;  // only this block's own threads write its vertices' flags
+            const uint32_t d = __ldcg(a.delta + v);
+            const u128 dv = (u128)d;
+            const KeyId c{a.ris ? dv : dv * a.W + (u128)a.T * (one_f - a.w[v]), (uint32_t)v, 1u, d, 0u};
             if (better(c, best)) best = c;
         }
         best = block_best(best, s_part);
-        if (threadIdx.x == 0) {
-            a.partial[blockIdx.x] = best;
-            __threadfence();
-            s_last = atomicAdd(&a.gs->done, 1ull) == gridDim.x - 1;
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
+        if (threadIdx.x == 0) a.partial[blockIdx.x] = best;
+        grid.sync();
+        if (wib == 0) {
             KeyId b{0, 0xFFFFFFFFu, 0};
-            for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+            for (unsigned i = lane; i < gridDim.x; i += 32) {
                 const KeyId c = ldcg_keyid(a.partial + i);
                 if (better(c, b)) b = c;
             }
-            __syncthreads();
-            b = block_best(b, s_part);
-            if (threadIdx.x == 0) {
-                const uint32_t v = b.id;
-                a.inS[v] = 1;
-                // the committing block differs between rounds: running
-                // totals are read through L2 as well
-                const unsigned long long cov = __ldcg(&a.gs->cov) + __ldcg(a.delta + v);
-                const unsigned long long sum_c = __ldcg(&a.gs->sum_c) + (one_f - a.w[v]);
-                a.gs->cov = cov;
-                a.gs->sum_c = sum_c;
-                a.gs->done = 0;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                const KeyId o = shfl_down_keyid(b, d);
+                if (better(o, b)) b = o;
+            }
+            if (lane == 0) s_win = b;
+        }
+        __syncthreads();
+        const uint32_t v = s_win.id;
+        if (threadIdx.x == 0) {
+            const int64_t owner = (int64_t)(v % (uint64_t)stride) / blockDim.x;
+            if (owner == blockIdx.x) a.inS[v] = 1;
+            if (blockIdx.x == 0) {
+                cov += s_win.d;  // Delta_v as scanned, before any walk of this round
+                sum_c += one_f - a.w[v];
                 a.seeds[round] = (int32_t)v;
                 a.cov_out[round] = (int64_t)cov;
                 const u128 N = a.ris ? (u128)cov * (uint64_t)a.n : (u128)cov * a.W + (u128)a.T * sum_c;
                 const u128 D = a.ris ? (u128)a.T : (u128)a.T << a.f;
                 a.est_out[round] = u128_to_double(N) / u128_to_double(D);
-                __threadfence();
             }
         }
-        grid.sync();
+        __syncthreads();
         // cover the uncovered samples of the committed vertex
-        const int32_t v = __ldcg(a.seeds + round);
         const uint64_t lo = a.inv_off[v], cnt = a.inv_off[v + 1] - lo;
-        const uint64_t nwarps = (uint64_t)gridDim.x * (kCovThreads / 32);
-        for (uint64_t base = ((uint64_t)blockIdx.x * (kCovThreads / 32) + wib) * 32; base < cnt;
+        const uint64_t nwarps = (uint64_t)gridDim.x * (kGreedyThreads / 32);
+        for (uint64_t base = ((uint64_t)blockIdx.x * (kGreedyThreads / 32) + wib) * 32; base < cnt;
              base += nwarps * 32) {
             const uint64_t x = base + lane;
             uint64_t off = 0;
@@ -535,7 +563,16 @@ __global__ void __launch_bounds__(kCovThreads) k_greedy_rounds(GreedyArgs a) {
                     len = a.h_len[j];
                 }
             }
-            warp_members(off, len, a.arena, [&](int, int32_t u) { add_aggregated(a.delta, u, -1); });
+            warp_members(off, len, a.arena, [&](int, int32_t u) { sub_merged(a.delta, u, s_hkey, s_hcnt); });
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kHotSlots; i += blockDim.x) {
+            const uint32_t key = s_hkey[i];
+            if (key != kHotEmpty) {
+                atomicSub(&a.delta[key], s_hcnt[i]);
+                s_hkey[i] = kHotEmpty;
+                s_hcnt[i] = 0;
+            }
         }
         grid.sync();
     }
@@ -598,25 +635,26 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
     uint32_t *delta = nullptr, *covered = nullptr;
     uint8_t* inS = nullptr;
     KeyId* partial = nullptr;
-    GreedyState* gs = nullptr;
     int32_t* d_seeds = nullptr;
     int64_t* d_cov = nullptr;
     double* d_est = nullptr;
     auto body = [&]() -> int {
         int per_sm = 0;
-        CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_rounds, kCovThreads, 0));
-        const int gblocks = sm_count() * std::max(1, std::min(per_sm, 4));
+        CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_greedy_rounds, kGreedyThreads, 0));
+        if (per_sm < 1) {
+            *err = "skis_greedy_maxcover: the cooperative kernel does not fit on an SM";
+            return SKIS_ERR_CUDA;
+        }
+        const int gblocks = sm_count();  // one block per SM
         CV_CUDA(dev_alloc_t(&delta, (size_t)n, st));
         CV_CUDA(dev_alloc_t(&inS, (size_t)n, st));
         CV_CUDA(dev_alloc_t(&covered, (size_t)((T + 31) / 32), st));
         CV_CUDA(dev_alloc_t(&partial, (size_t)gblocks, st));
-        CV_CUDA(dev_alloc_t(&gs, 1, st));
         CV_CUDA(dev_alloc_t(&d_seeds, (size_t)k, st));
         CV_CUDA(dev_alloc_t(&d_cov, (size_t)k, st));
         CV_CUDA(dev_alloc_t(&d_est, (size_t)k, st));
         CV_CUDA(cudaMemsetAsync(inS, 0, (size_t)n, st));
         CV_CUDA(cudaMemsetAsync(covered, 0, (size_t)((T + 31) / 32) * sizeof(uint32_t), st));
-        CV_CUDA(cudaMemsetAsync(gs, 0, sizeof(GreedyState), st));
         // Delta_R(v, {}) = number of samples containing v = length of v's list
         const int b1 = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8));
         k_delta_from_index<<<b1, 256, 0, st>>>(s->inv_off, n, delta); note_launch();
@@ -637,13 +675,12 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
         ga.arena = s->arena;
         ga.covered = covered;
         ga.partial = partial;
-        ga.gs = gs;
         ga.seeds = d_seeds;
         ga.cov_out = d_cov;
         ga.est_out = d_est;
         ga.ris = s->ris;
         void* kargs[] = {&ga};
-        CV_CUDA(cudaLaunchCooperativeKernel((const void*)k_greedy_rounds, gblocks, kCovThreads, kargs, 0, st));
+        CV_CUDA(cudaLaunchCooperativeKernel((const void*)k_greedy_rounds, gblocks, kGreedyThreads, kargs, 0, st));
         note_launch();
         CV_CUDA(cudaMemcpyAsync(h_seeds, d_seeds, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         if (h_cov) CV_CUDA(cudaMemcpyAsync(h_cov, d_cov, (size_t)k * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -656,7 +693,6 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
     dev_free(covered, st);
     dev_free(inS, st);
     dev_free(partial, st);
-    dev_free(gs, st);
     dev_free(d_seeds, st);
     dev_free(d_cov, st);
     dev_free(d_est, st);

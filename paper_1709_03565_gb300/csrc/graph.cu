@@ -137,7 +137,19 @@ __global__ void k_chain(const RowInfo* __restrict__ rows, const uint32_t* __rest
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const RowInfo r = rows[v];
         uint64_t Q = 1ull << 62;
-        for (uint32_t k = 0; k < r.deg; ++k) {
+        uint32_t k = 0;
+        for (; k + 8 <= r.deg; k += 8) {  // thresholds loaded 8 at a time ahead of the product
+            uint32_t t[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) t[i] = csr_tau ? csr_tau[r.off + k + i] : r.tau;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (t[i] == kSentinel) Q = 0;
+                else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t[i])) >> 32);
+                chain[r.off + k + i] = Q;
+            }
+        }
+        for (; k < r.deg; ++k) {
             const uint32_t t = csr_tau ? csr_tau[r.off + k] : r.tau;
             if (t == kSentinel) Q = 0;
             else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t)) >> 32);

@@ -258,23 +258,26 @@ def test_single_vertex_and_edgeless_graphs():
 
 
 # --------------------------------------------------- full-size workload
-@pytest.fixture(scope="module")
-def chunglu_full():
+@pytest.fixture(scope="module", params=["bucket", "rejection"])
+def chunglu_full(request):
     """The 1M-vertex / 10M-edge Chung-Lu TRI workload with 10M samples, in
-    the launch configuration the benchmark uses (defaults)."""
+    the launch configuration the benchmark uses (default tiers, bucket first
+    step), and with the rejection first step."""
     spec, src, dst, p = synth.workload("chunglu-1e6-tri")
     seed = 0x5EED0002
+    bucket = request.param == "bucket"
     g = skis.skis_load_graph(spec["n"], src, dst, p, skis.SKIS_W_EXPLICIT_P)
-    s = skis.skis_sketch_create(g, seed)
+    s = skis.skis_sketch_create(g, seed, int(spec["samples"] * 5.5))
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, 1 if bucket else 0)
     skis.skis_sample(s, spec["samples"])
     o = oracle.OracleGraph(spec["n"], src, dst, weights=p, model=oracle.W_P)
-    yield spec, g, s, o, seed
+    yield spec, g, s, o, seed, bucket
     s.close()
     g.close()
 
 
 def test_full_size_graph_and_sampled_ids(chunglu_full):
-    spec, g, s, o, seed = chunglu_full
+    spec, g, s, o, seed, bucket = chunglu_full
     a, b = skis.skis_graph_export(g), o.arrays()
     for k in ("off", "src", "tau", "perm", "w", "prob", "alias"):
         assert np.array_equal(a[k], b[k]), k
@@ -282,7 +285,7 @@ def test_full_size_graph_and_sampled_ids(chunglu_full):
     dev = skis.skis_sketch_export(s, 0, T)
     rng = np.random.default_rng(0)
     ids = np.unique(np.concatenate([np.arange(2000), np.arange(T - 2000, T), rng.integers(0, T, 30000)]))
-    ora = o.sample_ids(seed, ids.astype(np.uint64))
+    ora = o.sample_ids(seed, ids.astype(np.uint64), bucket=bucket)
     mo = dev["member_off"]
     sub = dict(src=dev["src"][ids], retries=dev["retries"][ids], len=dev["len"][ids], coins=dev["coins"][ids])
     lens = np.diff(mo)[ids]
@@ -292,8 +295,8 @@ def test_full_size_graph_and_sampled_ids(chunglu_full):
 
 
 def test_full_size_greedy_and_coverage(chunglu_full):
-    spec, g, s, o, seed = chunglu_full
-    osk = oracle.OracleSketch(o, seed, spec["samples"])
+    spec, g, s, o, seed, bucket = chunglu_full
+    osk = oracle.OracleSketch(o, seed, spec["samples"], bucket=bucket)
     k = spec["k"]
     sd, sc, se = skis.skis_greedy_maxcover(s, k)
     od, oc, oe = osk.greedy(k)
