@@ -498,6 +498,7 @@ void skis::sketch_release(skis_sketch* s) {
     dev_free(s->inv_off, st);
     dev_free(s->inv, st);
     dev_free(s->smask, st);
+    dev_free(s->vcount, st);
     dev_free(s->qcov, st);
     dev_free(s->qstatus, st);
     for (int i = 0; i < 4; ++i)

@@ -490,6 +490,8 @@ __device__ __forceinline__ KeyId ldcg_keyid(const KeyId* p) {
 // other blocks change during the launch (Delta, the block bests) is read
 // through L2 (ld.global.cg), never from a possibly stale L1 line.
 constexpr int kGreedyThreads = 1024;
+constexpr uint32_t kBigLen = 256;   // covered samples longer than this are walked by the whole block
+constexpr int kBigQueue = 64;
 
 __global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs a) {
     namespace cg = cooperative_groups;
@@ -497,6 +499,9 @@ __global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs 
     __shared__ KeyId s_part[kGreedyThreads / 32];
     __shared__ KeyId s_win;
     __shared__ uint32_t s_hkey[kHotSlots], s_hcnt[kHotSlots];
+    __shared__ uint64_t s_big_off[kBigQueue];
+    __shared__ uint32_t s_big_len[kBigQueue];
+    __shared__ uint32_t s_nbig;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t one_f = 1ull << a.f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -504,16 +509,35 @@ __global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs 
         s_hkey[i] = kHotEmpty;
         s_hcnt[i] = 0;
     }
+    if (threadIdx.x == 0) s_nbig = 0;
     uint64_t cov = 0, sum_c = 0;  // running totals, kept by block 0
     __syncthreads();
     for (int32_t round = 0; round < a.k; ++round) {
         KeyId best{0, 0xFFFFFFFFu, 0};
-        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
-            if (a.inS[v]) continue;  // only this block's own threads write its vertices' flags
-            const uint32_t d = __ldcg(a.delta + v);
-            const u128 dv = (u128)d;
-            const KeyId c{a.ris ? dv : dv * a.W + (u128)a.T * (one_f - a.w[v]), (uint32_t)v, 1u, d, 0u};
-            if (better(c, best)) best = c;
+        // four of the thread's vertices per pass, their loads issued together
+        // (a vertex's S flag is written only by the thread that scans it)
+        for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v0 < a.n; v0 += 4 * stride) {
+            uint8_t in4[4];
+            uint32_t d4[4];
+            uint64_t w4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t v = v0 + q * stride;
+                in4[q] = 1;
+                if (v < a.n) {
+                    in4[q] = a.inS[v];
+                    d4[q] = __ldcg(a.delta + v);
+                    w4[q] = a.w[v];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (in4[q]) continue;
+                const u128 dv = (u128)d4[q];
+                const KeyId c{a.ris ? dv : dv * a.W + (u128)a.T * (one_f - w4[q]), (uint32_t)(v0 + q * stride), 1u,
+                              d4[q], 0u};
+                if (better(c, best)) best = c;
+            }
         }
         best = block_best(best, s_part);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = best;
@@ -548,24 +572,45 @@ __global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs 
         }
         __syncthreads();
         // cover the uncovered samples of the committed vertex
+        // a warp takes spw list entries at a time, spw the power of two that
+        // spreads the list over every warp (up to 32), so a short list is
+        // not walked by a few warps one member at a time
         const uint64_t lo = a.inv_off[v], cnt = a.inv_off[v + 1] - lo;
         const uint64_t nwarps = (uint64_t)gridDim.x * (kGreedyThreads / 32);
-        for (uint64_t base = ((uint64_t)blockIdx.x * (kGreedyThreads / 32) + wib) * 32; base < cnt;
-             base += nwarps * 32) {
+        uint32_t spw = 1;
+        while (spw < 32 && (uint64_t)spw * nwarps < cnt) spw <<= 1;
+        for (uint64_t base = ((uint64_t)blockIdx.x * (kGreedyThreads / 32) + wib) * spw; base < cnt;
+             base += nwarps * spw) {
             const uint64_t x = base + lane;
             uint64_t off = 0;
             uint32_t len = 0;
-            if (x < cnt) {
+            if ((uint32_t)lane < spw && x < cnt) {
                 const uint32_t j = a.inv[lo + x];
                 const uint32_t bit = 1u << (j & 31);
                 if ((atomicOr(&a.covered[j >> 5], bit) & bit) == 0) {
                     off = a.h_off[j];
                     len = a.h_len[j];
+                    if (len > kBigLen) {  // a large sample: the whole block walks it below
+                        const uint32_t q = atomicAdd(&s_nbig, 1u);
+                        if (q < (uint32_t)kBigQueue) {
+                            s_big_off[q] = off;
+                            s_big_len[q] = len;
+                            len = 0;
+                        }
+                    }
                 }
             }
             warp_members(off, len, a.arena, [&](int, int32_t u) { sub_merged(a.delta, u, s_hkey, s_hcnt); });
         }
         __syncthreads();
+        const uint32_t nbig = min(s_nbig, (uint32_t)kBigQueue);
+        for (uint32_t b = 0; b < nbig; ++b) {
+            const uint64_t boff = s_big_off[b];
+            const uint32_t blen = s_big_len[b];
+            for (uint32_t i = threadIdx.x; i < blen; i += blockDim.x) sub_merged(a.delta, a.arena[boff + i], s_hkey, s_hcnt);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_nbig = 0;
         for (int i = threadIdx.x; i < kHotSlots; i += blockDim.x) {
             const uint32_t key = s_hkey[i];
             if (key != kHotEmpty) {
@@ -600,9 +645,13 @@ int sketch_inverted(skis_sketch* s, cudaStream_t st, std::string* err) {
     uint64_t E = 0;
     const int cblocks = coverage_blocks(T);
     CV_CUDA(dev_alloc_t(&cnt, (size_t)n, st));
-    CV_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), st));
-    k_count_members<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, T, s->arena, cnt); note_launch();
-    CV_CUDA(cudaGetLastError());
+    if (s->vcount && s->vcount_ok && s->vcount_T == T) {  // counted while sampling
+        CV_CUDA(cudaMemcpyAsync(cnt, s->vcount, (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    } else {
+        CV_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), st));
+        k_count_members<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, T, s->arena, cnt); note_launch();
+        CV_CUDA(cudaGetLastError());
+    }
     CV_CUDA(scan_u32_to_u64(cnt, s->inv_off, n, st));
     CV_CUDA(cudaMemcpyAsync(&E, s->inv_off + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     CV_CUDA(cudaStreamSynchronize(st));

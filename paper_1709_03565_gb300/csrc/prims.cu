@@ -164,7 +164,7 @@ cudaError_t scan_u128(const u128* in, u128* out, int64_t n, cudaStream_t st) {
 
 // ------------------------------------------------------------- radix sort
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;  // 4096 pairs per tile
+constexpr int kSortItems = 8;  // 2048 pairs per tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys, int64_t n,
@@ -182,21 +182,43 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __r
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_h[threadIdx.x];
 }
 
-// Stable scatter: items of a tile are taken in order in chunks of 256; within
-// a chunk, warp w precedes warp w+1 and lanes rank by lane id among equal
-// digits; the running per-digit base carries across chunks.
+// Stable scatter of one tile. The tile's items are ranked in order (chunks
+// of 256; within a chunk warp w precedes warp w+1 and lanes rank by lane id
+// among equal digits) and placed in shared memory in digit order; then the
+// tile is written out from shared memory, so that the items of one digit
+// leave as one contiguous run (coalesced) at the digit's global base.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out, int64_t n, int shift, const uint64_t* __restrict__ offs, int nblocks) {
+    uint32_t* __restrict__ vals_out, int64_t n, int shift, const uint32_t* __restrict__ hist,
+    const uint64_t* __restrict__ offs, int nblocks) {
+    __shared__ uint64_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_wcnt[kSortThreads / 32][256];
-    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_start[256];  // digit start within the tile
+    __shared__ uint32_t s_run[256];    // items of the digit placed so far
+    __shared__ uint32_t s_wsum[kSortThreads / 32];
     __shared__ uint64_t s_base[256];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     s_base[tid] = offs[(int64_t)tid * nblocks + blockIdx.x];
+    // exclusive scan of this tile's digit counts
+    const uint32_t cnt = hist[(int64_t)tid * nblocks + blockIdx.x];
+    uint32_t x = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) s_wsum[wid] = x;
 #pragma unroll
     for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][tid] = 0;
+    s_run[tid] = 0;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < wid; ++w) before += s_wsum[w];
+    s_start[tid] = before + x - cnt;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    const int tile_n = (int)min((int64_t)kSortTile, n - base);
     for (int c = 0; c < kSortItems; ++c) {
         const int64_t i = base + (int64_t)c * kSortThreads + tid;
         const bool valid = i < n;
@@ -207,27 +229,31 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         const int rank = __popc(peers & lanemask_lt());
         if (valid && lane == __ffs(peers) - 1) s_wcnt[wid][d] = (uint32_t)__popc(peers);
         __syncthreads();
-        {
-            uint32_t run = 0;
+        uint32_t run = 0;  // thread tid: digit tid's per-warp offsets within the chunk
 #pragma unroll
-            for (int w = 0; w < kSortThreads / 32; ++w) {
-                const uint32_t cnt = s_wcnt[w][tid];
-                s_wcnt[w][tid] = run;
-                run += cnt;
-            }
-            s_tot[tid] = run;
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const uint32_t c2 = s_wcnt[w][tid];
+            s_wcnt[w][tid] = run;
+            run += c2;
         }
         __syncthreads();
         if (valid) {
-            const uint64_t pos = s_base[d] + s_wcnt[wid][d] + (uint32_t)rank;
-            keys_out[pos] = key;
-            vals_out[pos] = val;
+            const uint32_t pos = s_start[d] + s_run[d] + s_wcnt[wid][d] + (uint32_t)rank;
+            s_keys[pos] = key;
+            s_vals[pos] = val;
         }
         __syncthreads();
-        s_base[tid] += s_tot[tid];
+        s_run[tid] += run;
 #pragma unroll
         for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][tid] = 0;
         __syncthreads();
+    }
+    for (int i = tid; i < tile_n; i += kSortThreads) {
+        const uint64_t key = s_keys[i];
+        const uint32_t d = (uint32_t)((key >> shift) & 255u);
+        const uint64_t pos = s_base[d] + (uint64_t)(i - (int)s_start[d]);
+        keys_out[pos] = key;
+        vals_out[pos] = s_vals[i];
     }
 }
 
@@ -257,7 +283,7 @@ cudaError_t radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, u
         k_radix_hist<<<nb, kSortThreads, 0, st>>>(ksrc, n, 8 * p, hist, nb); note_launch();
         e = scan_u32_to_u64(hist, offs, (int64_t)nb * 256, st);
         if (e != cudaSuccess) break;
-        k_radix_scatter<<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, n, 8 * p, offs, nb); note_launch();
+        k_radix_scatter<<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, n, 8 * p, hist, offs, nb); note_launch();
         e = cudaGetLastError();
         ksrc = kdst;
         vsrc = vdst;

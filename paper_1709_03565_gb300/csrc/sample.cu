@@ -76,7 +76,13 @@ struct SampleArgs {
     const uint4* srcrec;  // lane tier: source record per input t (k_sources)
     const uint64_t* lt_cum;  // LT graphs with per-edge thresholds: running weight sums, else nullptr
     const uint64_t* chain;   // bucket first step: the gamma chain per in-edge, else nullptr
+    uint32_t* vcount;        // per-vertex member counts kept for the inverted index, or nullptr
 };
+
+// a member written to the arena counts towards its vertex's list length
+__device__ __forceinline__ void count_member(const SampleArgs& a, int32_t u) {
+    if (a.vcount) atomicAdd(&a.vcount[u], 1u);
+}
 
 __device__ __forceinline__ uint64_t input_count(const SampleArgs& a) {
     return a.count_dev ? (uint64_t)*a.count_dev : a.count;
@@ -441,7 +447,11 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                         m &= m - 1;
                         const uint64_t at_s = shfl_u64(at, sl);
                         const uint32_t len_s = __shfl_sync(kFull, len, sl);
-                        if ((uint32_t)lane < len_s) a.arena[at_s + lane] = mq[sl * kLaneStride + lane];
+                        if ((uint32_t)lane < len_s) {
+                            const int32_t u = mq[sl * kLaneStride + lane];
+                            a.arena[at_s + lane] = u;
+                            count_member(a, u);
+                        }
                     }
                     chunk_pos += total;
                 }
@@ -675,7 +685,10 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
                 chunk_pos = base;
                 chunk_end = base + size;
             }
-            for (uint32_t i = lane; i < len; i += 32) a.arena[chunk_pos + i] = queue[i];
+            for (uint32_t i = lane; i < len; i += 32) {
+                a.arena[chunk_pos + i] = queue[i];
+                count_member(a, queue[i]);
+            }
             if (lane == 0) {
                 a.h_off[j] = chunk_pos;
                 a.h_len[j] = len;
@@ -878,7 +891,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
         const unsigned long long base = s_base;
         for (uint32_t i = threadIdx.x; i < len; i += kCtaThreads) {
             const int32_t u = queue[i];
-            if (base != ~0ull) a.arena[base + i] = u;
+            if (base != ~0ull) {
+                a.arena[base + i] = u;
+                count_member(a, u);
+            }
             bitmap[(uint32_t)u >> 5] = 0;  // restore the all-zero bitmap
         }
         __syncthreads();
@@ -1018,7 +1034,10 @@ __global__ void __launch_bounds__(kLtBlock) k_lt_walk(SampleArgs a) {
             if (done) {
                 if (fits) {
                     const uint64_t at = chunk_pos + (incl - mylen);
-                    for (uint32_t i = 0; i < len; ++i) a.arena[at + i] = mq[i][lane];
+                    for (uint32_t i = 0; i < len; ++i) {
+                        a.arena[at + i] = mq[i][lane];
+                        count_member(a, mq[i][lane]);
+                    }
                     a.h_off[j] = at;
                     a.h_len[j] = len;
                     a.h_src[j] = v;
@@ -1078,7 +1097,10 @@ __global__ void __launch_bounds__(32) k_lt_long(SampleArgs a) {
         const bool fits = base + len <= a.arena_cap;
         for (uint32_t i = lane; i < len; i += 32) {
             const int32_t u = queue[i];
-            if (fits) a.arena[base + i] = u;
+            if (fits) {
+                a.arena[base + i] = u;
+                count_member(a, u);
+            }
             bitmap[(uint32_t)u >> 5] = 0;  // restore the all-zero bitmap
         }
         if (lane == 0) {
@@ -1241,6 +1263,18 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.bitmap_words = s->bitmap_words;
     base.srcrec = nullptr;
     base.lt_cum = g->lt_cum;
+    // per-vertex member counts, kept while they describe exactly samples
+    // [0, T): invalid until this call succeeds
+    const bool counting = s->vcount_ok && s->vcount_T == s->T;
+    s->vcount_ok = false;
+    base.vcount = nullptr;
+    if (counting) {
+        if (!s->vcount) {
+            SK_CUDA(dev_alloc_t(&s->vcount, (size_t)g->n, st));
+            SK_CUDA(cudaMemsetAsync(s->vcount, 0, (size_t)g->n * sizeof(uint32_t), st));
+        }
+        base.vcount = s->vcount;
+    }
     base.chain = nullptr;
     if (s->bucket && !s->ris && !g->lt) {
         rc = graph_ensure_chain(g, st, err);
@@ -1355,6 +1389,10 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
         ++pass;
     }
     s->T += count;
+    if (counting) {
+        s->vcount_ok = true;
+        s->vcount_T = s->T;
+    }
     if (hst.flags & kStRetry) {
         *err = "skis_sample: a conditioned first step reached the retry cap (" + std::to_string(s->retry_cap) +
                " rounds) at sample id " + std::to_string(hst.first_bad) + "; failed samples are empty";
@@ -1416,6 +1454,7 @@ int sketch_sample_to_size(skis_sketch* s, uint64_t target, uint64_t max_count, c
             SK_CUDA(cudaMemcpyAsync(&upto, pre + at + 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
             SK_CUDA(cudaStreamSynchronize(st));
             s->T = T0 + at + 1;  // later samples of the batch are dropped
+            s->vcount_ok = false;  // the counts include them
             *appended += at + 1;
             cur += upto;
         } else {
@@ -1441,6 +1480,7 @@ int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* can
     tmp.seed = s->seed;
     tmp.retry_cap = s->retry_cap;
     tmp.ris = s->ris;
+    tmp.vcount_ok = false;
     tmp.bucket = s->bucket;
     tmp.thread_max_retries = s->thread_max_retries;
     tmp.cta_slots = s->cta_slots;

@@ -233,6 +233,9 @@ struct skis_sketch {
     int query_index = 0;                 // 0 auto (use the index if built), 1 always, 2 never
     int ris = 0;                         // plain RIS samples (uniform source, n Cov / T estimator)
     int bucket = 0;                      // first step in bucket form (Eq. probn) instead of rejection
+    uint32_t* vcount = nullptr;          // n: members per vertex over samples [0, vcount_T)
+    uint64_t vcount_T = 0;
+    bool vcount_ok = true;               // vcount is exact for samples [0, vcount_T)
     // query / greedy scratch (allocated on first use)
     uint64_t* smask = nullptr;           // T per-sample query bits (inverted-index path)
     uint64_t smask_cap = 0;

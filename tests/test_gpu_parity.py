@@ -382,9 +382,26 @@ def test_stop_at_size_matches_oracle(er_small):
     appended2, T2 = skis.skis_sample_to_size(s, 2 * target)
     ref2 = oracle.OracleSketch(o, seed, 10 * target, stop_entries=2 * target)
     assert T2 == ref2.T and appended2 == T2 - T1
+    # greedy after a truncation: the index counts the kept samples only
+    sd, sc, se = skis.skis_greedy_maxcover(s, 10)
+    od, oc, oe = ref2.greedy(10)
+    assert np.array_equal(sd, od) and np.array_equal(sc, oc)
     # a reached target appends nothing; max_count bounds a call
     assert skis.skis_sample_to_size(s, target) == (0, T2)
     assert skis.skis_sample_to_size(s, 100 * target, max_count=1000) == (1000, T2 + 1000)
+    s.close()
+
+
+def test_index_after_sampling_in_several_calls(er_small):
+    # the per-vertex counts kept while sampling add up over calls
+    spec, src, dst, g, o, osk, seed, T = er_small
+    s = skis.skis_sketch_create(g, seed)
+    for part in (T // 5, T // 3, T - T // 5 - T // 3):
+        skis.skis_sample(s, part)
+    sd, sc, se = skis.skis_greedy_maxcover(s, 25)
+    od, oc, oe = osk.greedy(25)
+    assert np.array_equal(sd, od) and np.array_equal(sc, oc)
+    np.testing.assert_allclose(se, oe, rtol=REL, atol=0)
     s.close()
 
 
