@@ -490,6 +490,7 @@ void skis::sketch_release(skis_sketch* s) {
     dev_free(s->to_warp_ids, st);
     dev_free(s->to_cta_ids, st);
     dev_free(s->srcrec, st);
+    dev_free(s->srcpick, st);
     dev_free(s->ovf_ids[0], st);
     dev_free(s->ovf_ids[1], st);
     dev_free(s->bitmaps, st);

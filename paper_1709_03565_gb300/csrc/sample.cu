@@ -74,6 +74,7 @@ struct SampleArgs {
     int32_t* queues;
     uint64_t bitmap_words;
     const uint4* srcrec;  // lane tier: source record per input t (k_sources)
+    const uint2* srcpick; // lane tier, bucket form: (picked in-edge, its source) per input t
     const uint64_t* lt_cum;  // LT graphs with per-edge thresholds: running weight sums, else nullptr
     const uint64_t* chain;   // bucket first step: the gamma chain per in-edge, else nullptr
     uint32_t* vcount;        // per-vertex member counts kept for the inverted index, or nullptr
@@ -348,15 +349,23 @@ __device__ __forceinline__ void record_retry_failure(const SampleArgs& a, uint64
 
 // Alg. 1 line 1 for every input id at once: the source of sample j and its
 // in-row, as 16 bytes (source, degree, row offset, row threshold), so that a
-// thread-tier lane starting a sample makes one coalesced load. Row offsets
-// fit 32 bits because graphs hold fewer than 2^32 - 8 edges.
-__global__ void k_sources(SampleArgs a, uint4* __restrict__ rec) {
+// lane-tier lane starting a sample makes one coalesced load; with the bucket
+// form, also the first step's picked in-edge and its source (8 bytes), whose
+// dependent chain loads are better spread over this many-thread pass than
+// paid by a lane at claim time. Row offsets fit 32 bits because graphs hold
+// fewer than 2^32 - 8 edges.
+__global__ void k_sources(SampleArgs a, uint4* __restrict__ rec, uint2* __restrict__ pick) {
     const uint64_t count = input_count(a);
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
          t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t v = draw_source(a, input_id(a, t));
+        const uint64_t j = input_id(a, t);
+        const uint32_t v = draw_source(a, j);
         const RowInfo rv = a.rows[v];
         rec[t] = make_uint4(v, rv.deg, (uint32_t)rv.off, rv.tau);
+        if (a.chain && rv.deg > 0) {  // the bucket form of the first step, drawn here in bulk
+            const uint64_t e = bucket_pick(a, j, rv.off, rv.deg);
+            pick[t] = make_uint2((uint32_t)e, (uint32_t)a.src[e]);
+        }
     }
 }
 
@@ -396,6 +405,7 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
     uint64_t pool_base = 0;
     uint32_t pool_n = 0, pool_used = 0;
     uint4 rec = make_uint4(0, 0, 0, 0);
+    uint2 prec = make_uint2(0, 0);
     uint64_t chunk_pos = 0, chunk_end = 0;
 
     for (;;) {
@@ -474,7 +484,10 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                     pool_base = base;
                     pool_n = (uint32_t)min(32ull, count - base);
                     pool_used = 0;
-                    if ((uint32_t)lane < pool_n) rec = __ldg(a.srcrec + base + lane);
+                    if ((uint32_t)lane < pool_n) {
+                        rec = __ldg(a.srcrec + base + lane);
+                        if (a.srcpick) prec = __ldg(a.srcpick + base + lane);
+                    }
                 }
                 const uint32_t take = min((uint32_t)__popc(idle), pool_n - pool_used);
                 const uint32_t rank = __popc(idle & lanemask_lt());
@@ -483,6 +496,8 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                 const uint32_t rv_deg = __shfl_sync(kFull, rec.y, from);
                 const uint32_t rv_off = __shfl_sync(kFull, rec.z, from);
                 const uint32_t rv_tau = __shfl_sync(kFull, rec.w, from);
+                const uint32_t pk_e = __shfl_sync(kFull, prec.x, from);
+                const uint32_t pk_u = __shfl_sync(kFull, prec.y, from);
                 if (!busy && rank < take) {
                     j = input_id(a, pool_base + pool_used + rank);
                     v = rv_src;  // Alg. 1 line 1, drawn by k_sources
@@ -502,11 +517,10 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                         lo = rv_off;
                         hi = rv_off + rv_deg;
                         q_last = hi > lo ? (hi - 1) >> 2 : lo >> 2;
-                        if (a.chain) {  // bucket form: the picked in-edge, round-0 coins after it
-                            const uint32_t e = (uint32_t)bucket_pick(a, j, rv_off, rv_deg);
-                            mine[1] = a.src[e];
+                        if (a.srcpick) {  // bucket form: the picked in-edge, round-0 coins after it
+                            mine[1] = (int32_t)pk_u;
                             len = 2;
-                            lo = e + 1;
+                            lo = pk_e + 1;
                             any = true;
                         }
                         qc = lo >> 2;
@@ -1171,8 +1185,11 @@ static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st
         SK_CUDA(dev_alloc_t(&s->ovf_ids[0], (size_t)count, st));
         SK_CUDA(dev_alloc_t(&s->ovf_ids[1], (size_t)count, st));
         dev_free(s->srcrec, st);
+        dev_free(s->srcpick, st);
         s->srcrec = nullptr;
+        s->srcpick = nullptr;
         SK_CUDA(dev_alloc_t(&s->srcrec, (size_t)count, st));
+        SK_CUDA(dev_alloc_t(&s->srcpick, (size_t)count, st));
         s->list_cap = count;
     }
     if (!s->arena) {
@@ -1262,6 +1279,7 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.queues = s->queues;
     base.bitmap_words = s->bitmap_words;
     base.srcrec = nullptr;
+    base.srcpick = nullptr;
     base.lt_cum = g->lt_cum;
     // per-vertex member counts, kept while they describe exactly samples
     // [0, T): invalid until this call succeeds
@@ -1335,8 +1353,9 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
             if (thread_tier) {
                 const uint64_t in_count = base.count;
                 k_sources<<<(int)std::max<uint64_t>(1, std::min<uint64_t>((in_count + 255) / 256, (uint64_t)sm_count() * 16)),
-                            256, 0, st>>>(at, s->srcrec); note_launch();
+                            256, 0, st>>>(at, s->srcrec, s->srcpick); note_launch();
                 at.srcrec = s->srcrec;
+                at.srcpick = base.chain ? s->srcpick : nullptr;
                 k_iis_lane<<<lane_blocks, kLaneBlock, 0, st>>>(at); note_launch();
                 SK_CUDA(cudaGetLastError());
             }

@@ -208,7 +208,8 @@ struct skis_sketch {
     uint64_t* to_warp_ids = nullptr;     // thread tier -> warp tier
     uint64_t* to_cta_ids = nullptr;      // warp tier -> CTA tier
     uint64_t* ovf_ids[2] = {nullptr, nullptr};
-    uint4* srcrec = nullptr;             // thread tier: prepared source records
+    uint4* srcrec = nullptr;             // lane tier: prepared source records
+    uint2* srcpick = nullptr;            // lane tier, bucket form: prepared first-step picks
     uint64_t list_cap = 0;
     uint32_t* bitmaps = nullptr;         // CTA tier: one n-bit visited bitmap per slot
     int32_t* queues = nullptr;           // CTA tier: one n-entry queue per slot
