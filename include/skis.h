@@ -100,13 +100,12 @@ typedef struct skis_stats {
     uint64_t last_passes;    /* sampling passes of the last call (> 1: the arena grew and reran) */
 } skis_stats;
 
-/* Sampling runs in three tiers chained by sample id: a packed first tier
- * in which a warp holds 32 samples and shares its lanes among their edge
- * quads (up to 32 members, in-rows up to THREAD_MAX_DEG edges, up to
- * THREAD_MAX_STEPS edge quads, up to 8 rejected rounds; the "thread" names
- * below refer to this tier), one warp per sample (up to 256 members), one
- * CTA per sample (any size). Options tune the split; they never change the
- * samples. */
+/* Sampling runs in three tiers chained by sample id: one lane per sample
+ * (up to 32 members, in-rows up to THREAD_MAX_DEG edges, up to
+ * THREAD_MAX_STEPS edge quads, up to THREAD_MAX_RETRIES rejected rounds;
+ * the "thread" names below refer to this tier), one warp per sample (up to
+ * 256 members), one CTA per sample (any size). Options tune the split; they
+ * never change the samples. */
 typedef enum skis_option {
     SKIS_OPT_RETRY_CAP = 0,      /* cap on rejected first-step rounds (default 2^24) */
     SKIS_OPT_CTA_SLOTS = 1,      /* CTAs of the CTA tier (default 2 per SM) */
