@@ -78,7 +78,13 @@ struct SampleArgs {
     const uint64_t* lt_cum;  // LT graphs with per-edge thresholds: running weight sums, else nullptr
     const uint64_t* chain;   // bucket first step: the gamma chain per in-edge, else nullptr
     uint32_t* vcount;        // per-vertex member counts kept for the inverted index, or nullptr
+    // the lane tier's prepass records for sample ids [up_first, up_first + up_count), which the
+    // later tiers reuse for the samples handed on to them (nullptr: draw again)
+    const uint4* up_rec;
+    const uint2* up_pick;
+    uint64_t up_first, up_count;
 };
+
 
 // a member written to the arena counts towards its vertex's list length
 __device__ __forceinline__ void count_member(const SampleArgs& a, int32_t u) {
@@ -136,6 +142,30 @@ __device__ __forceinline__ uint64_t bucket_pick(const SampleArgs& a, uint64_t j,
         else lo = mid + 1;
     }
     return off + lo;
+}
+
+// The source record (source, in-row) of sample j, from the prepass when it
+// holds j, else drawn; *pe / *pu receive the prepass's bucket pick (or -1).
+__device__ __forceinline__ uint32_t source_of(const SampleArgs& a, uint64_t j, RowInfo* rv, int64_t* pe,
+                                              int32_t* pu) {
+    *pe = -1;
+    *pu = -1;
+    if (a.up_rec && j - a.up_first < a.up_count) {
+        const uint64_t t = j - a.up_first;
+        const uint4 r = __ldg(a.up_rec + t);
+        rv->deg = r.y;
+        rv->off = r.z;
+        rv->tau = r.w;
+        if (a.up_pick && a.chain && r.y > 0) {
+            const uint2 p = __ldg(a.up_pick + t);
+            *pe = p.x;
+            *pu = (int32_t)p.y;
+        }
+        return r.x;
+    }
+    const uint32_t v = draw_source(a, j);
+    *rv = a.rows[v];
+    return v;
 }
 
 // ----------------------------------------------------------- inserters
@@ -265,15 +295,20 @@ __device__ __forceinline__ bool expand_rows(const SampleArgs& a, uint64_t j, uin
 // with *failed set.
 template <class Ins>
 __device__ __forceinline__ uint32_t first_step_warp(const SampleArgs& a, uint64_t j, const RowInfo& rv, Ins& ins,
-                                                    bool* failed) {
+                                                    bool* failed, int64_t pick_e = -1, int32_t pick_u = -1) {
     const int lane = threadIdx.x & 31;
     *failed = false;
     if (a.chain) {  // bucket form: the picked in-edge, then round-0 coins after it
         int32_t u = -1;
         uint64_t e = 0;
         if (lane == 0) {
-            e = bucket_pick(a, j, rv.off, rv.deg);
-            u = a.src[e];
+            if (pick_e >= 0) {  // drawn by the prepass
+                e = (uint64_t)pick_e;
+                u = pick_u;
+            } else {
+                e = bucket_pick(a, j, rv.off, rv.deg);
+                u = a.src[e];
+            }
         }
         e = __shfl_sync(kFull, e, 0);
         ins.insert(u);
@@ -653,14 +688,16 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
             __syncwarp();
 
             // Alg. 1 line 1: the source
-            const uint32_t v = draw_source(a, j);
-            const RowInfo rv = a.rows[v];
+            RowInfo rv;
+            int64_t pe;
+            int32_t pu;
+            const uint32_t v = source_of(a, j, &rv, &pe, &pu);
             WarpInserter ins{hash, queue, 0u, false};
             ins.insert(lane == 0 ? (int32_t)v : -1);
 
             // lines 2-6 by rejection: all in-edge coins of v, round r
             bool failed = false;
-            const uint32_t r = first_step_warp(a, j, rv, ins, &failed);
+            const uint32_t r = first_step_warp(a, j, rv, ins, &failed, pe, pu);
             if (failed) {
                 if (lane == 0) record_retry_failure(a, j, v, r, rv.deg);
                 continue;
@@ -741,8 +778,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
         const uint64_t j = s_j;
         if (j == ~0ull) break;
 
-        const uint32_t v = draw_source(a, j);
-        const RowInfo rv = a.rows[v];
+        RowInfo rv;
+        int64_t pe;
+        int32_t pu;
+        const uint32_t v = source_of(a, j, &rv, &pe, &pu);
         if (threadIdx.x == 0) {
             bitmap[v >> 5] |= 1u << (v & 31);
             queue[0] = (int32_t)v;
@@ -760,7 +799,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
         if (nq_src <= 16 || a.chain) {
             if (wid == 0) {
                 bool f = false;
-                const uint32_t rr = first_step_warp(a, j, rv, ins, &f);
+                const uint32_t rr = first_step_warp(a, j, rv, ins, &f, pe, pu);
                 if (lane == 0) {
                     s_r = rr;
                     s_failed = f ? 1u : 0u;
@@ -1280,6 +1319,10 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.bitmap_words = s->bitmap_words;
     base.srcrec = nullptr;
     base.srcpick = nullptr;
+    base.up_rec = nullptr;
+    base.up_pick = nullptr;
+    base.up_first = 0;
+    base.up_count = 0;
     base.lt_cum = g->lt_cum;
     // per-vertex member counts, kept while they describe exactly samples
     // [0, T): invalid until this call succeeds
@@ -1356,6 +1399,12 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
                             256, 0, st>>>(at, s->srcrec, s->srcpick); note_launch();
                 at.srcrec = s->srcrec;
                 at.srcpick = base.chain ? s->srcpick : nullptr;
+                if (!base.ids) {  // contiguous ids: later tiers find their samples' records by id
+                    aw.up_rec = ac.up_rec = s->srcrec;
+                    aw.up_pick = ac.up_pick = at.srcpick;
+                    aw.up_first = ac.up_first = base.first_id;
+                    aw.up_count = ac.up_count = base.count;
+                }
                 k_iis_lane<<<lane_blocks, kLaneBlock, 0, st>>>(at); note_launch();
                 SK_CUDA(cudaGetLastError());
             }
