@@ -51,9 +51,12 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help=f"{WORKLOAD} (the benchmark line) or rmat-2^25-wc (bounded-sample rates)")
+                    help=f"{WORKLOAD} (the benchmark line), rmat-2^25-wc (bounded-sample rates) or "
+                         "chunglu-4e7-wc-dssa (DSSA doubling)")
     ap.add_argument("--samples", type=int, default=200_000, help="samples of the bounded R-MAT run")
+    ap.add_argument("--dssa-max-samples", type=int, default=1 << 26, help="sample cap of the DSSA run")
     ap.add_argument("--first-step", default="bucket", choices=["bucket", "rejection"],
                     help="form of Alg. 1's conditioned first step (Eq. probn buckets, or rejection rounds)")
     ap.add_argument("--profile-step", action="store_true",
@@ -238,6 +241,64 @@ def serve_run(skis, s, queries, arrivals, slots, max_batch):
     return done_at - arrivals, wall
 
 
+def variants_benchmark(skis, torch, dev, stream, n, d_src, d_dst, d_p, T, seed, first_step):
+    """Sampling rates of the method's variants on the bench graph (10M
+    samples each, best of two, device time from the library's events):
+    the other form of the first step, plain RIS, the Linear Threshold model
+    (weighted-cascade weights on the same topology) and stop-at-size
+    (h n ln n entries, h = 5)."""
+    import math
+
+    def best(make, run):
+        out = None
+        for _ in range(2):
+            s = make()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = run(s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            st = skis.skis_sketch_stats(s)
+            st["call_ms"] = e0.elapsed_time(e1)
+            s.close()
+            if out is None or st["call_ms"] < out[0]["call_ms"]:
+                out = (st, r)
+        return out
+
+    res = {}
+    g = skis.skis_load_graph(n, d_src, d_dst, d_p, skis.SKIS_W_EXPLICIT_P, stream=stream)
+    other = 0 if first_step == 1 else 1
+
+    def mk(opt=None, val=None, sketch_graph=None, arena=None):
+        def f():
+            s = skis.skis_sketch_create(sketch_graph or g, seed, arena or int(T * 5.5), stream=stream)
+            if opt is not None:
+                skis.skis_sketch_set_option(s, opt, val)
+            return s
+        return f
+
+    st, _ = best(mk(skis.SKIS_OPT_FIRST_STEP, other), lambda s: skis.skis_sample(s, T, stream=stream))
+    res["first_step_" + ("bucket" if other else "rejection")] = {
+        "rr_sets_per_s": T / (st["last_sample_ms"] / 1e3), "sample_ms": st["last_sample_ms"],
+        "coins_per_sample": st["coins"] / T}
+    st, _ = best(mk(skis.SKIS_OPT_SAMPLER, 1), lambda s: skis.skis_sample(s, T, stream=stream))
+    res["ris"] = {"rr_sets_per_s": T / (st["last_sample_ms"] / 1e3), "sample_ms": st["last_sample_ms"],
+                  "members_per_sample": st["entries"] / T, "note": "uniform source, singular samples kept"}
+    target = int(5 * n * math.log(n))
+    st, (app, _) = best(mk(skis.SKIS_OPT_FIRST_STEP, first_step, arena=int(target * 1.3)),
+                        lambda s: skis.skis_sample_to_size(s, target, stream=stream))
+    res["stop_at_size"] = {"target_entries": target, "h": 5, "samples": app, "entries": st["entries"],
+                           "call_ms": st["call_ms"], "rr_sets_per_s": app / (st["call_ms"] / 1e3)}
+    g.close()
+    glt = skis.skis_load_graph_lt(n, d_src, d_dst, None, skis.SKIS_W_WC, stream=stream)
+    st, _ = best(mk(sketch_graph=glt), lambda s: skis.skis_sample(s, T, stream=stream))
+    res["lt_wc"] = {"rr_sets_per_s": T / (st["last_sample_ms"] / 1e3), "sample_ms": st["last_sample_ms"],
+                    "members_per_sample": st["entries"] / T, "walk_ms": st["last_thread_ms"],
+                    "long_walk_ms": st["last_warp_ms"], "long_walks": st["to_warp"]}
+    glt.close()
+    return res
+
+
 def serving_benchmark(skis, torch, dev, stream):
     """Influence-oracle serving on a device-resident sketch: saturation
     throughput (all requests at t = 0) of continuous batching versus one
@@ -342,6 +403,54 @@ def rmat_run(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------- DSSA run
+def dssa_run(args):
+    """DSSA-style doubling influence maximisation (two sketches grown in
+    place, exact stopping test) on the Chung-Lu WC graph with n = 40M and
+    m = 1.4B: k = 100, eps = 0.1, delta = 1/n, from 2^16 samples up to a
+    bounded cap; wall time of the whole run."""
+    import torch
+
+    import paper_1709_03565_gb300 as skis
+    import synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    spec, src, dst, _ = synth.workload("chunglu-4e7-wc-dssa")
+    t_gen = time.perf_counter() - t0
+    n, m = spec["n"], spec["m"]
+    d_src, d_dst = torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev)
+    del src, dst
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g = skis.skis_load_graph(n, d_src, d_dst, None, skis.SKIS_W_WC, stream=stream)
+    torch.cuda.synchronize()
+    load_s = time.perf_counter() - t1
+    del d_src, d_dst
+    torch.cuda.empty_cache()
+    info = skis.skis_graph_get_info(g)
+    k, eps, delta = 100, 0.1, 1.0 / n
+    t2 = time.perf_counter()
+    seeds, res = skis.skis_dssa_maxinf(g, SKETCH_SEED + 7, SKETCH_SEED + 8, k, eps, delta, 0, 1 << 16,
+                                       args.dssa_max_samples, stream=stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t2
+    g.close()
+    line = {
+        "metric": "DSSA doubling: seconds to an (1 - 1/e - eps)-approximate seed set", "value": wall, "unit": "s",
+        "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "chunglu-4e7-wc-dssa", "graph": "Chung-Lu directed, exponent 2.0, weighted cascade",
+                   "n": n, "m": m, "k": k, "eps": eps, "delta": delta, "n0": 1 << 16,
+                   "n_max": args.dssa_max_samples},
+        "result": {key: (float(v) if isinstance(v, float) else int(v)) for key, v in res.items()},
+        "samples_per_s": 2 * res["samples"] / wall, "graph_load_s": load_s, "generate_s": t_gen,
+        "Gamma": info["Gamma"], "seeds_head": [int(x) for x in seeds[:10]],
+    }
+    print(json.dumps(line))
+
+
 # ----------------------------------------------------------------- ours
 def main():
     args = _args()
@@ -349,9 +458,11 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.workload != WORKLOAD:
-        if args.workload != "rmat-2^25-wc":
-            raise SystemExit(f"unknown workload {args.workload}")
-        return rmat_run(args)
+        if args.workload == "rmat-2^25-wc":
+            return rmat_run(args)
+        if args.workload == "chunglu-4e7-wc-dssa":
+            return dssa_run(args)
+        raise SystemExit(f"unknown workload {args.workload}")
 
     import torch
 
@@ -482,11 +593,13 @@ def main():
     achieved = alg / (sample_ms / 1e3) / 1e9
     tps = _traffic_per_sample(args.first_step)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tps * T if tps is not None else None), "kernel": "k_iis_lane + k_iis_warp + k_iis_cta",
+                "traffic": (tps * T if tps is not None else None), "kernel": "k_sources + k_iis_lane + k_iis_warp + k_iis_cta",
                 "algorithmic_bytes": alg, "kernel_ms": sample_ms, "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
 
     # ---- influence-oracle serving (queries/s, p50/p99)
     serving = None if args.no_serving else serving_benchmark(skis, torch, dev, stream)
+    variants = None if args.no_variants else variants_benchmark(skis, torch, dev, stream, n, d_src, d_dst, d_p, T,
+                                                                seed, first_step)
 
     # ---- CPU baseline: the oracle, as it stands, on a bounded sample
     cpu = None
@@ -520,6 +633,7 @@ def main():
         "per_sample": {"members": entries / T, "coins": coins / T},
         "roofline": roofline,
         "serving": serving,
+        "variants": variants,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "RR sets/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -495,6 +495,9 @@ void skis::sketch_release(skis_sketch* s) {
     dev_free(s->ovf_ids[1], st);
     dev_free(s->bitmaps, st);
     dev_free(s->queues, st);
+    dev_free(s->lt_hash, st);
+    dev_free(s->lt_list, st);
+    dev_free(s->lt_slot, st);
     dev_free(s->qmask, st);
     dev_free(s->inv_off, st);
     dev_free(s->inv, st);

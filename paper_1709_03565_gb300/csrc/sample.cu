@@ -576,34 +576,54 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
         // ---- one edge quad: coins of lines 4-6 (first step, round r) or
         // of line 9 (reverse BFS); a RIS source may have no in-edges
         bool handed = false, failed = false;
+        uint32_t qdone = qc;  // the last quad drawn in this step
         if (hi > lo) {
+            // up to two quads of the row per step: their thresholds, sources
+            // and Philox blocks are independent, so their latencies overlap
+            const bool two = qc < q_last;
+            qdone = two ? qc + 1 : qc;
             const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_row, tau_row, tau_row, tau_row);
-            const uint4 x = coin_block(a.seed, qc, first ? r : 0u, first ? kDomFirst : kDomBfs, j);
-            const uint32_t e0 = qc << 2;
+            const uint4 t4b = (two && a.tau) ? __ldg(tau4 + qc + 1) : make_uint4(tau_row, tau_row, tau_row, tau_row);
+            const uint32_t rr = first ? r : 0u, dom = first ? kDomFirst : kDomBfs;
+            const uint4 x = coin_block(a.seed, qc, rr, dom, j);
+            uint4 xb = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+            if (two) xb = coin_block(a.seed, qc + 1, rr, dom, j);
+            const uint32_t e0 = qc << 2, e1 = e0 + 4;
             unsigned live = 0;
             live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
             live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
             live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
             live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
+            if (two) {  // e1 > lo: only the row's end bounds the second quad
+                live |= (e1 + 0 < hi && coin_live(xb.x, t4b.x)) ? 16u : 0u;
+                live |= (e1 + 1 < hi && coin_live(xb.y, t4b.y)) ? 32u : 0u;
+                live |= (e1 + 2 < hi && coin_live(xb.z, t4b.z)) ? 64u : 0u;
+                live |= (e1 + 3 < hi && coin_live(xb.w, t4b.w)) ? 128u : 0u;
+            }
             if (live) {
                 any = true;
-                const int4 s4 = __ldg(src4 + qc);
-                const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (!((live >> k) & 1u) || handed) continue;
-                    const int32_t u = cand[k];
-                    bool seen = false;
-                    for (uint32_t i = 0; i < len; ++i)
-                        if (mine[i] == u) { seen = true; break; }
-                    if (seen) continue;
-                    if (len == (uint32_t)kLaneQ) handed = true;  // the warp tier takes it
-                    else mine[len++] = u;
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned lh = (live >> (4 * h)) & 15u;
+                    if (!lh || handed) continue;
+                    const int4 s4 = __ldg(src4 + qc + h);
+                    const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (!((lh >> k) & 1u) || handed) continue;
+                        const int32_t u = cand[k];
+                        bool seen = false;
+                        for (uint32_t i = 0; i < len; ++i)
+                            if (mine[i] == u) { seen = true; break; }
+                        if (seen) continue;
+                        if (len == (uint32_t)kLaneQ) handed = true;  // the warp tier takes it
+                        else mine[len++] = u;
+                    }
                 }
             }
-            ++steps;
+            steps += two ? 2u : 1u;
         }
-        if (!handed && (hi <= lo || qc >= q_last)) {  // the row is used up
+        if (!handed && (hi <= lo || qdone >= q_last)) {  // the row is used up
             if (first) {
                 if (any || a.ris) {
                     first = false;
@@ -646,14 +666,14 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                 if (!row && !handed) done = true;
             }
         } else if (!handed) {
-            ++qc;
+            qc = qdone + 1;
         }
         if (!done && !handed && steps > a.max_steps) handed = true;
         if (handed) hand_on(a, j);
         if (failed) record_retry_failure(a, j, v, r, src_deg);
         if (handed || failed) busy = false;
         // load the next pop's row ahead while this row's last quads are drawn
-        if (busy && !done && !first && !pf_ok && head < len && q_last - qc <= 1u) {
+        if (busy && !done && !first && !pf_ok && head < len && q_last - qc <= 2u) {
             const RowInfo rw = a.rows[mine[head]];
             pf_off = (uint32_t)rw.off;
             pf_deg = rw.deg;
@@ -1106,6 +1126,79 @@ __global__ void __launch_bounds__(kLtBlock) k_lt_walk(SampleArgs a) {
     }
 }
 
+// Medium LT walks: one lane per walk with its own open-addressing visited
+// table (kLtMidHash slots, at most half full) and member list in global
+// memory; the table is restored to empty slot by slot after each walk. A
+// walk longer than kLtMidCap is handed on to the slot tier.
+constexpr int kLtMidBlock = 256;
+constexpr uint32_t kLtMidHash = 2048;
+constexpr uint32_t kLtMidCap = 1024;
+
+__global__ void __launch_bounds__(kLtMidBlock) k_lt_mid(SampleArgs a, uint32_t* __restrict__ hash_all,
+                                                        int32_t* __restrict__ list_all,
+                                                        uint32_t* __restrict__ slot_all) {
+    const uint64_t me = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t* hash = hash_all + me * kLtMidHash;
+    int32_t* list = list_all + me * kLtMidCap;
+    uint32_t* slot = slot_all + me * kLtMidCap;
+    const uint64_t count = input_count(a);
+    for (;;) {
+        const unsigned long long ti = atomicAdd(a.work, 1ull);
+        if (ti >= count) break;
+        const uint64_t j = input_id(a, ti);
+        const uint32_t v = draw_source(a, j);
+        uint32_t len = 0;
+        bool over = false;
+        uint64_t coins = 0;
+        int32_t x = (int32_t)v;
+        for (uint32_t t = 0;; ++t) {  // each step adds a new member or ends the walk
+            // x joins the visited table and the list
+            uint32_t h = ((uint32_t)x * 2654435761u) & (kLtMidHash - 1);
+            while (hash[h] != kEmpty) h = (h + 1) & (kLtMidHash - 1);  // x is new: a free slot exists
+            hash[h] = (uint32_t)x;
+            slot[len] = h;
+            list[len++] = x;
+            const RowInfo rw = a.rows[x];
+            coins += rw.deg;
+            const int32_t u = lt_step(a, j, t, rw);
+            if (u < 0) break;
+            uint32_t g = ((uint32_t)u * 2654435761u) & (kLtMidHash - 1);
+            bool seen = false;
+            for (;;) {  // the table is at most half full: the probe ends
+                const uint32_t key = hash[g];
+                if (key == kEmpty) break;
+                if (key == (uint32_t)u) { seen = true; break; }
+                g = (g + 1) & (kLtMidHash - 1);
+            }
+            if (seen) break;
+            if (len == kLtMidCap) {
+                over = true;
+                break;
+            }
+            x = u;
+        }
+        if (over) {
+            hand_on(a, j);
+        } else {
+            const unsigned long long base = atomicAdd(a.arena_cursor, (unsigned long long)len);
+            if (base + len <= a.arena_cap) {
+                for (uint32_t i = 0; i < len; ++i) {
+                    a.arena[base + i] = list[i];
+                    count_member(a, list[i]);
+                }
+                a.h_off[j] = base;
+                a.h_len[j] = len;
+                a.h_src[j] = v;
+                a.h_retries[j] = 0;
+                a.h_coins[j] = coins;
+            } else {
+                arena_overflow(a, j);
+            }
+        }
+        for (uint32_t i = 0; i < len; ++i) hash[slot[i]] = kEmpty;
+    }
+}
+
 // Long LT walks: one warp per slot; lane 0 walks with the slot's global
 // visited bitmap and queue, the warp copies the members out and clears the
 // bitmap.
@@ -1235,6 +1328,13 @@ static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st
         uint64_t cap = s->arena_hint ? s->arena_hint : std::max<uint64_t>(count * 8, 1u << 20);
         SK_CUDA(dev_alloc_t(&s->arena, (size_t)cap, st));
         s->arena_cap = cap;
+    }
+    if (g->lt && !s->lt_hash) {  // medium LT walks: one table, list and slot record per lane
+        s->lt_mid_lanes = (uint64_t)sm_count() * kLtMidBlock;
+        SK_CUDA(dev_alloc_t(&s->lt_hash, (size_t)(s->lt_mid_lanes * kLtMidHash), st));
+        SK_CUDA(cudaMemsetAsync(s->lt_hash, 0xFF, s->lt_mid_lanes * kLtMidHash * sizeof(uint32_t), st));
+        SK_CUDA(dev_alloc_t(&s->lt_list, (size_t)(s->lt_mid_lanes * kLtMidCap), st));
+        SK_CUDA(dev_alloc_t(&s->lt_slot, (size_t)(s->lt_mid_lanes * kLtMidCap), st));
     }
     int slots = s->cta_slots;
     if (slots <= 0) {
@@ -1382,15 +1482,18 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
         ac.out_count = nullptr;
 
         SK_CUDA(cudaEventRecord(s->ev[0], st));
-        if (g->lt) {  // LT: lane-per-sample walks, then long walks on the CTA-tier slots
+        if (g->lt) {  // LT: lane-per-sample walks, lane-per-walk medium walks, long walks on the slots
             aw.ids = s->to_warp_ids;
             aw.count_dev = &s->ctr->n_to_warp;
             k_lt_walk<<<lt_blocks, kLtBlock, 0, st>>>(at); note_launch();
             SK_CUDA(cudaGetLastError());
             SK_CUDA(cudaEventRecord(s->ev[1], st));
-            k_lt_long<<<s->cta_slots_alloc, 32, 0, st>>>(aw); note_launch();
+            k_lt_mid<<<s->lt_mid_lanes / kLtMidBlock, kLtMidBlock, 0, st>>>(aw, s->lt_hash, s->lt_list, s->lt_slot);
+            note_launch();
             SK_CUDA(cudaGetLastError());
             SK_CUDA(cudaEventRecord(s->ev[2], st));
+            k_lt_long<<<s->cta_slots_alloc, 32, 0, st>>>(ac); note_launch();
+            SK_CUDA(cudaGetLastError());
             SK_CUDA(cudaEventRecord(s->ev[3], st));
         } else {
             if (thread_tier) {

@@ -213,6 +213,10 @@ struct skis_sketch {
     uint64_t list_cap = 0;
     uint32_t* bitmaps = nullptr;         // CTA tier: one n-bit visited bitmap per slot
     int32_t* queues = nullptr;           // CTA tier: one n-entry queue per slot
+    uint32_t* lt_hash = nullptr;         // LT medium walks: visited table per lane
+    int32_t* lt_list = nullptr;          // LT medium walks: member list per lane
+    uint32_t* lt_slot = nullptr;         // LT medium walks: table slot of each listed member
+    uint64_t lt_mid_lanes = 0;
     int cta_slots_alloc = 0;
     uint64_t bitmap_words = 0;
     // options

@@ -42,8 +42,13 @@ def _graphs():
     n3 = 400
     s3 = np.concatenate([np.arange(n3 - 1), [5, 17, 260]]).astype(np.int32)
     d3 = np.concatenate([np.arange(1, n3), [300, 350, 390]]).astype(np.int32)
+    # a longer path: walks beyond the lane-per-walk tier's 1024 members
+    n4 = 2600
+    s4 = np.arange(n4 - 1).astype(np.int32)
+    d4 = np.arange(1, n4).astype(np.int32)
     return {
         "chunglu-wc": (n1, s1, d1, None, skis.SKIS_W_WC, oracle.W_WC),
+        "path-long-wc": (n4, s4, d4, None, skis.SKIS_W_WC, oracle.W_WC),
         "chunglu-p": (n2, s2, d2, p2, skis.SKIS_W_EXPLICIT_P, oracle.W_P),
         "path-wc": (n3, s3, d3, None, skis.SKIS_W_WC, oracle.W_WC),
     }
@@ -87,9 +92,11 @@ def test_lt_samples_match_oracle_in_walk_order(name, ris):
     assert np.array_equal(dev["len"].astype(np.int64), ora["len"])
     assert np.array_equal(dev["coins"], ora["coins"])
     assert np.array_equal(dev["members"], ora["members"])  # the walk order is unique
+    st = skis.skis_sketch_stats(s)
     if name == "path-wc":
-        st = skis.skis_sketch_stats(s)
-        assert st["to_warp"] > 0 and dev["len"].max() > 48  # the slot tier took part
+        assert st["to_warp"] > 0 and dev["len"].max() > 48  # the lane-per-walk tier took part
+    if name == "path-long-wc":
+        assert st["deferred"] > 0 and dev["len"].max() > 1024  # the slot tier took part
     s.close()
     g.close()
 
