@@ -132,8 +132,8 @@ typedef enum skis_option {
                                       Q_d) / 2^64), U the 64-bit word of the Philox block (q 0, retry 0,
                                       domain BUCKET = 6, sample j); the first e with 2^62 - Q_e > z is
                                       live and the in-edges after it get their FIRST coins of round 0.
-                                      IC graphs, IIS sampler; set before the first skis_sample; builds
-                                      the graph's per-edge chain (8 bytes an edge) on first use. */
+                                      IC graphs, IIS sampler; set before the first skis_sample; reads
+                                      the per-edge chain IC graphs keep from loading. */
 } skis_option;
 
 /* Load G = (V, E, w) (Sec. II-A) and build the device structures every later
@@ -145,7 +145,9 @@ typedef enum skis_option {
  *     in fixed point: Q = 2^62, Q <- floor(Q (2^32 - tau) / 2^32) along the
  *     row (Q = 0 on a sentinel), w_v = (2^62 - Q) >> (ceil(log2 n) + 1);
  *   - W = sum_v w_v (Gamma = sum gamma_v) and the alias table of the source
- *     law Pr[src = v] = w_v / W (Eq. probu).
+ *     law Pr[src = v] = w_v / W (Eq. probu);
+ *   - the chain of Q values after every in-edge (u64 per edge, computed
+ *     with gamma), which the bucket form of the first step reads.
  * src, dst: int32[m] vertex ids in [0, n); weights: see skis_weight_model;
  * all three in mem_space. Rejected with SKIS_EINVAL: n < 1, n > 2^31,
  * m < 0, m >= 2^32 - 8, an id outside [0, n), a self-loop, p outside [0, 1]

@@ -101,16 +101,16 @@ __global__ void k_rows(const uint64_t* __restrict__ off, int64_t n, int wc, RowI
 }
 
 // Eq. gamma_v in fixed point: Q = 2^62; Q <- floor(Q (2^32 - tau) / 2^32) for
-// each in-edge in CSR order (0 on a sentinel); w_v = (2^62 - Q) >> s.
+// each in-edge in CSR order (0 on a sentinel); w_v = (2^62 - Q) >> s. With
+// chain != nullptr the running Q after every in-edge is kept as well.
 __global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __restrict__ csr_tau, int64_t n, int s,
-                        uint64_t* __restrict__ w) {
+                        uint64_t* __restrict__ w, uint64_t* __restrict__ chain) {
     const uint64_t one62 = 1ull << 62;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const RowInfo r = rows[v];
         uint64_t Q = one62;
         uint32_t k = 0;
-        // thresholds are loaded 8 at a time ahead of the (sequential) product
-        for (; k + 8 <= r.deg && Q != 0; k += 8) {
+        for (; k + 8 <= r.deg && (Q != 0 || chain); k += 8) {
             uint32_t t[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) t[i] = csr_tau ? csr_tau[r.off + k + i] : r.tau;
@@ -118,12 +118,14 @@ __global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __rest
             for (int i = 0; i < 8; ++i) {
                 if (t[i] == kSentinel) Q = 0;
                 else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t[i])) >> 32);
+                if (chain) chain[r.off + k + i] = Q;
             }
         }
-        for (; k < r.deg && Q != 0; ++k) {
+        for (; k < r.deg && (Q != 0 || chain); ++k) {
             const uint32_t t = csr_tau ? csr_tau[r.off + k] : r.tau;
             if (t == kSentinel) Q = 0;
             else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t)) >> 32);
+            if (chain) chain[r.off + k] = Q;
         }
         w[v] = (one62 - Q) >> s;
     }
@@ -303,8 +305,8 @@ void graph_release(skis_graph* g) {
     g->perm = nullptr; g->w = nullptr; g->alias = nullptr; g->lt_cum = nullptr; g->chain = nullptr;
 }
 
-// The chain is a cache of the graph built by the first sketch that needs it
-// (the graph is otherwise immutable after loading).
+// IC graphs keep the chain from loading (k_gamma); this builds it for a
+// graph that has none.
 int graph_ensure_chain(const skis_graph* gc, cudaStream_t st, std::string* err) {
     skis_graph* g = const_cast<skis_graph*>(gc);
     if (g->chain || g->m == 0) return SKIS_OK;
@@ -418,7 +420,9 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
             GB_CUDA(scan_u64(lt_w, g->lt_cum, m, st));
         }
     } else {
-        k_gamma<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->s, g->w); note_launch();
+        // the chain is kept for the bucket form of the first step (8 bytes an edge)
+        if (m > 0) GB_CUDA(dev_alloc_t(&g->chain, (size_t)m, st));
+        k_gamma<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->s, g->w, g->chain); note_launch();
         GB_CUDA(cudaGetLastError());
     }
     GB_CUDA(sum_u64(g->w, n, d_W, st));

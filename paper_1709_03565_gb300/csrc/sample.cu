@@ -1330,7 +1330,7 @@ static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st
         s->arena_cap = cap;
     }
     if (g->lt && !s->lt_hash) {  // medium LT walks: one table, list and slot record per lane
-        s->lt_mid_lanes = (uint64_t)sm_count() * kLtMidBlock;
+        s->lt_mid_lanes = (uint64_t)sm_count() * kLtMidBlock * 2;  // two blocks per SM
         SK_CUDA(dev_alloc_t(&s->lt_hash, (size_t)(s->lt_mid_lanes * kLtMidHash), st));
         SK_CUDA(cudaMemsetAsync(s->lt_hash, 0xFF, s->lt_mid_lanes * kLtMidHash * sizeof(uint32_t), st));
         SK_CUDA(dev_alloc_t(&s->lt_list, (size_t)(s->lt_mid_lanes * kLtMidCap), st));
