@@ -171,6 +171,46 @@ def algorithmic_bytes(T: int, entries: int, coins: int, per_edge_tau: bool) -> i
 
 
 # -------------------------------------------------------------- reference
+# The oracle on every host core: worker processes (spawned, never forked after
+# CUDA is up) each hold the oracle's graph and sample disjoint id ranges.
+_REF_GRAPH = None
+
+
+def _ref_init(n, src, dst, p, bucket):
+    global _REF_GRAPH, _REF_BUCKET
+    import oracle
+
+    _REF_GRAPH = oracle.OracleGraph(n, src, dst, weights=p, model=oracle.W_P)
+    _REF_BUCKET = bucket
+
+
+def _ref_sample(job):
+    seed, start, count = job
+    out = _REF_GRAPH.sample_ids(seed, np.arange(start, start + count, dtype=np.uint64), bucket=_REF_BUCKET)
+    return int(out["coins"].sum())
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_pool(n, src, dst, p, bucket, cores):
+    import multiprocessing as mp
+
+    import oracle
+
+    oracle.build()  # once, before the workers load it
+    return mp.get_context("spawn").Pool(cores, initializer=_ref_init, initargs=(n, src, dst, p, bucket))
+
+
+def pool_step(pool, seed, start, per_core, cores):
+    jobs = [(seed, start + i * per_core, per_core) for i in range(cores)]
+    return sum(pool.map(_ref_sample, jobs))
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -178,17 +218,17 @@ def run_reference(args, rank, world):
     import synth
 
     spec, src, dst, p = synth.workload(WORKLOAD)
-    oracle.build()
-    g = oracle.OracleGraph(spec["n"], src, dst, weights=p, model=oracle.W_P)
-    per_step = 200_000
+    cores = host_cores()
+    per_core = 50_000
+    per_step = per_core * cores
+    pool = oracle_pool(spec["n"], src, dst, p, args.first_step == "bucket", cores)
     nxt = 0
 
     def step():
         nonlocal nxt
-        ids = np.arange(nxt, nxt + per_step, dtype=np.uint64)
+        c = pool_step(pool, SKETCH_SEED, nxt, per_core, cores)
         nxt += per_step
-        out = g.sample_ids(SKETCH_SEED, ids, bucket=args.first_step == "bucket")
-        return int(out["coins"].sum())
+        return c
 
     for _ in range(args.warmup):
         step()
@@ -197,6 +237,8 @@ def run_reference(args, rank, world):
     for _ in range(args.steps):
         coins += step()
     dt = time.perf_counter() - t0
+    pool.close()
+    pool.join()
     value = args.steps * per_step / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "RR sets/s", "n_gpus": world,
@@ -206,8 +248,8 @@ def run_reference(args, rank, world):
                    "k": spec["k"], "step": f"{per_step} consecutive sample ids of the workload",
                    "first_step": args.first_step},
         "sampled_edges_per_s": coins / dt,
-        "cpu_baseline": {"value": value, "unit": "RR sets/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} sample ids per step, single-threaded C oracle"},
+        "cpu_baseline": {"value": value, "unit": "RR sets/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} sample ids per step, the C oracle in {cores} worker processes"},
         "e2e": {"value": value, "unit": "RR sets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -327,6 +369,14 @@ def serving_benchmark(skis, torch, dev, stream):
     rate = 0.5 * sat_batched
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nq))
     lat_p, wall_p = serve_run(skis, s, queries, arrivals, 4, 64)
+    # latency against offered load, swept up to saturation
+    sweep = []
+    for frac in (0.25, 0.75, 0.9, 1.0):
+        lam = frac * sat_batched
+        arr = np.cumsum(rng.exponential(1.0 / lam, size=nq))
+        lat, wall = serve_run(skis, s, queries, arr, 4, 64)
+        sweep.append({"offered_fraction": frac, "offered_per_s": lam, "served_per_s": nq / wall,
+                      "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)})
     s.close()
     g.close()
     return {
@@ -338,6 +388,7 @@ def serving_benchmark(skis, torch, dev, stream):
         "poisson_rate_per_s": rate, "queries_per_s": nq / wall_p,
         "p50_ms": float(np.percentile(lat_p, 50) * 1e3), "p99_ms": float(np.percentile(lat_p, 99) * 1e3),
         "saturation_p50_ms": float(np.percentile(lat_b, 50) * 1e3),
+        "load_sweep": sweep,
         "slots": 4, "max_batch": 64,
     }
 
@@ -407,8 +458,8 @@ def rmat_run(args):
 def dssa_run(args):
     """DSSA-style doubling influence maximisation (two sketches grown in
     place, exact stopping test) on the Chung-Lu WC graph with n = 40M and
-    m = 1.4B: k = 100, eps = 0.1, delta = 1/n, from 2^16 samples up to a
-    bounded cap; wall time of the whole run."""
+    m = 1.4B: k in {1, 100, 1000}, eps = 0.1, delta = 1/n, from 2^16
+    samples up to a bounded cap; wall time of each whole run."""
     import torch
 
     import paper_1709_03565_gb300 as skis
@@ -430,23 +481,30 @@ def dssa_run(args):
     del d_src, d_dst
     torch.cuda.empty_cache()
     info = skis.skis_graph_get_info(g)
-    k, eps, delta = 100, 0.1, 1.0 / n
-    t2 = time.perf_counter()
-    seeds, res = skis.skis_dssa_maxinf(g, SKETCH_SEED + 7, SKETCH_SEED + 8, k, eps, delta, 0, 1 << 16,
-                                       args.dssa_max_samples, stream=stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t2
+    eps, delta = 0.1, 1.0 / n
+    runs = {}
+    seeds = None
+    for k in (1, 100, 1000):
+        t2 = time.perf_counter()
+        sk, res = skis.skis_dssa_maxinf(g, SKETCH_SEED + 7, SKETCH_SEED + 8, k, eps, delta, 0, 1 << 16,
+                                        args.dssa_max_samples, stream=stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t2
+        runs[str(k)] = {"seconds": wall, "samples_per_s": 2 * res["samples"] / wall,
+                        "result": {key: (float(v) if isinstance(v, float) else int(v)) for key, v in res.items()}}
+        if k == 100:
+            seeds = sk
     g.close()
     line = {
-        "metric": "DSSA doubling: seconds to an (1 - 1/e - eps)-approximate seed set", "value": wall, "unit": "s",
+        "metric": "DSSA doubling: seconds to an (1 - 1/e - eps)-approximate seed set (k = 100)",
+        "value": runs["100"]["seconds"], "unit": "s",
         "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
         "config": {"workload": "chunglu-4e7-wc-dssa", "graph": "Chung-Lu directed, exponent 2.0, weighted cascade",
-                   "n": n, "m": m, "k": k, "eps": eps, "delta": delta, "n0": 1 << 16,
+                   "n": n, "m": m, "k": [1, 100, 1000], "eps": eps, "delta": delta, "n0": 1 << 16,
                    "n_max": args.dssa_max_samples},
-        "result": {key: (float(v) if isinstance(v, float) else int(v)) for key, v in res.items()},
-        "samples_per_s": 2 * res["samples"] / wall, "graph_load_s": load_s, "generate_s": t_gen,
-        "Gamma": info["Gamma"], "seeds_head": [int(x) for x in seeds[:10]],
+        "runs": runs, "graph_load_s": load_s, "generate_s": t_gen,
+        "Gamma": info["Gamma"], "seeds_head_k100": [int(x) for x in seeds[:10]],
     }
     print(json.dumps(line))
 
@@ -596,6 +654,18 @@ def main():
                 "traffic": (tps * T if tps is not None else None), "kernel": "k_sources + k_iis_lane + k_iis_warp + k_iis_cta",
                 "algorithmic_bytes": alg, "kernel_ms": sample_ms, "peak_kind": f"{peak_kind} hbm_gbs (burst)"}
 
+    # the second ceiling: integer ALU work of the coins, Philox4x32-10 blocks
+    # (4 coins each; 10 rounds of two 32x32->64 multiplies), against 64
+    # integer multiply-adds per clock per SM with each wide multiply counted
+    # as two, at the maximum SM clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+    alu_peak = sms * 64 / 40 * max_mhz * 1e6
+    alu_achieved = coins / 4 / (sample_ms / 1e3)
+    roofline_alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Philox blocks/s",
+                    "frac": alu_achieved / alu_peak, "kernel": "k_sources + k_iis_lane + k_iis_warp + k_iis_cta",
+                    "peak_kind": f"derived: {sms} SMs x 64 IMAD/clk / 40 per block x {max_mhz:.0f} MHz"}
+
     # ---- influence-oracle serving (queries/s, p50/p99)
     serving = None if args.no_serving else serving_benchmark(skis, torch, dev, stream)
     variants = None if args.no_variants else variants_benchmark(skis, torch, dev, stream, n, d_src, d_dst, d_p, T,
@@ -615,6 +685,21 @@ def main():
         dt = time.perf_counter() - t0
         cpu = {"value": done / dt, "unit": "RR sets/s", "cores": 1, "kind": "oracle",
                "sample": f"sample ids 0..{done - 1} of the same workload (single-threaded C oracle)"}
+        # the same oracle on every host core (worker processes over disjoint id ranges)
+        cores = host_cores()
+        if cores > 1:
+            pool = oracle_pool(n, src, dst, p, args.first_step == "bucket", cores)
+            per_core = 20_000
+            pool_step(pool, seed, 0, 1000, cores)  # workers ready
+            start, t0 = 0, time.perf_counter()
+            while time.perf_counter() - t0 < args.cpu_seconds:
+                pool_step(pool, seed, start, per_core, cores)
+                start += per_core * cores
+            dt_all = time.perf_counter() - t0
+            pool.close()
+            pool.join()
+            cpu["all_cores"] = {"value": start / dt_all, "unit": "RR sets/s", "cores": cores,
+                                "sample": f"sample ids 0..{start - 1}, {cores} worker processes"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "RR sets/s", "n_gpus": world, "steps": args.steps,
@@ -632,6 +717,7 @@ def main():
                           "passes": stats[-1]["last_passes"], "arena_capacity": stats[-1]["arena_capacity"]},
         "per_sample": {"members": entries / T, "coins": coins / T},
         "roofline": roofline,
+        "roofline_alu": roofline_alu,
         "serving": serving,
         "variants": variants,
         "cpu_baseline": cpu,
