@@ -502,6 +502,8 @@ __global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs 
     __shared__ uint64_t s_big_off[kBigQueue];
     __shared__ uint32_t s_big_len[kBigQueue];
     __shared__ uint32_t s_nbig;
+    __shared__ KeyId s_best;  // this block's best of the previous round
+    __shared__ int s_reuse;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t one_f = 1ull << a.f;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -509,11 +511,25 @@ __global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs 
         s_hkey[i] = kHotEmpty;
         s_hcnt[i] = 0;
     }
-    if (threadIdx.x == 0) s_nbig = 0;
+    if (threadIdx.x == 0) {
+        s_nbig = 0;
+        s_best = KeyId{0, 0xFFFFFFFFu, 0};
+    }
     uint64_t cov = 0, sum_c = 0;  // running totals, kept by block 0
     __syncthreads();
     for (int32_t round = 0; round < a.k; ++round) {
+        // keys only decrease, so if the block's previous best is still
+        // outside S with an unchanged Delta it is still the block's best
+        // (every other key is at most what it was; ties keep the lowest id)
+        if (threadIdx.x == 0) {
+            int reuse = 0;
+            if (s_best.valid) reuse = !a.inS[s_best.id] && __ldcg(a.delta + s_best.id) == s_best.d;
+            s_reuse = reuse;
+        }
+        __syncthreads();
+        const bool reuse = s_reuse != 0;
         KeyId best{0, 0xFFFFFFFFu, 0};
+        if (!reuse) {
         // four of the thread's vertices per pass, their loads issued together
         // (a vertex's S flag is written only by the thread that scans it)
         for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v0 < a.n; v0 += 4 * stride) {
@@ -540,6 +556,10 @@ __global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs 
             }
         }
         best = block_best(best, s_part);
+        if (threadIdx.x == 0) s_best = best;
+        } else {
+            best = s_best;
+        }
         if (threadIdx.x == 0) a.partial[blockIdx.x] = best;
         grid.sync();
         if (wib == 0) {
