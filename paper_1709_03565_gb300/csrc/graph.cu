@@ -305,8 +305,8 @@ void graph_release(skis_graph* g) {
     g->perm = nullptr; g->w = nullptr; g->alias = nullptr; g->lt_cum = nullptr; g->chain = nullptr;
 }
 
-// IC graphs keep the chain from loading (k_gamma); this builds it for a
-// graph that has none.
+// IC graphs keep the chain from loading (k_gamma); a graph without one gets
+// it built here.
 int graph_ensure_chain(const skis_graph* gc, cudaStream_t st, std::string* err) {
     skis_graph* g = const_cast<skis_graph*>(gc);
     if (g->chain || g->m == 0) return SKIS_OK;
