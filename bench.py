@@ -587,12 +587,18 @@ def main():
     launches0 = skis.skis_kernel_launches()
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     e0.record(stream)
-    stats = [step() for _ in range(args.steps)]
+    marks[0].record(stream)
+    stats = []
+    for i in range(args.steps):
+        stats.append(step())
+        marks[i + 1].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
+    step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(args.steps)]
     launches = skis.skis_kernel_launches() - launches0
     elapsed_ms = reduce_over_ranks(e0.elapsed_time(e1), "max")
     value = reduce_over_ranks(args.steps * T, "sum") / (elapsed_ms / 1e3)
@@ -711,6 +717,7 @@ def main():
                    "first_step": args.first_step + (" (Eq. probn)" if args.first_step == "bucket" else " rounds"),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "sampled_edges_per_s": world * args.steps * coins / (elapsed_ms / 1e3),
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
         "sampling_only": {"rr_sets_per_s": T / (sample_ms / 1e3), "edges_per_s": coins / (sample_ms / 1e3),
                           "thread_tier_ms": thread_ms, "warp_tier_ms": warp_ms, "cta_tier_ms": cta_ms,
                           "to_warp_tier": stats[-1]["to_warp"], "to_cta_tier": stats[-1]["deferred"],

@@ -110,7 +110,7 @@ typedef enum skis_option {
     SKIS_OPT_RETRY_CAP = 0,      /* cap on rejected first-step rounds (default 2^24) */
     SKIS_OPT_CTA_SLOTS = 1,      /* CTAs of the CTA tier (default 2 per SM) */
     SKIS_OPT_WARP_BLOCKS = 2,    /* CTAs of the warp tier (default: full occupancy) */
-    SKIS_OPT_THREAD_MAX_DEG = 3, /* longest in-row the thread tier expands (default 256; 0 = tier off) */
+    SKIS_OPT_THREAD_MAX_DEG = 3, /* longest in-row the thread tier expands (default 192; 0 = tier off) */
     SKIS_OPT_THREAD_BLOCKS = 4,  /* CTAs of the thread tier (default: full occupancy) */
     SKIS_OPT_QUERY_INDEX = 5,    /* skis_estimate: 0 = walk the inverted index (vertex -> samples) when
                                     it is built for the current samples, else scan the sketch (default);
@@ -193,7 +193,7 @@ int skis_sketch_set_option(skis_sketch *s, int option, uint64_t value);
 
 /* Autotuner of the sampling tiers: times pilot sampling of ids
  * [0, pilot_samples) on a scratch sketch under each candidate split
- * (SKIS_OPT_THREAD_MAX_DEG in {0, 64, 128, 256, 512, 1024} x
+ * (SKIS_OPT_THREAD_MAX_DEG in {0, 64, 128, 192, 256, 512} x
  * SKIS_OPT_THREAD_MAX_STEPS in {128, 256, 1024}), keeps the fastest on s and
  * reports it (outputs nullable; candidate_ms receives up to candidate_cap
  * pilot times in that order, candidates_out their number). The pilot samples

@@ -904,38 +904,47 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                 if (2u * threadIdx.x + 1 < nw) s_pre[2u * threadIdx.x + 1] = before + pair;
                 __syncthreads();
                 const uint32_t total = s_pre[nw - 1];
-                for (uint32_t c = wid; c * 32u < total; c += kWarps) {
-                    const uint32_t g = c * 32u + lane;
-                    int32_t c0 = -1, c1 = -1, c2 = -1, c3 = -1;
-                    if (g < total) {
-                        uint32_t i = 0;  // the row of quad g: entries with prefix <= g
-#pragma unroll
-                        for (uint32_t b = kCtaWin / 2; b; b >>= 1)
-                            if (i + b - 1 < nw && s_pre[i + b - 1] <= g) i += b;
-                        const uint32_t lo = s_lo[i], hi = s_hi[i], tr = s_tau[i];
-                        const uint32_t q = (lo >> 2) + (g - (i ? s_pre[i - 1] : 0u));
-                        const uint4 xq = coin_block(a.seed, q, 0, kDomBfs, j);
-                        const uint4 t4 = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q)
-                                               : make_uint4(tr, tr, tr, tr);
-                        const uint32_t e0 = q << 2;
-                        unsigned live = 0;
-                        live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(xq.x, t4.x)) ? 1u : 0u;
-                        live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(xq.y, t4.y)) ? 2u : 0u;
-                        live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(xq.z, t4.z)) ? 4u : 0u;
-                        live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(xq.w, t4.w)) ? 8u : 0u;
-                        if (live) {
-                            const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
-                            if (live & 1u) c0 = s4.x;
-                            if (live & 2u) c1 = s4.y;
-                            if (live & 4u) c2 = s4.z;
-                            if (live & 8u) c3 = s4.w;
-                        }
+                // the live candidates of quad g (none when g is past the window)
+                auto draw = [&](uint32_t g, int32_t* c) {
+                    c[0] = c[1] = c[2] = c[3] = -1;
+                    if (g >= total) return;
+                    uint32_t i = 0;  // the row of quad g: entries with prefix <= g
+                    // (steps from the window's own size: a lone hub row needs none)
+                    for (uint32_t b = nw > 1 ? 1u << (31 - __clz(nw - 1)) : 0u; b; b >>= 1)
+                        if (i + b - 1 < nw && s_pre[i + b - 1] <= g) i += b;
+                    const uint32_t lo = s_lo[i], hi = s_hi[i], tr = s_tau[i];
+                    const uint32_t q = (lo >> 2) + (g - (i ? s_pre[i - 1] : 0u));
+                    const uint4 xq = coin_block(a.seed, q, 0, kDomBfs, j);
+                    const uint4 t4 = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q)
+                                           : make_uint4(tr, tr, tr, tr);
+                    const uint32_t e0 = q << 2;
+                    unsigned live = 0;
+                    live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(xq.x, t4.x)) ? 1u : 0u;
+                    live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(xq.y, t4.y)) ? 2u : 0u;
+                    live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(xq.z, t4.z)) ? 4u : 0u;
+                    live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(xq.w, t4.w)) ? 8u : 0u;
+                    if (live) {
+                        const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
+                        if (live & 1u) c[0] = s4.x;
+                        if (live & 2u) c[1] = s4.y;
+                        if (live & 4u) c[2] = s4.z;
+                        if (live & 8u) c[3] = s4.w;
                     }
-                    if (__any_sync(kFull, (c0 >= 0) | (c1 >= 0) | (c2 >= 0) | (c3 >= 0))) {
-                        if (__any_sync(kFull, c0 >= 0)) ins.insert(c0);
-                        if (__any_sync(kFull, c1 >= 0)) ins.insert(c1);
-                        if (__any_sync(kFull, c2 >= 0)) ins.insert(c2);
-                        if (__any_sync(kFull, c3 >= 0)) ins.insert(c3);
+                };
+                // two chunks of 32 quads per warp step: independent Philox
+                // blocks and loads per lane
+                for (uint32_t c = 2 * wid; c * 32u < total; c += 2 * kWarps) {
+                    int32_t ca[4], cb[4];
+                    draw(c * 32u + lane, ca);
+                    draw((c + 1) * 32u + lane, cb);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int32_t* cc = h ? cb : ca;
+                        if (__any_sync(kFull, (cc[0] >= 0) | (cc[1] >= 0) | (cc[2] >= 0) | (cc[3] >= 0))) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (__any_sync(kFull, cc[k] >= 0)) ins.insert(cc[k]);
+                        }
                     }
                 }
                 __syncthreads();  // the window's shared arrays are reused
@@ -1644,7 +1653,7 @@ int sketch_sample_to_size(skis_sketch* s, uint64_t target, uint64_t max_count, c
 // time is compared.
 int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* cand_ms, int cand_cap, int* ncand,
                     std::string* err) {
-    static const uint32_t kDeg[] = {0, 64, 128, 256, 512, 1024};
+    static const uint32_t kDeg[] = {0, 64, 128, 192, 256, 512};
     static const uint32_t kSteps[] = {128, 256, 1024};
     skis_sketch tmp;
     tmp.g = s->g;

@@ -224,7 +224,7 @@ struct skis_sketch {
     int cta_slots = 0;                   // 0 = automatic
     int warp_blocks = 0;                 // 0 = automatic
     int thread_blocks = 0;               // 0 = automatic
-    uint32_t thread_max_deg = 256;       // longest in-row the thread tier expands (0 = tier off)
+    uint32_t thread_max_deg = 192;       // longest in-row the thread tier expands (0 = tier off)
     uint32_t thread_max_steps = 256;     // edge quads per sample in the thread tier
     uint32_t thread_max_retries = 32;    // rejected rounds in the thread tier before the warp tier
     // last-call statistics

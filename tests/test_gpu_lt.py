@@ -129,3 +129,34 @@ def test_lt_rejects_rows_above_one():
     g = skis.skis_load_graph_lt(4, src, dst, np.array([0.5, 0.3, 0.2]), skis.SKIS_W_EXPLICIT_P)
     assert skis.skis_graph_get_info(g)["diffusion"] == skis.SKIS_DIFF_LT
     g.close()
+
+
+def test_lt_sketch_through_the_server_and_noalloc():
+    # queries on an LT sketch through the server and the no-allocation entry
+    # point give skis_estimate's exact results
+    n, g, o = _pair("chunglu-wc")
+    s = skis.skis_sketch_create(g, 0x1717)
+    skis.skis_sample(s, 100_000)
+    off, seeds = synth.seed_sets(n, [1, 5, 50] * 6, 97)
+    cov, est = skis.skis_estimate(s, off, seeds)
+    srv = skis.skis_server_create(s, slots=2, max_batch=8)
+    tickets = [skis.skis_server_submit(srv, seeds[off[b]:off[b + 1]]) for b in range(len(off) - 1)]
+    skis.skis_server_progress(srv, wait=True)
+    while True:
+        res = [skis.skis_server_poll(srv, t) for t in tickets]
+        if all(r[0] == 1 for r in res):
+            break
+        skis.skis_server_progress(srv, wait=True)
+    assert np.array_equal(np.array([r[1] for r in res]), cov)
+    assert np.array_equal(np.array([r[2] for r in res]), est)
+    srv.close()
+    import torch
+
+    dev = torch.device("cuda", 0)
+    d_off, d_seeds = torch.from_numpy(off).to(dev), torch.from_numpy(seeds).to(dev)
+    d_cov = torch.empty(len(off) - 1, dtype=torch.int64, device=dev)
+    d_est = torch.empty(len(off) - 1, dtype=torch.float64, device=dev)
+    skis.skis_estimate_noalloc(s, d_off, d_seeds, d_cov, d_est)
+    assert np.array_equal(d_cov.cpu().numpy(), cov) and np.array_equal(d_est.cpu().numpy(), est)
+    s.close()
+    g.close()

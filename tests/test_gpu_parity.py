@@ -313,7 +313,7 @@ def test_autotuned_split_gives_the_same_samples(er_small):
     spec, src, dst, g, o, osk, seed, T = er_small
     s = skis.skis_sketch_create(g, seed)
     tune = skis.skis_sketch_autotune(s, 20_000)
-    assert tune["max_deg"] in (0, 64, 128, 256, 512, 1024) and tune["max_steps"] in (128, 256, 1024)
+    assert tune["max_deg"] in (0, 64, 128, 192, 256, 512) and tune["max_steps"] in (128, 256, 1024)
     assert len(tune["candidate_ms"]) == 16 and all(x > 0 for x in tune["candidate_ms"])
     skis.skis_sample(s, 30_000)
     dev = skis.skis_sketch_export(s, 0, 30_000)
