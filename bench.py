@@ -57,6 +57,9 @@ def _args():
                          "chunglu-4e7-wc-dssa (DSSA doubling)")
     ap.add_argument("--samples", type=int, default=200_000, help="samples of the bounded R-MAT run")
     ap.add_argument("--dssa-max-samples", type=int, default=1 << 26, help="sample cap of the DSSA run")
+    ap.add_argument("--rmat-scale", type=int, default=25,
+                    help="R-MAT levels of the bounded run (25; smaller for profiler captures)")
+    ap.add_argument("--no-autotune", action="store_true", help="R-MAT run: default tier split")
     ap.add_argument("--first-step", default="bucket", choices=["bucket", "rejection"],
                     help="form of Alg. 1's conditioned first step (Eq. probn buckets, or rejection rounds)")
     ap.add_argument("--profile-step", action="store_true",
@@ -407,7 +410,11 @@ def rmat_run(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
-    spec, src, dst, _ = synth.workload("rmat-2^25-wc")
+    if args.rmat_scale == 25:
+        spec, src, dst, _ = synth.workload("rmat-2^25-wc")
+    else:  # the same generator at a smaller scale (32 edges a vertex)
+        spec = {"n": 1 << args.rmat_scale, "m": 32 << args.rmat_scale}
+        src, dst = synth.rmat(args.rmat_scale, spec["m"], 0.57, 0.19, 0.19, 3)
     t_gen = time.perf_counter() - t0
     n, m = spec["n"], spec["m"]
     d_src, d_dst = torch.from_numpy(src).to(dev), torch.from_numpy(dst).to(dev)
@@ -424,7 +431,7 @@ def rmat_run(args):
     torch.cuda.empty_cache()
     info = skis.skis_graph_get_info(g)
     s = skis.skis_sketch_create(g, SKETCH_SEED + 3, args.samples * 64, stream=stream)
-    tune = skis.skis_sketch_autotune(s, max(2000, args.samples // 20), stream=stream)
+    tune = None if args.no_autotune else skis.skis_sketch_autotune(s, max(2000, args.samples // 20), stream=stream)
     skis.skis_sample(s, args.samples, stream=stream)
     st = skis.skis_sketch_stats(s)
     e0.record(stream)
@@ -438,7 +445,8 @@ def rmat_run(args):
         "metric": METRIC, "value": args.samples / sample_s, "unit": "RR sets/s", "n_gpus": 1, "steps": 1,
         "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": "rmat-2^25-wc", "graph": "R-MAT (0.57, 0.19, 0.19, 0.05), weighted cascade",
+        "config": {"workload": "rmat-2^25-wc" if args.rmat_scale == 25 else f"rmat-2^{args.rmat_scale}-wc",
+                   "graph": "R-MAT (0.57, 0.19, 0.19, 0.05), weighted cascade",
                    "n": n, "m": m, "samples": args.samples, "bounded_run": True},
         "sampled_edges_per_s": st["coins"] / sample_s,
         "per_sample": {"members": st["entries"] / args.samples, "coins": st["coins"] / args.samples},
