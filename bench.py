@@ -430,7 +430,9 @@ def rmat_run(args):
     del d_src, d_dst
     torch.cuda.empty_cache()
     info = skis.skis_graph_get_info(g)
-    s = skis.skis_sketch_create(g, SKETCH_SEED + 3, args.samples * 64, stream=stream)
+    # member arena for ~94 members a sample with room to spare: an arena that
+    # fills up makes skis_sample grow it and rerun the samples that missed
+    s = skis.skis_sketch_create(g, SKETCH_SEED + 3, args.samples * 256, stream=stream)
     tune = None if args.no_autotune else skis.skis_sketch_autotune(s, max(2000, args.samples // 20), stream=stream)
     skis.skis_sample(s, args.samples, stream=stream)
     st = skis.skis_sketch_stats(s)
@@ -453,7 +455,8 @@ def rmat_run(args):
         "seconds_for_1e8_samples": 1e8 / (args.samples / sample_s),
         "graph_load_ms": load_ms, "generate_s": t_gen, "Gamma": info["Gamma"],
         "tiers_ms": {"thread": st["last_thread_ms"], "warp": st["last_warp_ms"], "cta": st["last_cta_ms"]},
-        "to_warp_tier": st["to_warp"], "to_cta_tier": st["deferred"], "autotune": tune,
+        "to_warp_tier": st["to_warp"], "to_cta_tier": st["deferred"], "passes": st["last_passes"],
+        "autotune": tune,
         "greedy_k100_ms": greedy_ms, "greedy_coverage": int(cov[-1]), "greedy_estimate": float(est[-1]),
         "device_memory_used_gb": (free0 - free1) / 1e9,
     }

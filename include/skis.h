@@ -98,13 +98,16 @@ typedef struct skis_stats {
     double last_cta_ms;      /* device time of the last CTA-tier sampling launch(es) */
     double last_sample_ms;   /* device time of all sampling launches of the last skis_sample call */
     uint64_t last_passes;    /* sampling passes of the last call (> 1: the arena grew and reran) */
+    uint64_t thread_max_deg;   /* the tier split in force (SKIS_OPT_THREAD_MAX_DEG, ...) */
+    uint64_t thread_max_steps;
+    uint64_t warp_max_coins;
 } skis_stats;
 
 /* Sampling runs in three tiers chained by sample id: one lane per sample
  * (up to 32 members, in-rows up to THREAD_MAX_DEG edges, up to
  * THREAD_MAX_STEPS edge quads, up to THREAD_MAX_RETRIES rejected rounds;
  * the "thread" names below refer to this tier), one warp per sample (up to
- * 256 members), one CTA per sample (any size). Options tune the split; they
+ * 256 members, up to WARP_MAX_COINS in-edges), one CTA per sample (any size). Options tune the split; they
  * never change the samples. */
 typedef enum skis_option {
     SKIS_OPT_RETRY_CAP = 0,      /* cap on rejected first-step rounds (default 2^24) */
@@ -133,7 +136,10 @@ typedef enum skis_option {
                                       domain BUCKET = 6, sample j); the first e with 2^62 - Q_e > z is
                                       live and the in-edges after it get their FIRST coins of round 0.
                                       IC graphs, IIS sampler; set before the first skis_sample; reads
-                                      the per-edge chain IC graphs keep from loading. */
+                                      the per-edge chain IC graphs keep from loading. */,
+    SKIS_OPT_WARP_MAX_COINS = 10   /* in-edges a sample's BFS may draw in the warp tier before the CTA
+                                      tier (all warps of a block on one sample) takes it over
+                                      (default 65536; samples that reach huge in-rows) */
 } skis_option;
 
 /* Load G = (V, E, w) (Sec. II-A) and build the device structures every later
@@ -192,12 +198,15 @@ int skis_sketch_create(skis_sketch **out, const skis_graph *g, uint64_t seed,
 int skis_sketch_set_option(skis_sketch *s, int option, uint64_t value);
 
 /* Autotuner of the sampling tiers: times pilot sampling of ids
- * [0, pilot_samples) on a scratch sketch under each candidate split
- * (SKIS_OPT_THREAD_MAX_DEG in {0, 64, 128, 192, 256, 512} x
- * SKIS_OPT_THREAD_MAX_STEPS in {128, 256, 1024}), keeps the fastest on s and
- * reports it (outputs nullable; candidate_ms receives up to candidate_cap
- * pilot times in that order, candidates_out their number). The pilot samples
- * are discarded; the samples of s never depend on the split. */
+ * [0, pilot_samples) on a scratch sketch under each candidate split, first
+ * the lane/warp split (SKIS_OPT_THREAD_MAX_DEG in {0, 64, 128, 192, 256, 512}
+ * x SKIS_OPT_THREAD_MAX_STEPS in {128, 256, 1024}, 16 candidates), then under
+ * the fastest of those the warp/CTA split (SKIS_OPT_WARP_MAX_COINS in {4096,
+ * 16384, 65536, 262144}); keeps the fastest on s and reports the lane/warp
+ * choice (outputs nullable; candidate_ms receives up to candidate_cap pilot
+ * times in that order, candidates_out their number; skis_sketch_stats gives
+ * the whole split). The pilot samples are discarded; the samples of s never
+ * depend on the split. */
 int skis_sketch_autotune(skis_sketch *s, uint64_t pilot_samples, uint32_t *chosen_max_deg,
                          uint32_t *chosen_max_steps, double *candidate_ms, int32_t candidate_cap,
                          int32_t *candidates_out, void *cuda_stream);

@@ -20,6 +20,7 @@ SKIS_MEM_HOST, SKIS_MEM_DEVICE = 0, 1
 SKIS_OPT_RETRY_CAP, SKIS_OPT_CTA_SLOTS, SKIS_OPT_WARP_BLOCKS = 0, 1, 2
 SKIS_OPT_THREAD_MAX_DEG, SKIS_OPT_THREAD_BLOCKS, SKIS_OPT_QUERY_INDEX, SKIS_OPT_THREAD_MAX_STEPS = 3, 4, 5, 6
 SKIS_OPT_SAMPLER, SKIS_OPT_THREAD_MAX_RETRIES, SKIS_OPT_FIRST_STEP = 7, 8, 9
+SKIS_OPT_WARP_MAX_COINS = 10
 SKIS_DIFF_IC, SKIS_DIFF_LT = 0, 1
 
 
@@ -41,7 +42,9 @@ class skis_stats(ctypes.Structure):
                 ("arena_reserved", ctypes.c_uint64), ("to_warp", ctypes.c_uint64),
                 ("deferred", ctypes.c_uint64), ("last_thread_ms", ctypes.c_double),
                 ("last_warp_ms", ctypes.c_double), ("last_cta_ms", ctypes.c_double),
-                ("last_sample_ms", ctypes.c_double), ("last_passes", ctypes.c_uint64)]
+                ("last_sample_ms", ctypes.c_double), ("last_passes", ctypes.c_uint64),
+                ("thread_max_deg", ctypes.c_uint64), ("thread_max_steps", ctypes.c_uint64),
+                ("warp_max_coins", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -255,7 +258,8 @@ def skis_sketch_autotune(s: Sketch, pilot_samples: int, stream=None) -> dict:
     ms = np.zeros(32, np.float64)
     _check(lib().skis_sketch_autotune(s.ptr, int(pilot_samples), ctypes.byref(d), ctypes.byref(m),
                                       ctypes.c_void_p(ms.ctypes.data), 32, ctypes.byref(nc), _stream(stream)))
-    return dict(max_deg=d.value, max_steps=m.value, candidate_ms=ms[: nc.value].tolist())
+    return dict(max_deg=d.value, max_steps=m.value, warp_max_coins=skis_sketch_stats(s)["warp_max_coins"],
+                candidate_ms=ms[: nc.value].tolist())
 
 
 def skis_sample(s: Sketch, count: int, stream=None) -> int:

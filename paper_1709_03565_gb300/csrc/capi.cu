@@ -220,6 +220,10 @@ extern "C" int skis_sketch_set_option(skis_sketch* s, int option, uint64_t value
             if (value < 1 || value > (1u << 24)) return fail(SKIS_EINVAL, "thread-tier retry limit must be in [1, 2^24]");
             s->thread_max_retries = (uint32_t)value;
             return SKIS_OK;
+        case SKIS_OPT_WARP_MAX_COINS:
+            if (value < 1 || value > (1u << 31)) return fail(SKIS_EINVAL, "warp-tier coin budget must be in [1, 2^31]");
+            s->warp_max_coins = (uint32_t)value;
+            return SKIS_OK;
         case SKIS_OPT_SAMPLER:
             if (value > 1) return fail(SKIS_EINVAL, "sampler must be 0 (IIS) or 1 (RIS)");
             if (s->T != 0) return fail(SKIS_EINVAL, "the sampler is chosen before the first sample");
@@ -396,6 +400,9 @@ extern "C" int skis_sketch_stats(const skis_sketch* s, skis_stats* out) {
     out->last_cta_ms = s->last_cta_ms;
     out->last_sample_ms = s->last_sample_ms;
     out->last_passes = s->last_passes;
+    out->thread_max_deg = s->thread_max_deg;
+    out->thread_max_steps = s->thread_max_steps;
+    out->warp_max_coins = s->warp_max_coins;
     if (s->T == 0) return SKIS_OK;
     cudaStream_t st = s->stream;
     unsigned long long* d = nullptr;

@@ -46,10 +46,12 @@ struct SampleArgs {
     const int32_t* __restrict__ src;
     const uint32_t* __restrict__ tau;  // nullptr: thresholds are per row
     uint64_t n, W, seed;
+    PhiloxKeys rk;                     // the round keys of seed
     uint32_t retry_cap;
     uint32_t max_deg;                  // thread tier: longest in-row it expands
     uint32_t max_steps;                // thread tier: edge quads per sample before handing it on
     uint32_t max_retries;              // thread tier: rejected rounds before handing it on
+    uint32_t warp_max_coins;           // warp tier: in-edges a BFS may draw before handing it on
     int ris;                           // plain RIS: uniform source, one unconditioned round
     // input ids: first_id + t (ids == nullptr) or ids[t], t < count (or
     // t < *count_dev when the list was filled by the previous tier)
@@ -113,7 +115,7 @@ __device__ __forceinline__ void arena_overflow(const SampleArgs& a, uint64_t j) 
 // Eq. probu through the alias table: column floor(U1 n), threshold draw
 // floor(U2 W) from the SRC-domain block of sample j.
 __device__ __forceinline__ uint32_t draw_source(const SampleArgs& a, uint64_t j) {
-    const uint4 x = coin_block(a.seed, 0, 0, kDomSrc, j);
+    const uint4 x = coin_block(a.rk, 0, 0, kDomSrc, j);
     const uint64_t u1 = (uint64_t)x.x | ((uint64_t)x.y << 32);
     const uint64_t u2 = (uint64_t)x.z | ((uint64_t)x.w << 32);
     const uint64_t col = __umul64hi(u1, a.n);
@@ -132,7 +134,7 @@ __device__ __forceinline__ uint32_t draw_source(const SampleArgs& a, uint64_t j)
 __device__ __forceinline__ uint64_t bucket_pick(const SampleArgs& a, uint64_t j, uint64_t off, uint32_t deg) {
     const uint64_t one62 = 1ull << 62;
     const uint64_t G = one62 - a.chain[off + deg - 1];
-    const uint4 x = coin_block(a.seed, 0, 0, kDomBucket, j);
+    const uint4 x = coin_block(a.rk, 0, 0, kDomBucket, j);
     const uint64_t z = __umul64hi((uint64_t)x.x | ((uint64_t)x.y << 32), G);
     const uint64_t lim = one62 - z;
     uint32_t lo = 0, hi = deg - 1;  // the answer exists: Q_d = 2^62 - G < lim
@@ -255,7 +257,7 @@ __device__ __forceinline__ bool expand_rows(const SampleArgs& a, uint64_t j, uin
         int32_t c0 = -1, c1 = -1, c2 = -1, c3 = -1;
         if (g < total) {
             const uint64_t q = (o_off >> 2) + (g - o_excl);
-            const uint4 x = coin_block(a.seed, q, retry, dom, j);
+            const uint4 x = coin_block(a.rk, q, retry, dom, j);
             const uint4 t4 = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q)
                                    : make_uint4(o_tau, o_tau, o_tau, o_tau);
             const uint64_t e0 = q << 2, lo = o_off, hi = o_off + o_deg;
@@ -337,7 +339,7 @@ __device__ __forceinline__ uint32_t first_step_warp(const SampleArgs& a, uint64_
         const uint32_t r = r0 + ri;
         unsigned live = 0;
         if (ri < rounds && r < a.retry_cap) {
-            const uint4 x = coin_block(a.seed, q, r, kDomFirst, j);
+            const uint4 x = coin_block(a.rk, q, r, kDomFirst, j);
             live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
             live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
             live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
@@ -585,9 +587,9 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
             const uint4 t4 = a.tau ? __ldg(tau4 + qc) : make_uint4(tau_row, tau_row, tau_row, tau_row);
             const uint4 t4b = (two && a.tau) ? __ldg(tau4 + qc + 1) : make_uint4(tau_row, tau_row, tau_row, tau_row);
             const uint32_t rr = first ? r : 0u, dom = first ? kDomFirst : kDomBfs;
-            const uint4 x = coin_block(a.seed, qc, rr, dom, j);
+            const uint4 x = coin_block(a.rk, qc, rr, dom, j);
             uint4 xb = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-            if (two) xb = coin_block(a.seed, qc + 1, rr, dom, j);
+            if (two) xb = coin_block(a.rk, qc + 1, rr, dom, j);
             const uint32_t e0 = qc << 2, e1 = e0 + 4;
             unsigned live = 0;
             live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
@@ -725,17 +727,26 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
 
             // lines 7-11: reverse BFS over the queue, up to 32 vertices at a time
             uint64_t coins = lane == 0 ? (uint64_t)rv.deg * (r + 1) : 0;
+            uint64_t drawn = 0;  // in-edges of the rows taken so far (warp-uniform)
+            bool heavy = false;
             uint32_t head = 1;
             while (head < ins.qlen && !ins.overflow) {
                 const uint32_t cnt = min(ins.qlen - head, 32u);
                 RowInfo rw;
                 rw.off = 0; rw.deg = 0; rw.tau = 0;
                 if ((uint32_t)lane < cnt) rw = a.rows[queue[head + lane]];
+                // a sample that reaches huge in-rows goes to the CTA tier,
+                // where every warp of a block shares its rows
+                drawn += __reduce_add_sync(kFull, min(rw.deg, 1u << 26));
+                if (drawn > a.warp_max_coins) {
+                    heavy = true;
+                    break;
+                }
                 coins += rw.deg;
                 expand_rows(a, j, kDomBfs, 0, rw.off, rw.deg, rw.tau, ins);
                 head += cnt;
             }
-            if (ins.overflow) {  // too large for shared memory: CTA tier
+            if (ins.overflow || heavy) {  // too large for shared memory or too many coins: CTA tier
                 if (lane == 0) hand_on(a, j);
                 continue;
             }
@@ -914,7 +925,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                         if (i + b - 1 < nw && s_pre[i + b - 1] <= g) i += b;
                     const uint32_t lo = s_lo[i], hi = s_hi[i], tr = s_tau[i];
                     const uint32_t q = (lo >> 2) + (g - (i ? s_pre[i - 1] : 0u));
-                    const uint4 xq = coin_block(a.seed, q, 0, kDomBfs, j);
+                    const uint4 xq = coin_block(a.rk, q, 0, kDomBfs, j);
                     const uint4 t4 = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q)
                                            : make_uint4(tr, tr, tr, tr);
                     const uint32_t e0 = q << 2;
@@ -1006,7 +1017,7 @@ __device__ __forceinline__ int32_t lt_step(const SampleArgs& a, uint64_t j, uint
     if (rw.deg == 0) return -1;
     const uint64_t base = a.lt_cum ? a.lt_cum[rw.off] : 0;
     const uint64_t S = a.lt_cum ? a.lt_cum[rw.off + rw.deg] - base : (uint64_t)rw.deg * lt_weight(rw.tau);
-    const uint4 b = coin_block(a.seed, t, 0, kDomLt, j);
+    const uint4 b = coin_block(a.rk, t, 0, kDomLt, j);
     uint64_t y;
     if (t == 0 && !a.ris) {
         y = __umul64hi((uint64_t)b.x | ((uint64_t)b.y << 32), S);  // Pr[u] = w(u, v) / gamma_v
@@ -1404,10 +1415,12 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.n = (uint64_t)g->n;
     base.W = g->W;
     base.seed = s->seed;
+    base.rk = philox_keys(s->seed);
     base.retry_cap = s->retry_cap;
     base.max_deg = s->thread_max_deg;
     base.max_steps = s->thread_max_steps;
     base.max_retries = s->thread_max_retries;
+    base.warp_max_coins = s->warp_max_coins;
     base.ris = s->ris;
     base.ids = nullptr;
     base.first_id = s->T;
@@ -1655,6 +1668,7 @@ int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* can
                     std::string* err) {
     static const uint32_t kDeg[] = {0, 64, 128, 192, 256, 512};
     static const uint32_t kSteps[] = {128, 256, 1024};
+    static const uint32_t kCoins[] = {4096, 16384, 65536, 262144};
     skis_sketch tmp;
     tmp.g = s->g;
     tmp.seed = s->seed;
@@ -1663,31 +1677,38 @@ int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* can
     tmp.vcount_ok = false;
     tmp.bucket = s->bucket;
     tmp.thread_max_retries = s->thread_max_retries;
+    tmp.warp_max_coins = s->warp_max_coins;
     tmp.cta_slots = s->cta_slots;
     tmp.warp_blocks = s->warp_blocks;
     tmp.thread_blocks = s->thread_blocks;
     tmp.stream = st;
     double best = 1e300;
-    uint32_t best_deg = s->thread_max_deg, best_steps = s->thread_max_steps;
+    uint32_t best_deg = s->thread_max_deg, best_steps = s->thread_max_steps, best_coins = s->warp_max_coins;
     int k = 0, rc = SKIS_OK;
+    // the pilot time of the current candidate (best of two runs)
+    auto time_pilot = [&]() -> double {
+        double ms = 1e300;
+        for (int rep = 0; rep < 2 && rc == SKIS_OK; ++rep) {
+            tmp.T = 0;
+            if (tmp.ctr) {
+                const cudaError_t e = cudaMemsetAsync(&tmp.ctr->arena, 0, sizeof(unsigned long long), st);
+                if (e != cudaSuccess) { *err = cudaGetErrorString(e); rc = SKIS_ERR_CUDA; }
+            }
+            if (rc == SKIS_OK) rc = sketch_sample(&tmp, pilot, st, err);
+            if (rc == SKIS_OK) ms = std::min(ms, tmp.last_sample_ms);
+        }
+        if (rc == SKIS_OK && cand_ms && k < cand_cap) cand_ms[k] = ms;
+        ++k;
+        return ms;
+    };
+    // first the lane/warp split, then the warp/CTA split under the chosen one
     for (uint32_t d : kDeg) {
         for (uint32_t m : kSteps) {
             if (d == 0 && m != kSteps[0]) continue;  // no thread tier: the budget is moot
             tmp.thread_max_deg = d;
             tmp.thread_max_steps = m;
-            double ms = 1e300;
-            for (int rep = 0; rep < 2 && rc == SKIS_OK; ++rep) {
-                tmp.T = 0;
-                if (tmp.ctr) {
-                    const cudaError_t e = cudaMemsetAsync(&tmp.ctr->arena, 0, sizeof(unsigned long long), st);
-                    if (e != cudaSuccess) { *err = cudaGetErrorString(e); rc = SKIS_ERR_CUDA; }
-                }
-                if (rc == SKIS_OK) rc = sketch_sample(&tmp, pilot, st, err);
-                if (rc == SKIS_OK) ms = std::min(ms, tmp.last_sample_ms);
-            }
+            const double ms = time_pilot();
             if (rc != SKIS_OK) break;
-            if (cand_ms && k < cand_cap) cand_ms[k] = ms;
-            ++k;
             if (ms < best) {
                 best = ms;
                 best_deg = d;
@@ -1696,11 +1717,23 @@ int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* can
         }
         if (rc != SKIS_OK) break;
     }
+    tmp.thread_max_deg = best_deg;
+    tmp.thread_max_steps = best_steps;
+    for (uint32_t c : kCoins) {
+        if (rc != SKIS_OK) break;
+        tmp.warp_max_coins = c;
+        const double ms = time_pilot();
+        if (rc == SKIS_OK && ms < best) {
+            best = ms;
+            best_coins = c;
+        }
+    }
     sketch_release(&tmp);
     if (ncand) *ncand = k;
     if (rc != SKIS_OK) return rc;
     s->thread_max_deg = best_deg;
     s->thread_max_steps = best_steps;
+    s->warp_max_coins = best_coins;
     return SKIS_OK;
 }
 

@@ -79,6 +79,46 @@ __device__ __forceinline__ uint4 coin_block(uint64_t seed, uint64_t q, uint32_t 
     return philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
+// The ten round keys of a Philox key, (k0 + i W0, k1 + i W1) for round i,
+// held in a kernel's parameters so that each round reads its key pair as an
+// operand instead of advancing it; the block is the same as philox10's.
+struct PhiloxKeys {
+    uint32_t k[20];
+};
+
+inline PhiloxKeys philox_keys(uint64_t seed) {
+    PhiloxKeys r;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        r.k[2 * i] = k0;
+        r.k[2 * i + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint4 philox10(uint4 c, const PhiloxKeys& rk) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint64_t pa = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t pb = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(pb >> 32) ^ c.y ^ rk.k[2 * i], (uint32_t)pb,
+                       (uint32_t)(pa >> 32) ^ c.w ^ rk.k[2 * i + 1], (uint32_t)pa);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 coin_block(const PhiloxKeys& rk, uint64_t q, uint32_t retry, uint32_t dom,
+                                            uint64_t j) {
+    uint4 c;
+    c.x = (uint32_t)q;
+    c.y = ((uint32_t)(q >> 32) & 0xFu) | ((retry & 0xFFFFFFu) << 4) | (dom << 28);
+    c.z = (uint32_t)j;
+    c.w = (uint32_t)(j >> 32);
+    return philox10(c, rk);
+}
+
 __device__ __forceinline__ uint32_t word_of(const uint4& x, int k) {
     return k == 0 ? x.x : k == 1 ? x.y : k == 2 ? x.z : x.w;
 }
@@ -227,6 +267,7 @@ struct skis_sketch {
     uint32_t thread_max_deg = 192;       // longest in-row the thread tier expands (0 = tier off)
     uint32_t thread_max_steps = 256;     // edge quads per sample in the thread tier
     uint32_t thread_max_retries = 32;    // rejected rounds in the thread tier before the warp tier
+    uint32_t warp_max_coins = 65536;     // in-edges a sample may draw in the warp tier before the CTA tier
     // last-call statistics
     uint64_t last_to_warp = 0, last_deferred = 0, last_passes = 0;
     double last_thread_ms = 0, last_warp_ms = 0, last_cta_ms = 0, last_sample_ms = 0;

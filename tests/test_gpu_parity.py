@@ -134,10 +134,14 @@ def test_er_workload_full_parity(er_small):
 def test_results_do_not_depend_on_launch_configuration(er_small):
     spec, src, dst, g, o, osk, seed, T = er_small
     ref = None
-    # (thread-tier degree limit, thread blocks, warp blocks, CTA slots, initial arena)
-    configs = ((None, 0, 0, 0, 0), (0, 0, 3, 1, 1000), (1 << 30, 5, 1000, 7, 50_000), (8, 1, 2, 2, 0))
-    for max_deg, thread_blocks, warp_blocks, cta_slots, arena in configs:
+    # (thread-tier degree limit, thread blocks, warp blocks, CTA slots, initial arena,
+    #  warp-tier coin budget)
+    configs = ((None, 0, 0, 0, 0, 0), (0, 0, 3, 1, 1000, 1), (1 << 30, 5, 1000, 7, 50_000, 0),
+               (8, 1, 2, 2, 0, 40), (0, 0, 0, 0, 0, 200))
+    for max_deg, thread_blocks, warp_blocks, cta_slots, arena, warp_coins in configs:
         s = skis.skis_sketch_create(g, seed, arena)
+        if warp_coins:
+            skis.skis_sketch_set_option(s, skis.SKIS_OPT_WARP_MAX_COINS, warp_coins)
         if max_deg is not None:
             skis.skis_sketch_set_option(s, skis.SKIS_OPT_THREAD_MAX_DEG, max_deg)
         if thread_blocks:
@@ -203,6 +207,11 @@ def test_bad_inputs_are_rejected():
         assert e.value.code == skis.SKIS_EINVAL
     with pytest.raises(skis.SkisError):
         skis.skis_greedy_maxcover(s, n + 1)
+    for opt, bad in ((skis.SKIS_OPT_WARP_MAX_COINS, 0), (skis.SKIS_OPT_WARP_MAX_COINS, (1 << 31) + 1),
+                     (skis.SKIS_OPT_THREAD_MAX_STEPS, 0), (99, 1)):
+        with pytest.raises(skis.SkisError) as e:
+            skis.skis_sketch_set_option(s, opt, bad)
+        assert e.value.code == skis.SKIS_EINVAL
     s.close()
     g.close()
     # Gamma = 0: no non-singular sample exists
@@ -314,7 +323,10 @@ def test_autotuned_split_gives_the_same_samples(er_small):
     s = skis.skis_sketch_create(g, seed)
     tune = skis.skis_sketch_autotune(s, 20_000)
     assert tune["max_deg"] in (0, 64, 128, 192, 256, 512) and tune["max_steps"] in (128, 256, 1024)
-    assert len(tune["candidate_ms"]) == 16 and all(x > 0 for x in tune["candidate_ms"])
+    assert tune["warp_max_coins"] in (4096, 16384, 65536, 262144)
+    assert len(tune["candidate_ms"]) == 20 and all(x > 0 for x in tune["candidate_ms"])
+    st = skis.skis_sketch_stats(s)
+    assert (st["thread_max_deg"], st["thread_max_steps"]) == (tune["max_deg"], tune["max_steps"])
     skis.skis_sample(s, 30_000)
     dev = skis.skis_sketch_export(s, 0, 30_000)
     ora = o.sample_ids(seed, np.arange(30_000, dtype=np.uint64))
