@@ -887,10 +887,11 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                         s_lo[i] = lo;
                         s_hi[i] = hi;
                         s_tau[i] = rw.tau;
-                        nq2[h] = rw.deg ? ((hi - 1) >> 2) - (lo >> 2) + 1 : 0u;
+                        // the row's edge quads, taken two at a time
+                        nq2[h] = rw.deg ? (((hi - 1) >> 2) - (lo >> 2) + 2) >> 1 : 0u;
                     }
                 }
-                // block-wide inclusive prefix of the quad counts
+                // block-wide inclusive prefix of the quad-pair counts
                 const uint32_t pair = nq2[0] + nq2[1];
                 uint32_t x = pair;
 #pragma unroll
@@ -915,47 +916,79 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                 if (2u * threadIdx.x + 1 < nw) s_pre[2u * threadIdx.x + 1] = before + pair;
                 __syncthreads();
                 const uint32_t total = s_pre[nw - 1];
-                // the live candidates of quad g (none when g is past the window)
+                // the live candidates of quad pair g (none when g is past the
+                // window): quads q and q + 1 of one row, two independent
+                // Philox blocks; a quad inside the row skips the edge bounds
                 auto draw = [&](uint32_t g, int32_t* c) {
-                    c[0] = c[1] = c[2] = c[3] = -1;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) c[k] = -1;
                     if (g >= total) return;
-                    uint32_t i = 0;  // the row of quad g: entries with prefix <= g
+                    uint32_t i = 0;  // the row of pair g: entries with prefix <= g
                     // (steps from the window's own size: a lone hub row needs none)
                     for (uint32_t b = nw > 1 ? 1u << (31 - __clz(nw - 1)) : 0u; b; b >>= 1)
                         if (i + b - 1 < nw && s_pre[i + b - 1] <= g) i += b;
                     const uint32_t lo = s_lo[i], hi = s_hi[i], tr = s_tau[i];
-                    const uint32_t q = (lo >> 2) + (g - (i ? s_pre[i - 1] : 0u));
-                    const uint4 xq = coin_block(a.rk, q, 0, kDomBfs, j);
-                    const uint4 t4 = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q)
+                    const uint32_t q = (lo >> 2) + 2u * (g - (i ? s_pre[i - 1] : 0u));
+                    const bool two = q < ((hi - 1) >> 2);
+                    const uint4 xa = coin_block(a.rk, q, 0, kDomBfs, j);
+                    uint4 xb = make_uint4(0, 0, 0, 0);
+                    if (two) xb = coin_block(a.rk, q + 1, 0, kDomBfs, j);
+                    const uint4 ta = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q)
                                            : make_uint4(tr, tr, tr, tr);
-                    const uint32_t e0 = q << 2;
+                    const uint4 tb = (a.tau && two) ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q + 1)
+                                                    : make_uint4(tr, tr, tr, tr);
+                    const uint32_t e0 = q << 2, e1 = e0 + 4;
                     unsigned live = 0;
-                    live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(xq.x, t4.x)) ? 1u : 0u;
-                    live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(xq.y, t4.y)) ? 2u : 0u;
-                    live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(xq.z, t4.z)) ? 4u : 0u;
-                    live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(xq.w, t4.w)) ? 8u : 0u;
-                    if (live) {
+                    if (e0 >= lo && e1 <= hi) {
+                        live |= coin_live(xa.x, ta.x) ? 1u : 0u;
+                        live |= coin_live(xa.y, ta.y) ? 2u : 0u;
+                        live |= coin_live(xa.z, ta.z) ? 4u : 0u;
+                        live |= coin_live(xa.w, ta.w) ? 8u : 0u;
+                    } else {
+                        live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(xa.x, ta.x)) ? 1u : 0u;
+                        live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(xa.y, ta.y)) ? 2u : 0u;
+                        live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(xa.z, ta.z)) ? 4u : 0u;
+                        live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(xa.w, ta.w)) ? 8u : 0u;
+                    }
+                    if (two) {  // e1 > lo: only the row's end bounds the second quad
+                        if (e1 + 4 <= hi) {
+                            live |= coin_live(xb.x, tb.x) ? 16u : 0u;
+                            live |= coin_live(xb.y, tb.y) ? 32u : 0u;
+                            live |= coin_live(xb.z, tb.z) ? 64u : 0u;
+                            live |= coin_live(xb.w, tb.w) ? 128u : 0u;
+                        } else {
+                            live |= (e1 + 0 < hi && coin_live(xb.x, tb.x)) ? 16u : 0u;
+                            live |= (e1 + 1 < hi && coin_live(xb.y, tb.y)) ? 32u : 0u;
+                            live |= (e1 + 2 < hi && coin_live(xb.z, tb.z)) ? 64u : 0u;
+                            live |= (e1 + 3 < hi && coin_live(xb.w, tb.w)) ? 128u : 0u;
+                        }
+                    }
+                    if (live & 15u) {
                         const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
                         if (live & 1u) c[0] = s4.x;
                         if (live & 2u) c[1] = s4.y;
                         if (live & 4u) c[2] = s4.z;
                         if (live & 8u) c[3] = s4.w;
                     }
+                    if (live & 240u) {
+                        const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q + 1);
+                        if (live & 16u) c[4] = s4.x;
+                        if (live & 32u) c[5] = s4.y;
+                        if (live & 64u) c[6] = s4.z;
+                        if (live & 128u) c[7] = s4.w;
+                    }
                 };
-                // two chunks of 32 quads per warp step: independent Philox
-                // blocks and loads per lane
-                for (uint32_t c = 2 * wid; c * 32u < total; c += 2 * kWarps) {
-                    int32_t ca[4], cb[4];
-                    draw(c * 32u + lane, ca);
-                    draw((c + 1) * 32u + lane, cb);
+                // one pair (64 quads) per lane and warp step
+                for (uint32_t c = wid; c * 32u < total; c += kWarps) {
+                    int32_t cc[8];
+                    draw(c * 32u + lane, cc);
+                    bool any = false;
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int32_t* cc = h ? cb : ca;
-                        if (__any_sync(kFull, (cc[0] >= 0) | (cc[1] >= 0) | (cc[2] >= 0) | (cc[3] >= 0))) {
+                    for (int k = 0; k < 8; ++k) any |= cc[k] >= 0;
+                    if (__any_sync(kFull, any)) {
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                if (__any_sync(kFull, cc[k] >= 0)) ins.insert(cc[k]);
-                        }
+                        for (int k = 0; k < 8; ++k)
+                            if (__any_sync(kFull, cc[k] >= 0)) ins.insert(cc[k]);
                     }
                 }
                 __syncthreads();  // the window's shared arrays are reused
