@@ -55,7 +55,8 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD,
                     help=f"{WORKLOAD} (the benchmark line), rmat-2^25-wc (bounded-sample rates) or "
                          "chunglu-4e7-wc-dssa (DSSA doubling)")
-    ap.add_argument("--samples", type=int, default=200_000, help="samples of the bounded R-MAT run")
+    ap.add_argument("--samples", type=int, default=200_000,
+                    help="samples of the R-MAT run (200K: a bounded run; 100000000: the full count)")
     ap.add_argument("--dssa-max-samples", type=int, default=1 << 26, help="sample cap of the DSSA run")
     ap.add_argument("--rmat-scale", type=int, default=25,
                     help="R-MAT levels of the bounded run (25; smaller for profiler captures)")
@@ -398,10 +399,11 @@ def serving_benchmark(skis, torch, dev, stream):
 
 # ----------------------------------------------------------- R-MAT run
 def rmat_run(args):
-    """The R-MAT workload (2^25 vertices, 2^30 edges, weighted cascade) on a
-    bounded number of samples: weighted cascade on R-MAT reaches its hubs'
-    huge in-rows (about 10^6 coins per sample), so 10^8 samples are about
-    10^14 coin flips; the rates measured here set the time of any count."""
+    """The R-MAT workload (2^25 vertices, 2^30 edges, weighted cascade):
+    weighted cascade on R-MAT reaches its hubs' huge in-rows (about 10^6
+    coins per sample), so 10^8 samples are about 10^14 coin flips. The
+    default is a bounded number of samples whose rates set the time of any
+    count; --samples 100000000 generates the full count in one call."""
     import torch
 
     import paper_1709_03565_gb300 as skis
@@ -430,10 +432,11 @@ def rmat_run(args):
     del d_src, d_dst
     torch.cuda.empty_cache()
     info = skis.skis_graph_get_info(g)
-    # member arena for ~94 members a sample with room to spare: an arena that
+    # member arena for ~93 members a sample with room to spare: an arena that
     # fills up makes skis_sample grow it and rerun the samples that missed
-    s = skis.skis_sketch_create(g, SKETCH_SEED + 3, args.samples * 256, stream=stream)
-    tune = None if args.no_autotune else skis.skis_sketch_autotune(s, max(2000, args.samples // 20), stream=stream)
+    s = skis.skis_sketch_create(g, SKETCH_SEED + 3, args.samples * 128, stream=stream)
+    pilot = min(max(2000, args.samples // 20), 50_000)
+    tune = None if args.no_autotune else skis.skis_sketch_autotune(s, pilot, stream=stream)
     skis.skis_sample(s, args.samples, stream=stream)
     st = skis.skis_sketch_stats(s)
     e0.record(stream)
@@ -449,7 +452,7 @@ def rmat_run(args):
         "data": "synthetic",
         "config": {"workload": "rmat-2^25-wc" if args.rmat_scale == 25 else f"rmat-2^{args.rmat_scale}-wc",
                    "graph": "R-MAT (0.57, 0.19, 0.19, 0.05), weighted cascade",
-                   "n": n, "m": m, "samples": args.samples, "bounded_run": True},
+                   "n": n, "m": m, "samples": args.samples, "bounded_run": args.samples < 100_000_000},
         "sampled_edges_per_s": st["coins"] / sample_s,
         "per_sample": {"members": st["entries"] / args.samples, "coins": st["coins"] / args.samples},
         "seconds_for_1e8_samples": 1e8 / (args.samples / sample_s),

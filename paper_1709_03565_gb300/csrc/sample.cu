@@ -38,6 +38,9 @@ constexpr uint32_t kArenaChunk = 2048;        // entries reserved per arena atom
 constexpr uint32_t kLaneArenaChunk = 512;     // entries reserved per arena atomic (lane tiers)
 constexpr int kCtaThreads = 512;
 constexpr int kCtaWin = 2 * kCtaThreads;  // queued vertices per load-balanced CTA-tier window
+constexpr int kCtaGroupLog2 = 2;
+constexpr int kCtaGroup = 1 << kCtaGroupLog2;  // edge quads of a long row a CTA-tier lane draws per step
+constexpr int kCtaLongRow = 64;            // quads that make a row long
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 struct SampleArgs {
@@ -887,11 +890,19 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                         s_lo[i] = lo;
                         s_hi[i] = hi;
                         s_tau[i] = rw.tau;
-                        // the row's edge quads, taken two at a time
-                        nq2[h] = rw.deg ? (((hi - 1) >> 2) - (lo >> 2) + 2) >> 1 : 0u;
+                        nq2[h] = rw.deg ? ((hi - 1) >> 2) - (lo >> 2) + 1 : 0u;  // edge quads
                     }
                 }
-                // block-wide inclusive prefix of the quad-pair counts
+                // a window with a long row (a hub) deals its quads kCtaGroup at
+                // a time to amortise the row search; others one at a time, so
+                // that short rows keep every lane busy
+                const uint32_t gsh =
+                    __syncthreads_or(nq2[0] >= (uint32_t)kCtaLongRow || nq2[1] >= (uint32_t)kCtaLongRow)
+                        ? (uint32_t)kCtaGroupLog2 : 0u;  // group of 2^gsh quads
+                const uint32_t grp = 1u << gsh;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) nq2[h] = (nq2[h] + grp - 1) >> gsh;
+                // block-wide inclusive prefix of the quad-group counts
                 const uint32_t pair = nq2[0] + nq2[1];
                 uint32_t x = pair;
 #pragma unroll
@@ -916,79 +927,64 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                 if (2u * threadIdx.x + 1 < nw) s_pre[2u * threadIdx.x + 1] = before + pair;
                 __syncthreads();
                 const uint32_t total = s_pre[nw - 1];
-                // the live candidates of quad pair g (none when g is past the
-                // window): quads q and q + 1 of one row, two independent
-                // Philox blocks; a quad inside the row skips the edge bounds
-                auto draw = [&](uint32_t g, int32_t* c) {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) c[k] = -1;
-                    if (g >= total) return;
-                    uint32_t i = 0;  // the row of pair g: entries with prefix <= g
+                // quad group g (nothing when g is past the window): quads q ..
+                // q + grp - 1 of one row, independent Philox blocks; a
+                // quad inside the row skips the edge bounds. Returns the live
+                // edges as a bit mask (bit 4h + k: edge k of quad q + h).
+                auto draw = [&](uint32_t g, uint32_t* q_out) -> unsigned {
+                    *q_out = 0;
+                    if (g >= total) return 0u;
+                    uint32_t i = 0;  // the row of group g: entries with prefix <= g
                     // (steps from the window's own size: a lone hub row needs none)
                     for (uint32_t b = nw > 1 ? 1u << (31 - __clz(nw - 1)) : 0u; b; b >>= 1)
                         if (i + b - 1 < nw && s_pre[i + b - 1] <= g) i += b;
                     const uint32_t lo = s_lo[i], hi = s_hi[i], tr = s_tau[i];
-                    const uint32_t q = (lo >> 2) + 2u * (g - (i ? s_pre[i - 1] : 0u));
-                    const bool two = q < ((hi - 1) >> 2);
-                    const uint4 xa = coin_block(a.rk, q, 0, kDomBfs, j);
-                    uint4 xb = make_uint4(0, 0, 0, 0);
-                    if (two) xb = coin_block(a.rk, q + 1, 0, kDomBfs, j);
-                    const uint4 ta = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q)
-                                           : make_uint4(tr, tr, tr, tr);
-                    const uint4 tb = (a.tau && two) ? __ldg(reinterpret_cast<const uint4*>(a.tau) + q + 1)
-                                                    : make_uint4(tr, tr, tr, tr);
-                    const uint32_t e0 = q << 2, e1 = e0 + 4;
+                    const uint32_t q = (lo >> 2) + ((g - (i ? s_pre[i - 1] : 0u)) << gsh);
+                    const uint32_t q_last = (hi - 1) >> 2;
+                    *q_out = q;
                     unsigned live = 0;
-                    if (e0 >= lo && e1 <= hi) {
-                        live |= coin_live(xa.x, ta.x) ? 1u : 0u;
-                        live |= coin_live(xa.y, ta.y) ? 2u : 0u;
-                        live |= coin_live(xa.z, ta.z) ? 4u : 0u;
-                        live |= coin_live(xa.w, ta.w) ? 8u : 0u;
-                    } else {
-                        live |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(xa.x, ta.x)) ? 1u : 0u;
-                        live |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(xa.y, ta.y)) ? 2u : 0u;
-                        live |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(xa.z, ta.z)) ? 4u : 0u;
-                        live |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(xa.w, ta.w)) ? 8u : 0u;
-                    }
-                    if (two) {  // e1 > lo: only the row's end bounds the second quad
-                        if (e1 + 4 <= hi) {
-                            live |= coin_live(xb.x, tb.x) ? 16u : 0u;
-                            live |= coin_live(xb.y, tb.y) ? 32u : 0u;
-                            live |= coin_live(xb.z, tb.z) ? 64u : 0u;
-                            live |= coin_live(xb.w, tb.w) ? 128u : 0u;
+#pragma unroll
+                    for (int h = 0; h < kCtaGroup; ++h) {
+                        const uint32_t qh = q + h;
+                        if ((uint32_t)h >= grp || qh > q_last) break;
+                        const uint4 x = coin_block(a.rk, qh, 0, kDomBfs, j);
+                        const uint4 t4 = a.tau ? __ldg(reinterpret_cast<const uint4*>(a.tau) + qh)
+                                               : make_uint4(tr, tr, tr, tr);
+                        const uint32_t e0 = qh << 2;
+                        unsigned l4 = 0;
+                        if (e0 >= lo && e0 + 4 <= hi) {
+                            l4 |= coin_live(x.x, t4.x) ? 1u : 0u;
+                            l4 |= coin_live(x.y, t4.y) ? 2u : 0u;
+                            l4 |= coin_live(x.z, t4.z) ? 4u : 0u;
+                            l4 |= coin_live(x.w, t4.w) ? 8u : 0u;
                         } else {
-                            live |= (e1 + 0 < hi && coin_live(xb.x, tb.x)) ? 16u : 0u;
-                            live |= (e1 + 1 < hi && coin_live(xb.y, tb.y)) ? 32u : 0u;
-                            live |= (e1 + 2 < hi && coin_live(xb.z, tb.z)) ? 64u : 0u;
-                            live |= (e1 + 3 < hi && coin_live(xb.w, tb.w)) ? 128u : 0u;
+                            l4 |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
+                            l4 |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
+                            l4 |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
+                            l4 |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
                         }
+                        live |= l4 << (4 * h);
                     }
-                    if (live & 15u) {
-                        const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
-                        if (live & 1u) c[0] = s4.x;
-                        if (live & 2u) c[1] = s4.y;
-                        if (live & 4u) c[2] = s4.z;
-                        if (live & 8u) c[3] = s4.w;
-                    }
-                    if (live & 240u) {
-                        const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q + 1);
-                        if (live & 16u) c[4] = s4.x;
-                        if (live & 32u) c[5] = s4.y;
-                        if (live & 64u) c[6] = s4.z;
-                        if (live & 128u) c[7] = s4.w;
-                    }
+                    return live;
                 };
-                // one pair (64 quads) per lane and warp step
+                // one group (32 grp quads) per warp step; the
+                // sources of live edges are loaded only when some lane has one
                 for (uint32_t c = wid; c * 32u < total; c += kWarps) {
-                    int32_t cc[8];
-                    draw(c * 32u + lane, cc);
-                    bool any = false;
+                    uint32_t q;
+                    const unsigned live = draw(c * 32u + lane, &q);
+                    if (!__any_sync(kFull, live != 0u)) continue;
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) any |= cc[k] >= 0;
-                    if (__any_sync(kFull, any)) {
+                    for (int h = 0; h < kCtaGroup; ++h) {
+                        const unsigned lh = (live >> (4 * h)) & 15u;
+                        if (!__any_sync(kFull, lh != 0u)) continue;
+                        int4 s4 = make_int4(-1, -1, -1, -1);
+                        if (lh) s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q + h);
+                        const int32_t cand[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            if (__any_sync(kFull, cc[k] >= 0)) ins.insert(cc[k]);
+                        for (int k = 0; k < 4; ++k) {
+                            const int32_t u = ((lh >> k) & 1u) ? cand[k] : -1;
+                            if (__any_sync(kFull, u >= 0)) ins.insert(u);
+                        }
                     }
                 }
                 __syncthreads();  // the window's shared arrays are reused
