@@ -387,15 +387,10 @@ __global__ void __launch_bounds__(kCovThreads) k_fill_inverted(const uint64_t* _
         const uint64_t j0 = gidx * 32;
         const uint64_t j = j0 + lane;
         const bool valid = j < T;
+        // one slot reservation per entry: lanes rarely share a vertex, and
+        // the atomics of those that do are served at L2 in turn
         warp_members(valid ? h_off[j] : 0, valid ? h_len[j] : 0u, arena, [&](int owner, int32_t u) {
-            // lanes holding the same vertex reserve their slots with one atomic
-            const unsigned active = __activemask();
-            const unsigned peers = __match_any_sync(active, u);
-            const int leader = __ffs(peers) - 1;
-            uint32_t base = 0;
-            if ((threadIdx.x & 31) == leader) base = atomicAdd(&fill[u], (uint32_t)__popc(peers));
-            base = __shfl_sync(peers, base, leader);
-            const uint32_t pos = base + __popc(peers & lanemask_lt());
+            const uint32_t pos = atomicAdd(&fill[u], 1u);
             inv[inv_off[u] + pos] = (uint32_t)(j0 + owner);
         });
     }
