@@ -432,9 +432,10 @@ def rmat_run(args):
     del d_src, d_dst
     torch.cuda.empty_cache()
     info = skis.skis_graph_get_info(g)
-    # member arena for ~93 members a sample with room to spare: an arena that
-    # fills up makes skis_sample grow it and rerun the samples that missed
-    s = skis.skis_sketch_create(g, SKETCH_SEED + 3, args.samples * 128, stream=stream)
+    # member arena for ~93 members a sample with room to spare, plus the
+    # tiers' per-warp chunk reservations: an arena that fills up makes
+    # skis_sample grow it and rerun the samples that missed it
+    s = skis.skis_sketch_create(g, SKETCH_SEED + 3, args.samples * 128 + (1 << 23), stream=stream)
     pilot = min(max(2000, args.samples // 20), 50_000)
     tune = None if args.no_autotune else skis.skis_sketch_autotune(s, pilot, stream=stream)
     skis.skis_sample(s, args.samples, stream=stream)
