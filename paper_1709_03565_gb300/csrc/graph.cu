@@ -103,67 +103,31 @@ __global__ void k_rows(const uint64_t* __restrict__ off, int64_t n, int wc, RowI
 // Eq. gamma_v in fixed point: Q = 2^62; Q <- floor(Q (2^32 - tau) / 2^32) for
 // each in-edge in CSR order (0 on a sentinel); w_v = (2^62 - Q) >> s. With
 // chain != nullptr the running Q after every in-edge is kept as well.
-//
-// The product is sequential within a row (each step truncates), so one lane
-// runs one row. A warp takes 32 consecutive rows, whose edges are one
-// contiguous CSR range: when the range has at most kGammaStage edges the
-// warp reads its thresholds and writes its chain entries through shared
-// memory in coalesced runs; a longer range is worked on global memory.
-constexpr int kGammaWarps = 8;
-constexpr int kGammaStage = 512;
-
-__device__ __forceinline__ uint64_t gamma_step(uint64_t Q, uint32_t t) {
-    return t == kSentinel ? 0ull : (uint64_t)(((u128)Q * (u128)((1ull << 32) - t)) >> 32);
-}
-
-__global__ void __launch_bounds__(kGammaWarps * 32) k_gamma(const RowInfo* __restrict__ rows,
-                                                            const uint32_t* __restrict__ csr_tau, int64_t n, int s,
-                                                            uint64_t* __restrict__ w, uint64_t* __restrict__ chain) {
-    __shared__ uint32_t s_tau[kGammaWarps][kGammaStage];
-    __shared__ uint64_t s_q[kGammaWarps][kGammaStage];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+__global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __restrict__ csr_tau, int64_t n, int s,
+                        uint64_t* __restrict__ w, uint64_t* __restrict__ chain) {
     const uint64_t one62 = 1ull << 62;
-    const int64_t groups = (n + 31) / 32;
-    for (int64_t gi = (int64_t)blockIdx.x * kGammaWarps + wib; gi < groups; gi += (int64_t)gridDim.x * kGammaWarps) {
-        const int64_t v = gi * 32 + lane;
-        RowInfo r;
-        r.off = 0; r.deg = 0; r.tau = 0;
-        if (v < n) r = rows[v];
-        const int last = (int)min((int64_t)31, n - 1 - gi * 32);
-        const uint64_t e0 = __shfl_sync(kFull, r.off, 0);
-        const uint64_t e1 = __shfl_sync(kFull, r.off + r.deg, last);
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const RowInfo r = rows[v];
         uint64_t Q = one62;
-        if (e1 - e0 <= (uint64_t)kGammaStage) {
-            const uint32_t ne = (uint32_t)(e1 - e0), b = (uint32_t)(r.off - e0);
-            if (csr_tau)
-                for (uint32_t i = lane; i < ne; i += 32) s_tau[wib][i] = csr_tau[e0 + i];
-            __syncwarp();
-            for (uint32_t k = 0; k < r.deg && (Q != 0 || chain); ++k) {
-                Q = gamma_step(Q, csr_tau ? s_tau[wib][b + k] : r.tau);
-                s_q[wib][b + k] = Q;
-            }
-            __syncwarp();
-            if (chain)
-                for (uint32_t i = lane; i < ne; i += 32) chain[e0 + i] = s_q[wib][i];
-            __syncwarp();
-        } else {
-            uint32_t k = 0;
-            for (; k + 8 <= r.deg && (Q != 0 || chain); k += 8) {
-                uint32_t t[8];  // thresholds loaded 8 at a time ahead of the product
+        uint32_t k = 0;
+        for (; k + 8 <= r.deg && (Q != 0 || chain); k += 8) {
+            uint32_t t[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) t[i] = csr_tau ? csr_tau[r.off + k + i] : r.tau;
+            for (int i = 0; i < 8; ++i) t[i] = csr_tau ? csr_tau[r.off + k + i] : r.tau;
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    Q = gamma_step(Q, t[i]);
-                    if (chain) chain[r.off + k + i] = Q;
-                }
-            }
-            for (; k < r.deg && (Q != 0 || chain); ++k) {
-                Q = gamma_step(Q, csr_tau ? csr_tau[r.off + k] : r.tau);
-                if (chain) chain[r.off + k] = Q;
+            for (int i = 0; i < 8; ++i) {
+                if (t[i] == kSentinel) Q = 0;
+                else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t[i])) >> 32);
+                if (chain) chain[r.off + k + i] = Q;
             }
         }
-        if (v < n) w[v] = (one62 - Q) >> s;
+        for (; k < r.deg && (Q != 0 || chain); ++k) {
+            const uint32_t t = csr_tau ? csr_tau[r.off + k] : r.tau;
+            if (t == kSentinel) Q = 0;
+            else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t)) >> 32);
+            if (chain) chain[r.off + k] = Q;
+        }
+        w[v] = (one62 - Q) >> s;
     }
 }
 
@@ -458,9 +422,7 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     } else {
         // the chain is kept for the bucket form of the first step (8 bytes an edge)
         if (m > 0) GB_CUDA(dev_alloc_t(&g->chain, (size_t)m, st));
-        const int ggrid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 32 * kGammaWarps - 1) / (32 * kGammaWarps),
-                                                                      (int64_t)sm_count() * 8));
-        k_gamma<<<ggrid, kGammaWarps * 32, 0, st>>>(g->rows, g->tau, n, g->s, g->w, g->chain); note_launch();
+        k_gamma<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->s, g->w, g->chain); note_launch();
         GB_CUDA(cudaGetLastError());
     }
     GB_CUDA(sum_u64(g->w, n, d_W, st));

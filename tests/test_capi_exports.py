@@ -53,3 +53,42 @@ def test_bad_arguments_are_rejected_before_any_device_work():
                              ctypes.c_void_p(dst.ctypes.data), None, 9, 0, skis.SKIS_MEM_HOST, None)
     assert rc == skis.SKIS_EINVAL
     assert lib.skis_sketch_set_option(None, 0, 1) == skis.SKIS_EINVAL
+
+
+_CTYPES = {"int32_t": ctypes.c_int32, "uint32_t": ctypes.c_uint32, "int64_t": ctypes.c_int64,
+           "uint64_t": ctypes.c_uint64, "double": ctypes.c_double, "int": ctypes.c_int}
+
+
+def _header_text():
+    text = open(os.path.join(ROOT, "include", "skis.h")).read()
+    return re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+
+
+def test_binding_structs_match_the_header():
+    """Every struct the binding passes by pointer has the header's fields, in
+    order, with the same C types (a drifted layout would corrupt results)."""
+    text = _header_text()
+    for name in ("skis_graph_info", "skis_stats", "skis_dssa_result"):
+        body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), text, flags=re.S).group(1)
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            ctype, names = decl.split(None, 1)
+            for f in names.split(","):
+                fields.append((f.strip(), _CTYPES[ctype]))
+        ours = getattr(skis._binding, name)._fields_
+        assert [(f, t) for f, t in ours] == fields, name
+        hsize = sum(ctypes.sizeof(t) for _, t in fields)
+        assert ctypes.sizeof(getattr(skis._binding, name)) >= hsize
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, weight models, memory spaces, diffusion models and
+    sketch options carry the header's values."""
+    text = _header_text()
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(SKIS_[A-Z0-9_]+)\s*=\s*(\d+)", text))
+    assert len(consts) >= 25
+    for k, v in consts.items():
+        assert getattr(skis, k) == v, k
