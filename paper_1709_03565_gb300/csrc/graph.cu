@@ -131,35 +131,6 @@ __global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __rest
     }
 }
 
-// The gamma chain of every row kept edge by edge, for the bucket form of the
-// first step (Eq. probn): chain[e] = Q after in-edge e of its row, with the
-// same arithmetic as k_gamma, so that chain[last edge] >> s gives w_v back.
-__global__ void k_chain(const RowInfo* __restrict__ rows, const uint32_t* __restrict__ csr_tau, int64_t n,
-                        uint64_t* __restrict__ chain) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const RowInfo r = rows[v];
-        uint64_t Q = 1ull << 62;
-        uint32_t k = 0;
-        for (; k + 8 <= r.deg; k += 8) {  // thresholds loaded 8 at a time ahead of the product
-            uint32_t t[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) t[i] = csr_tau ? csr_tau[r.off + k + i] : r.tau;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (t[i] == kSentinel) Q = 0;
-                else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t[i])) >> 32);
-                chain[r.off + k + i] = Q;
-            }
-        }
-        for (; k < r.deg; ++k) {
-            const uint32_t t = csr_tau ? csr_tau[r.off + k] : r.tau;
-            if (t == kSentinel) Q = 0;
-            else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t)) >> 32);
-            chain[r.off + k] = Q;
-        }
-    }
-}
-
 // Linear Threshold model (Sec. "Extensions to other diffusion models"):
 // gamma_v = the sum of the row's weights, exactly, as w_v = sum tau' with
 // f = 32 (tau' = tau, or 2^32 for the always-live sentinel). A row above 1
@@ -305,24 +276,12 @@ void graph_release(skis_graph* g) {
     g->perm = nullptr; g->w = nullptr; g->alias = nullptr; g->lt_cum = nullptr; g->chain = nullptr;
 }
 
-// IC graphs keep the chain from loading (k_gamma); a graph without one gets
-// it built here.
-int graph_ensure_chain(const skis_graph* gc, cudaStream_t st, std::string* err) {
-    skis_graph* g = const_cast<skis_graph*>(gc);
+// IC graphs keep the chain from loading (k_gamma, 8 bytes an edge); LT
+// graphs have none, and the bucket form does not apply to them.
+int graph_ensure_chain(const skis_graph* g, cudaStream_t, std::string* err) {
     if (g->chain || g->m == 0) return SKIS_OK;
-    uint64_t* chain = nullptr;
-    cudaError_t e = dev_alloc_t(&chain, (size_t)g->m, st);
-    if (e == cudaSuccess) {
-        k_chain<<<sm_count() * 8, 256, 0, st>>>(g->rows, g->row_uniform ? nullptr : g->tau, g->n, chain); note_launch();
-        e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) {
-        dev_free(chain, st);
-        *err = std::string("CUDA error building the gamma chain: ") + cudaGetErrorString(e);
-        return e == cudaErrorMemoryAllocation ? SKIS_ENOMEM : SKIS_ERR_CUDA;
-    }
-    g->chain = chain;
-    return SKIS_OK;
+    *err = "the bucket form of the first step needs an IC graph (its gamma chain is kept from loading)";
+    return SKIS_EINVAL;
 }
 
 int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const void* d_weights, int model,
