@@ -117,8 +117,11 @@ __device__ __forceinline__ void arena_overflow(const SampleArgs& a, uint64_t j) 
 
 // Eq. probu through the alias table: column floor(U1 n), threshold draw
 // floor(U2 W) from the SRC-domain block of sample j.
+// (kSeedKey: the Philox keys advanced from the seed in registers, for a
+// kernel whose occupancy the preloaded round keys would cut)
+template <bool kSeedKey = false>
 __device__ __forceinline__ uint32_t draw_source(const SampleArgs& a, uint64_t j) {
-    const uint4 x = coin_block(a.rk, 0, 0, kDomSrc, j);
+    const uint4 x = kSeedKey ? coin_block(a.seed, 0, 0, kDomSrc, j) : coin_block(a.rk, 0, 0, kDomSrc, j);
     const uint64_t u1 = (uint64_t)x.x | ((uint64_t)x.y << 32);
     const uint64_t u2 = (uint64_t)x.z | ((uint64_t)x.w << 32);
     const uint64_t col = __umul64hi(u1, a.n);
@@ -134,10 +137,11 @@ __device__ __forceinline__ uint32_t draw_source(const SampleArgs& a, uint64_t j)
 // BUCKET-domain block of sample j picks the first edge e with
 // 2^62 - Q_e > z, i.e. Q_e < 2^62 - z (the chain does not increase).
 // Returns the edge position; the edges after it get FIRST coins of round 0.
+template <bool kSeedKey = false>
 __device__ __forceinline__ uint64_t bucket_pick(const SampleArgs& a, uint64_t j, uint64_t off, uint32_t deg) {
     const uint64_t one62 = 1ull << 62;
     const uint64_t G = one62 - a.chain[off + deg - 1];
-    const uint4 x = coin_block(a.rk, 0, 0, kDomBucket, j);
+    const uint4 x = kSeedKey ? coin_block(a.seed, 0, 0, kDomBucket, j) : coin_block(a.rk, 0, 0, kDomBucket, j);
     const uint64_t z = __umul64hi((uint64_t)x.x | ((uint64_t)x.y << 32), G);
     const uint64_t lim = one62 - z;
     uint32_t lo = 0, hi = deg - 1;  // the answer exists: Q_d = 2^62 - G < lim
@@ -399,11 +403,11 @@ __global__ void k_sources(SampleArgs a, uint4* __restrict__ rec, uint2* __restri
     for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count;
          t += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t j = input_id(a, t);
-        const uint32_t v = draw_source(a, j);
+        const uint32_t v = draw_source<true>(a, j);
         const RowInfo rv = a.rows[v];
         rec[t] = make_uint4(v, rv.deg, (uint32_t)rv.off, rv.tau);
         if (a.chain && rv.deg > 0) {  // the bucket form of the first step, drawn here in bulk
-            const uint64_t e = bucket_pick(a, j, rv.off, rv.deg);
+            const uint64_t e = bucket_pick<true>(a, j, rv.off, rv.deg);
             pick[t] = make_uint2((uint32_t)e, (uint32_t)a.src[e]);
         }
     }
