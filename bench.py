@@ -345,6 +345,42 @@ def variants_benchmark(skis, torch, dev, stream, n, d_src, d_dst, d_p, T, seed, 
     return res
 
 
+def coverage_benchmark(skis, torch, dev, stream, n, d_src, d_dst, d_p, T, seed, first_step, d_off, d_seeds, peak):
+    """Coverage counting of one batch of 64 queries (seed sets of 10) over the
+    bench sketch (10M samples), both ways: a scan of the whole sketch (headers
+    and members streamed once, per-vertex query masks gathered from L2) and a
+    walk of the inverted index (the lists of the queries' seeds)."""
+    g = skis.skis_load_graph(n, d_src, d_dst, d_p, skis.SKIS_W_EXPLICIT_P, stream=stream)
+    s = skis.skis_sketch_create(g, seed, int(T * 5.5), stream=stream)
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, first_step)
+    skis.skis_sample(s, T, stream=stream)
+    entries = skis.skis_sketch_stats(s)["entries"]
+    q = int(d_off.numel()) - 1
+    d_cov = torch.empty(q, dtype=torch.int64, device=dev)
+    d_est = torch.empty(q, dtype=torch.float64, device=dev)
+    out = {"queries": q, "query_size": QUERY_SIZE, "samples": T, "entries": entries}
+    for name, mode in (("scan", 2), ("index", 1)):
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_QUERY_INDEX, mode)
+        for _ in range(3):  # warm-up (the index walk builds the index on the first call)
+            skis.skis_estimate(s, d_off, d_seeds, d_cov, d_est, stream=stream)
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            skis.skis_estimate(s, d_off, d_seeds, d_cov, d_est, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_batch": ms, "queries_per_s": q / (ms / 1e3)}
+        if name == "scan":  # algorithmic bytes: 12-byte header per sample, 4 bytes per member
+            nbytes = 12 * T + 4 * entries
+            out[name].update({"algorithmic_bytes": nbytes, "gb_per_s": nbytes / (ms / 1e3) / 1e9,
+                              "frac_of_hbm_peak": nbytes / (ms / 1e3) / 1e9 / peak})
+    s.close()
+    g.close()
+    return out
+
+
 def serving_benchmark(skis, torch, dev, stream):
     """Influence-oracle serving on a device-resident sketch: saturation
     throughput (all requests at t = 0) of continuous batching versus one
@@ -687,7 +723,9 @@ def main():
                     "frac": alu_achieved / alu_peak, "kernel": "k_sources + k_iis_lane + k_iis_warp + k_iis_cta",
                     "peak_kind": f"derived: {sms} SMs x 64 IMAD/clk / 40 per block x {max_mhz:.0f} MHz"}
 
-    # ---- influence-oracle serving (queries/s, p50/p99)
+    # ---- coverage counting (GB/s of the sketch scan) and influence-oracle serving (queries/s, p50/p99)
+    coverage = coverage_benchmark(skis, torch, dev, stream, n, d_src, d_dst, d_p, T, seed, first_step, d_off, d_seeds,
+                                  peak)
     serving = None if args.no_serving else serving_benchmark(skis, torch, dev, stream)
     variants = None if args.no_variants else variants_benchmark(skis, torch, dev, stream, n, d_src, d_dst, d_p, T,
                                                                 seed, first_step)
@@ -740,6 +778,7 @@ def main():
         "per_sample": {"members": entries / T, "coins": coins / T},
         "roofline": roofline,
         "roofline_alu": roofline_alu,
+        "coverage": coverage,
         "serving": serving,
         "variants": variants,
         "cpu_baseline": cpu,

@@ -506,6 +506,7 @@ void skis::sketch_release(skis_sketch* s) {
     dev_free(s->lt_list, st);
     dev_free(s->lt_slot, st);
     dev_free(s->qmask, st);
+    dev_free(s->qbits, st);
     dev_free(s->inv_off, st);
     dev_free(s->inv, st);
     dev_free(s->smask, st);

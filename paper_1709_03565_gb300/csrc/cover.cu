@@ -85,8 +85,12 @@ __device__ __forceinline__ void sub_merged(uint32_t* counter, int32_t u, uint32_
 }
 
 // ------------------------------------------------------------- coverage
+// qbits (nullable): one bit per vertex, set for the batch's seeds, so that
+// the sketch scan gathers a vertex's 8-byte mask only when the vertex is a
+// seed (the bit array is small enough to stay in L1 and L2).
 __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
-                            int32_t qn, int64_t n, uint64_t* __restrict__ qmask, DevStatus* st) {
+                            int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits,
+                            DevStatus* st) {
     const int lane = threadIdx.x & 31;
     const int32_t b = q0 + (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (b >= q0 + qn) return;
@@ -100,6 +104,7 @@ __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __re
         const int32_t v = seeds[i];
         bool bad = v < 0 || v >= n;
         if (!bad) bad = (atomicOr((unsigned long long*)&qmask[v], (unsigned long long)bit) & bit) != 0;
+        if (!bad && qbits) atomicOr(&qbits[v >> 5], 1u << (v & 31));
         if (bad) {
             atomicOr(&st->flags, kStInval);
             atomicMin(&st->first_bad, (unsigned long long)b);
@@ -108,13 +113,16 @@ __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __re
 }
 
 __global__ void k_qmask_clear(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
-                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask) {
+                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits) {
     const int lane = threadIdx.x & 31;
     const int32_t b = q0 + (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (b >= q0 + qn) return;
     for (int64_t i = off[b] + lane; i < off[b + 1]; i += 32) {
         const int32_t v = seeds[i];
-        if (v >= 0 && v < n) qmask[v] = 0;
+        if (v >= 0 && v < n) {
+            qmask[v] = 0;
+            if (qbits) qbits[v >> 5] = 0;  // every bit set in the array is a seed of this batch
+        }
     }
 }
 
@@ -122,6 +130,7 @@ __global__ void __launch_bounds__(kCovThreads) k_coverage(const uint64_t* __rest
                                                           const uint32_t* __restrict__ h_len, uint64_t T,
                                                           const int32_t* __restrict__ arena,
                                                           const uint64_t* __restrict__ qmask,
+                                                          const uint32_t* __restrict__ qbits,
                                                           unsigned long long* __restrict__ cov) {
     __shared__ unsigned long long s_acc[kCovThreads / 32][32];
     __shared__ unsigned long long s_cnt[64];
@@ -140,6 +149,7 @@ __global__ void __launch_bounds__(kCovThreads) k_coverage(const uint64_t* __rest
         __syncwarp();
         unsigned long long* acc_row = s_acc[wib];
         warp_members(off, len, arena, [&](int owner, int32_t u) {
+            if (qbits && !((__ldg(qbits + (u >> 5)) >> (u & 31)) & 1u)) return;  // not a seed
             const uint64_t msk = qmask[u];
             if (msk) atomicOr(&acc_row[owner], (unsigned long long)msk);
         });
@@ -304,6 +314,8 @@ int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32
     if (!s->qmask) {
         CV_CUDA(dev_alloc_t(&s->qmask, (size_t)g->n, st));
         CV_CUDA(cudaMemsetAsync(s->qmask, 0, (size_t)g->n * sizeof(uint64_t), st));
+        CV_CUDA(dev_alloc_t(&s->qbits, (size_t)((g->n + 31) / 32), st));
+        CV_CUDA(cudaMemsetAsync(s->qbits, 0, (size_t)((g->n + 31) / 32) * sizeof(uint32_t), st));
         CV_CUDA(dev_alloc_t(&s->qcov, 64, st));
         CV_CUDA(dev_alloc_t(&s->qstatus, 1, st));
     }
@@ -330,19 +342,20 @@ int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32
         const int32_t qn = std::min<int32_t>(64, q - q0);
         const int wb = div_up((int64_t)qn * 32, 256);
         CV_CUDA(cudaMemsetAsync(s->qcov, 0, 64 * sizeof(unsigned long long), st));
-        k_qmask_set<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask, s->qstatus); note_launch();
+        k_qmask_set<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask, s->qbits, s->qstatus); note_launch();
         CV_CUDA(cudaGetLastError());
         if (by_index) {
             CV_CUDA(coverage_by_index(s, d_off, d_seeds, q0, qn, h_off[q0], h_off[q0 + qn] - h_off[q0], chunk_cnt,
                                       chunk_off, s->smask, s->qcov, st));
         } else {
-            k_coverage<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, s->qmask, s->qcov); note_launch();
+            k_coverage<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, s->qmask, s->qbits, s->qcov);
+            note_launch();
             CV_CUDA(cudaGetLastError());
         }
         k_estimate<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, g->w, g->f, g->W, s->T, s->qcov, d_cov, d_est,
                                        s->ris); note_launch();
         CV_CUDA(cudaGetLastError());
-        k_qmask_clear<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask); note_launch();
+        k_qmask_clear<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask, s->qbits); note_launch();
         CV_CUDA(cudaGetLastError());
     }
     dev_free(chunk_cnt, st);

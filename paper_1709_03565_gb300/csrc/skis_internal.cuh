@@ -286,6 +286,7 @@ struct skis_sketch {
     uint64_t* smask = nullptr;           // T per-sample query bits (inverted-index path)
     uint64_t smask_cap = 0;
     uint64_t* qmask = nullptr;           // n per-vertex query bits
+    uint32_t* qbits = nullptr;           // n bits: the vertex is a seed of the current batch
     unsigned long long* qcov = nullptr;  // 64 coverage counters
     skis::DevStatus* qstatus = nullptr;
     cudaStream_t stream = nullptr;
@@ -316,11 +317,13 @@ int set_last_error(int code, const std::string& msg);
 
 // Coverage kernels (defined in cover.cu).
 __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
-                            int32_t qn, int64_t n, uint64_t* __restrict__ qmask, DevStatus* st);
+                            int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits,
+                            DevStatus* st);
 __global__ void k_qmask_clear(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
-                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask);
+                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits);
 __global__ void __launch_bounds__(256) k_coverage(const uint64_t* __restrict__ h_off, const uint32_t* __restrict__ h_len, uint64_t T,
                            const int32_t* __restrict__ arena, const uint64_t* __restrict__ qmask,
+                                                 const uint32_t* __restrict__ qbits,
                            unsigned long long* __restrict__ cov);
 __global__ void k_estimate(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
                            int32_t qn, int64_t n, const uint64_t* __restrict__ w, int f, uint64_t W, uint64_t T,
