@@ -36,17 +36,25 @@ __device__ __forceinline__ void warp_members(uint64_t off, uint32_t len, const i
     }
     const uint64_t total = __shfl_sync(kFull, incl, 31);
     const uint64_t excl = incl - len;
-    for (uint64_t base = 0; base < total; base += 32) {
-        const uint64_t p = base + lane;
-        int owner = 0;
+    // two runs of 32 members per pass: both member loads are in flight
+    // before either member is handed to f
+    for (uint64_t base = 0; base < total; base += 64) {
+        const uint64_t p0 = base + lane, p1 = base + 32 + lane;
+        int own0 = 0, own1 = 0;
 #pragma unroll
         for (int step = 16; step >= 1; step >>= 1) {
-            const uint64_t v = __shfl_sync(kFull, incl, owner + step - 1);
-            if (v <= p) owner += step;
+            const uint64_t v0 = __shfl_sync(kFull, incl, own0 + step - 1);
+            const uint64_t v1 = __shfl_sync(kFull, incl, own1 + step - 1);
+            if (v0 <= p0) own0 += step;
+            if (v1 <= p1) own1 += step;
         }
-        const uint64_t o_off = __shfl_sync(kFull, off, owner);
-        const uint64_t o_excl = __shfl_sync(kFull, excl, owner);
-        if (p < total) f(owner, arena[o_off + (p - o_excl)]);
+        const uint64_t off0 = __shfl_sync(kFull, off, own0), ex0 = __shfl_sync(kFull, excl, own0);
+        const uint64_t off1 = __shfl_sync(kFull, off, own1), ex1 = __shfl_sync(kFull, excl, own1);
+        int32_t u0 = 0, u1 = 0;
+        if (p0 < total) u0 = arena[off0 + (p0 - ex0)];
+        if (p1 < total) u1 = arena[off1 + (p1 - ex1)];
+        if (p0 < total) f(own0, u0);
+        if (p1 < total) f(own1, u1);
     }
 }
 
