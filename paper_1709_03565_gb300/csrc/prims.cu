@@ -20,7 +20,7 @@ static std::once_flag g_pool_once;
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
     std::call_once(g_pool_once, [] {
         // Keep freed blocks in this process's default pool so that repeated
-        // graph/sketch builds do not return memory to the driver and map it
+        // graph/sketch builds do not return memory to the CUDA driver and map it
         // again. The attribute belongs to this process's pool only.
         int dev = 0;
         cudaMemPool_t pool;
