@@ -1,0 +1,42 @@
+"""Host-side logic of bench.py (no GPU): the algorithmic-bytes model and the
+rule that measured DRAM traffic is reported only for the kernel source and
+first-step form it was captured on."""
+import hashlib
+import json
+import os
+
+import bench
+
+
+def test_algorithmic_bytes_is_32T_68E_4C():
+    # per sample: alias sector + header (64 B); per member: row sector + write
+    # (36 B); per non-source member: source sector (32 B); per coin: threshold
+    for T, E, C in ((1, 1, 0), (10, 41, 664), (10_000_000, 41_685_976, 664_326_661)):
+        assert bench.algorithmic_bytes(T, E, C, True) == 32 * T + 68 * E + 4 * C
+        assert bench.algorithmic_bytes(T, E, C, False) == 32 * T + 68 * E
+
+
+def _fake_root(tmp_path, src: bytes, record: dict):
+    os.makedirs(tmp_path / "profiles")
+    os.makedirs(tmp_path / "paper_1709_03565_gb300" / "csrc")
+    (tmp_path / "paper_1709_03565_gb300" / "csrc" / "sample.cu").write_bytes(src)
+    (tmp_path / "profiles" / "iis_sampler_dram.json").write_text(json.dumps(record))
+
+
+def test_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
+    src = b"// sampler source\n"
+    record = {"sample_cu_sha256": hashlib.sha256(src).hexdigest(), "first_step": "bucket",
+              "dram_bytes_per_sample": 497.5}
+    _fake_root(tmp_path, src, record)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._traffic_per_sample("bucket") == 497.5
+    assert bench._traffic_per_sample("rejection") is None  # captured on the other form
+    (tmp_path / "paper_1709_03565_gb300" / "csrc" / "sample.cu").write_bytes(src + b"// changed\n")
+    assert bench._traffic_per_sample("bucket") is None  # the kernel changed since the capture
+
+
+def test_committed_record_names_its_capture():
+    d = json.load(open(os.path.join(bench.ROOT, "profiles", "iis_sampler_dram.json")))
+    assert d["first_step"] in ("bucket", "rejection")
+    assert d["dram_bytes_per_sample"] > 0 and len(d["sample_cu_sha256"]) == 64
+    assert d["command"].startswith("ncu ") and "--clock-control none" in d["command"]
