@@ -458,3 +458,30 @@ def test_bucket_first_step_full_er_workload(er_small):
     assert np.array_equal(cov, ocov)
     np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
     s.close()
+
+
+@pytest.mark.parametrize("bucket", [False, True])
+def test_hub_rows_on_every_tier_match_oracle(bucket):
+    # R-MAT with weighted cascade: in-rows of thousands of edges (the top one
+    # about 7K), so a sample that reaches a hub draws its whole row. Sent
+    # through each tier in turn the samples are the oracle's; on the CTA tier
+    # a window holding such a row deals its quads several to a lane.
+    n, m = 1 << 13, 32 << 13
+    src, dst = synth.rmat(13, m, 0.57, 0.19, 0.19, 17)
+    g, o = _pair(n, src, dst, "wc")
+    seed, T = 0x5EED0017, 600
+    ora = o.sample_ids(seed, np.arange(T, dtype=np.uint64), bucket=bucket)
+    assert np.bincount(dst, minlength=n).max() >= 4 * 64  # rows of 64+ quads exist
+    configs = ({}, {skis.SKIS_OPT_THREAD_MAX_DEG: 0},
+               {skis.SKIS_OPT_THREAD_MAX_DEG: 0, skis.SKIS_OPT_WARP_MAX_COINS: 1})
+    for opts in configs:
+        s = skis.skis_sketch_create(g, seed)
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, 1 if bucket else 0)
+        for k, v in opts.items():
+            skis.skis_sketch_set_option(s, k, v)
+        skis.skis_sample(s, T)
+        assert_samples_equal(skis.skis_sketch_export(s, 0, T), ora)
+        if skis.SKIS_OPT_WARP_MAX_COINS in opts:
+            assert skis.skis_sketch_stats(s)["deferred"] > T // 4  # most samples ran on the CTA tier
+        s.close()
+    g.close()
