@@ -40,3 +40,18 @@ def test_committed_record_names_its_capture():
     assert d["first_step"] in ("bucket", "rejection")
     assert d["dram_bytes_per_sample"] > 0 and len(d["sample_cu_sha256"]) == 64
     assert d["command"].startswith("ncu ") and "--clock-control none" in d["command"]
+
+
+def test_profile_summaries_name_commands_on_committed_files():
+    """Every ncu summary gives the command that made it; the command runs
+    ncu with --clock-control none on the committed bench, nothing else."""
+    pdir = os.path.join(bench.ROOT, "profiles")
+    mds = [f for f in os.listdir(pdir) if f.endswith(".md")]
+    assert mds
+    for f in mds:
+        blocks = open(os.path.join(pdir, f)).read().split("```")[1::2]  # fenced code blocks
+        cmds = [ln.strip() for b in blocks for ln in b.splitlines() if ln.strip().startswith("ncu ")]
+        assert cmds, f
+        for c in cmds:
+            assert "--clock-control none" in c, f
+            assert " python bench.py" in c and "_work" not in c, f
