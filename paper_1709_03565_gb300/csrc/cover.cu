@@ -25,8 +25,9 @@ constexpr int kCovThreads = 256;
 
 // Calls f(owner_lane, member) for every member of the samples held by the
 // lanes (lane i: arena offset off, length len), spread over the warp.
-template <class F>
+template <int kRuns = 2, class F>
 __device__ __forceinline__ void warp_members(uint64_t off, uint32_t len, const int32_t* __restrict__ arena, F&& f) {
+    static_assert(kRuns == 1 || kRuns == 2, "one or two runs of 32 members per pass");
     const int lane = threadIdx.x & 31;
     uint64_t incl = len;
 #pragma unroll
@@ -36,25 +37,40 @@ __device__ __forceinline__ void warp_members(uint64_t off, uint32_t len, const i
     }
     const uint64_t total = __shfl_sync(kFull, incl, 31);
     const uint64_t excl = incl - len;
-    // two runs of 32 members per pass: both member loads are in flight
-    // before either member is handed to f
-    for (uint64_t base = 0; base < total; base += 64) {
-        const uint64_t p0 = base + lane, p1 = base + 32 + lane;
-        int own0 = 0, own1 = 0;
+    if constexpr (kRuns == 1) {
+        for (uint64_t base = 0; base < total; base += 32) {
+            const uint64_t p = base + lane;
+            int owner = 0;
 #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            const uint64_t v0 = __shfl_sync(kFull, incl, own0 + step - 1);
-            const uint64_t v1 = __shfl_sync(kFull, incl, own1 + step - 1);
-            if (v0 <= p0) own0 += step;
-            if (v1 <= p1) own1 += step;
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint64_t v = __shfl_sync(kFull, incl, owner + step - 1);
+                if (v <= p) owner += step;
+            }
+            const uint64_t o_off = __shfl_sync(kFull, off, owner);
+            const uint64_t o_excl = __shfl_sync(kFull, excl, owner);
+            if (p < total) f(owner, arena[o_off + (p - o_excl)]);
         }
-        const uint64_t off0 = __shfl_sync(kFull, off, own0), ex0 = __shfl_sync(kFull, excl, own0);
-        const uint64_t off1 = __shfl_sync(kFull, off, own1), ex1 = __shfl_sync(kFull, excl, own1);
-        int32_t u0 = 0, u1 = 0;
-        if (p0 < total) u0 = arena[off0 + (p0 - ex0)];
-        if (p1 < total) u1 = arena[off1 + (p1 - ex1)];
-        if (p0 < total) f(own0, u0);
-        if (p1 < total) f(own1, u1);
+    } else {
+        // two runs of 32 members per pass: both member loads are in flight
+        // before either member is handed to f
+        for (uint64_t base = 0; base < total; base += 64) {
+            const uint64_t p0 = base + lane, p1 = base + 32 + lane;
+            int own0 = 0, own1 = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint64_t v0 = __shfl_sync(kFull, incl, own0 + step - 1);
+                const uint64_t v1 = __shfl_sync(kFull, incl, own1 + step - 1);
+                if (v0 <= p0) own0 += step;
+                if (v1 <= p1) own1 += step;
+            }
+            const uint64_t off0 = __shfl_sync(kFull, off, own0), ex0 = __shfl_sync(kFull, excl, own0);
+            const uint64_t off1 = __shfl_sync(kFull, off, own1), ex1 = __shfl_sync(kFull, excl, own1);
+            int32_t u0 = 0, u1 = 0;
+            if (p0 < total) u0 = arena[off0 + (p0 - ex0)];
+            if (p1 < total) u1 = arena[off1 + (p1 - ex1)];
+            if (p0 < total) f(own0, u0);
+            if (p1 < total) f(own1, u1);
+        }
     }
 }
 
@@ -410,7 +426,9 @@ __global__ void __launch_bounds__(kCovThreads) k_fill_inverted(const uint64_t* _
         const bool valid = j < T;
         // one slot reservation per entry: lanes rarely share a vertex, and
         // the atomics of those that do are served at L2 in turn
-        warp_members(valid ? h_off[j] : 0, valid ? h_len[j] : 0u, arena, [&](int owner, int32_t u) {
+        // one run per pass keeps this latency-bound kernel at 32 registers
+        // and every warp slot
+        warp_members<1>(valid ? h_off[j] : 0, valid ? h_len[j] : 0u, arena, [&](int owner, int32_t u) {
             const uint32_t pos = atomicAdd(&fill[u], 1u);
             inv[inv_off[u] + pos] = (uint32_t)(j0 + owner);
         });
