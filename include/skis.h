@@ -51,7 +51,7 @@ typedef enum skis_status {
     SKIS_ERR_CUDA = 3,         /* a CUDA call failed (message has the CUDA error) */
     SKIS_ERR_RETRY_LIMIT = 4,  /* a conditioned first step hit the retry cap */
     SKIS_ERR_ARENA_FULL = 5,   /* the sketch arena could not be grown */
-    SKIS_ERR_ABORTED = 6       /* device-side work stopped on a bounded wait */
+    SKIS_ERR_INTERNAL = 6      /* a library invariant failed on the device (a bug: the message says which) */
 } skis_status;
 
 /* Edge-probability models (Sec. II-A; Sec. VI "Weight Settings"). Every
@@ -85,7 +85,7 @@ typedef struct skis_graph_info {
 } skis_graph_info;
 
 typedef struct skis_stats {
-    uint64_t T;              /* samples in the sketch (ids 0 .. T-1) */
+    uint64_t T;              /* samples in the sketch (ids first_id .. first_id + T - 1) */
     uint64_t entries;        /* sum of |R_j| */
     uint64_t coins;          /* sum over samples of in-edges examined (see skis_sample) */
     uint64_t retries;        /* sum of rejected first-step rounds */
@@ -101,6 +101,8 @@ typedef struct skis_stats {
     uint64_t thread_max_deg;   /* the tier split in force (SKIS_OPT_THREAD_MAX_DEG, ...) */
     uint64_t thread_max_steps;
     uint64_t warp_max_coins;
+    uint64_t cta_hub_quads;
+    uint64_t first_id;       /* sample id of the sketch's first sample (SKIS_OPT_FIRST_ID) */
 } skis_stats;
 
 /* Sampling runs in three tiers chained by sample id: one lane per sample
@@ -137,9 +139,21 @@ typedef enum skis_option {
                                       live and the in-edges after it get their FIRST coins of round 0.
                                       IC graphs, IIS sampler; set before the first skis_sample; reads
                                       the per-edge chain IC graphs keep from loading. */,
-    SKIS_OPT_WARP_MAX_COINS = 10   /* in-edges a sample's BFS may draw in the warp tier before the CTA
+    SKIS_OPT_WARP_MAX_COINS = 10,  /* in-edges a sample's BFS may draw in the warp tier before the CTA
                                       tier (all warps of a block on one sample) takes it over
                                       (default 65536; samples that reach huge in-rows) */
+    SKIS_OPT_CTA_HUB_QUADS = 11,   /* CTA tier: in-rows of at least this many edge quads (default 256)
+                                      are drawn by the whole block in one strided loop instead of being
+                                      dealt with the level's other rows; 0 = never */
+    SKIS_OPT_FIRST_ID = 12,        /* sample id of the sketch's first sample (default 0): the sketch
+                                      holds ids [first, first + T), so that several sketches with one
+                                      seed hold disjoint id ranges of one sketch (Alg. 2's R, sharded
+                                      by id). Set before the first skis_sample; at most 2^62. */
+    SKIS_OPT_CTA_QUEUE_CAP = 13,   /* member queue entries of a CTA-tier slot (default 2^20, at most n;
+                                      in [32, 2^31]): a sample with more members moves to a second
+                                      pass over fewer slots with n-entry queues */
+    SKIS_OPT_CTA_THREADS = 14      /* threads of a CTA-tier block: 512 (default; two per SM) or 256
+                                      (four per SM) */
 } skis_option;
 
 /* Load G = (V, E, w) (Sec. II-A) and build the device structures every later
@@ -211,8 +225,8 @@ int skis_sketch_autotune(skis_sketch *s, uint64_t pilot_samples, uint32_t *chose
                          uint32_t *chosen_max_steps, double *candidate_ms, int32_t candidate_cap,
                          int32_t *candidates_out, void *cuda_stream);
 
-/* Append IIS samples (Alg. 1) with ids [T, T + count) to the sketch. For
- * sample j:
+/* Append IIS samples (Alg. 1) with ids [F + T, F + T + count) to the sketch
+ * (F = SKIS_OPT_FIRST_ID, 0 by default). For sample j:
  *   - source: Philox block (key seed, domain SRC, id j) gives col = floor(U1 n)
  *     and y = floor(U2 W); src = col if y < prob[col] else alias[col];
  *   - first step (Alg. 1 lines 2-6, Eq. probn) by rejection: round
@@ -225,7 +239,7 @@ int skis_sketch_autotune(skis_sketch *s, uint64_t pilot_samples, uint32_t *chose
  * over the other members. Returns SKIS_ERR_RETRY_LIMIT (the failing samples
  * are left empty) if a first step reaches the retry cap, SKIS_EINVAL if
  * W = 0 (no non-singular sample exists). Synchronises the stream.
- * next_sample_id_out (nullable) receives the new T. */
+ * next_sample_id_out (nullable) receives the next sample id, F + T. */
 int skis_sample(skis_sketch *s, uint64_t count, uint64_t *next_sample_id_out, void *cuda_stream);
 
 /* Stop-at-size sampling (the experiments' rule, Sec. VI "Algorithms
@@ -236,7 +250,7 @@ int skis_sample(skis_sketch *s, uint64_t count, uint64_t *next_sample_id_out, vo
  * after max_count samples. Samples are drawn in batches; those of the last
  * batch after the stopping one are dropped (the next call regenerates the
  * same ids). appended_out / next_sample_id_out (nullable) receive the number
- * appended and the new T. Errors as skis_sample; target_entries = 0 is
+ * appended and the next sample id. Errors as skis_sample; target_entries = 0 is
  * SKIS_EINVAL. Synchronises the stream. */
 int skis_sample_to_size(skis_sketch *s, uint64_t target_entries, uint64_t max_count, uint64_t *appended_out,
                         uint64_t *next_sample_id_out, void *cuda_stream);
@@ -264,8 +278,8 @@ int skis_greedy_maxcover(skis_sketch *s, int32_t k, int32_t *seeds_out, int64_t 
 
 int skis_sketch_stats(const skis_sketch *s, skis_stats *out);
 
-/* Copy samples [first_id, first_id + count) to host arrays (any may be
- * NULL): src int32[count], retries uint32[count], len uint32[count],
+/* Copy the samples with ids [first_id, first_id + count) (sample ids, as
+ * SKIS_OPT_FIRST_ID places them) to host arrays (any may be NULL): src int32[count], retries uint32[count], len uint32[count],
  * coins uint64[count], member_offsets int64[count+1] and members (the
  * members of each sample, in device order, which is unspecified) with
  * capacity members_cap. Returns SKIS_EINVAL if the range is outside the

@@ -14,13 +14,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libskis.so")
 
 SKIS_OK, SKIS_EINVAL, SKIS_ENOMEM, SKIS_ERR_CUDA = 0, 1, 2, 3
-SKIS_ERR_RETRY_LIMIT, SKIS_ERR_ARENA_FULL, SKIS_ERR_ABORTED = 4, 5, 6
+SKIS_ERR_RETRY_LIMIT, SKIS_ERR_ARENA_FULL, SKIS_ERR_INTERNAL = 4, 5, 6
 SKIS_W_EXPLICIT_P, SKIS_W_EXPLICIT_TAU, SKIS_W_WC, SKIS_W_TRI = 0, 1, 2, 3
 SKIS_MEM_HOST, SKIS_MEM_DEVICE = 0, 1
 SKIS_OPT_RETRY_CAP, SKIS_OPT_CTA_SLOTS, SKIS_OPT_WARP_BLOCKS = 0, 1, 2
 SKIS_OPT_THREAD_MAX_DEG, SKIS_OPT_THREAD_BLOCKS, SKIS_OPT_QUERY_INDEX, SKIS_OPT_THREAD_MAX_STEPS = 3, 4, 5, 6
 SKIS_OPT_SAMPLER, SKIS_OPT_THREAD_MAX_RETRIES, SKIS_OPT_FIRST_STEP = 7, 8, 9
-SKIS_OPT_WARP_MAX_COINS = 10
+SKIS_OPT_WARP_MAX_COINS, SKIS_OPT_CTA_HUB_QUADS, SKIS_OPT_FIRST_ID, SKIS_OPT_CTA_QUEUE_CAP = 10, 11, 12, 13
+SKIS_OPT_CTA_THREADS = 14
 SKIS_DIFF_IC, SKIS_DIFF_LT = 0, 1
 
 
@@ -44,7 +45,8 @@ class skis_stats(ctypes.Structure):
                 ("last_warp_ms", ctypes.c_double), ("last_cta_ms", ctypes.c_double),
                 ("last_sample_ms", ctypes.c_double), ("last_passes", ctypes.c_uint64),
                 ("thread_max_deg", ctypes.c_uint64), ("thread_max_steps", ctypes.c_uint64),
-                ("warp_max_coins", ctypes.c_uint64)]
+                ("warp_max_coins", ctypes.c_uint64), ("cta_hub_quads", ctypes.c_uint64),
+                ("first_id", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

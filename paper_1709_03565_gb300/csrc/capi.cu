@@ -224,6 +224,23 @@ extern "C" int skis_sketch_set_option(skis_sketch* s, int option, uint64_t value
             if (value < 1 || value > (1u << 31)) return fail(SKIS_EINVAL, "warp-tier coin budget must be in [1, 2^31]");
             s->warp_max_coins = (uint32_t)value;
             return SKIS_OK;
+        case SKIS_OPT_CTA_HUB_QUADS:
+            if (value > (1u << 30)) return fail(SKIS_EINVAL, "CTA-tier hub threshold must be at most 2^30 quads");
+            s->cta_hub_quads = (uint32_t)value;
+            return SKIS_OK;
+        case SKIS_OPT_CTA_QUEUE_CAP:
+            if (value < 32 || value > (1ull << 31)) return fail(SKIS_EINVAL, "CTA-tier queue capacity must be in [32, 2^31]");
+            s->cta_queue_cap = (uint32_t)value;
+            return SKIS_OK;
+        case SKIS_OPT_CTA_THREADS:
+            if (value != 256 && value != 512) return fail(SKIS_EINVAL, "CTA-tier block size must be 256 or 512");
+            s->cta_threads = (int)value;
+            return SKIS_OK;
+        case SKIS_OPT_FIRST_ID:
+            if (value > (1ull << 62)) return fail(SKIS_EINVAL, "first sample id must be at most 2^62");
+            if (s->T != 0) return fail(SKIS_EINVAL, "the first sample id is chosen before the first sample");
+            s->id_base = value;
+            return SKIS_OK;
         case SKIS_OPT_SAMPLER:
             if (value > 1) return fail(SKIS_EINVAL, "sampler must be 0 (IIS) or 1 (RIS)");
             if (s->T != 0) return fail(SKIS_EINVAL, "the sampler is chosen before the first sample");
@@ -250,7 +267,7 @@ extern "C" int skis_sample(skis_sketch* s, uint64_t count, uint64_t* next_sample
     s->stream = st;
     std::string err;
     const int rc = sketch_sample(s, count, st, &err);
-    if (next_sample_id_out) *next_sample_id_out = s->T;
+    if (next_sample_id_out) *next_sample_id_out = s->id_base + s->T;
     if (rc != SKIS_OK) return fail(rc, err);
     return SKIS_OK;
     API_CATCH
@@ -268,7 +285,7 @@ extern "C" int skis_sample_to_size(skis_sketch* s, uint64_t target_entries, uint
     uint64_t appended = 0;
     const int rc = sketch_sample_to_size(s, target_entries, max_count, st, &appended, &err);
     if (appended_out) *appended_out = appended;
-    if (next_sample_id_out) *next_sample_id_out = s->T;
+    if (next_sample_id_out) *next_sample_id_out = s->id_base + s->T;
     if (rc != SKIS_OK) return fail(rc, err);
     return SKIS_OK;
     API_CATCH
@@ -403,6 +420,8 @@ extern "C" int skis_sketch_stats(const skis_sketch* s, skis_stats* out) {
     out->thread_max_deg = s->thread_max_deg;
     out->thread_max_steps = s->thread_max_steps;
     out->warp_max_coins = s->warp_max_coins;
+    out->cta_hub_quads = s->cta_hub_quads;
+    out->first_id = s->id_base;
     if (s->T == 0) return SKIS_OK;
     cudaStream_t st = s->stream;
     unsigned long long* d = nullptr;
@@ -444,7 +463,9 @@ extern "C" int skis_sketch_export(const skis_sketch* s, uint64_t first_id, uint6
                                   int32_t* members, uint64_t members_cap, void* cuda_stream) {
     API_TRY
     if (!s) return fail(SKIS_EINVAL, "skis_sketch_export: NULL sketch");
-    if (first_id > s->T || count > s->T - first_id) return fail(SKIS_EINVAL, "skis_sketch_export: range outside the sketch");
+    if (first_id < s->id_base || first_id - s->id_base > s->T || count > s->T - (first_id - s->id_base))
+        return fail(SKIS_EINVAL, "skis_sketch_export: range outside the sketch");
+    first_id -= s->id_base;  // header position
     if (count == 0) {
         if (member_offsets) member_offsets[0] = 0;
         return SKIS_OK;
@@ -502,6 +523,8 @@ void skis::sketch_release(skis_sketch* s) {
     dev_free(s->ovf_ids[1], st);
     dev_free(s->bitmaps, st);
     dev_free(s->queues, st);
+    dev_free(s->big_queues, st);
+    dev_free(s->big_ids, st);
     dev_free(s->lt_hash, st);
     dev_free(s->lt_list, st);
     dev_free(s->lt_slot, st);

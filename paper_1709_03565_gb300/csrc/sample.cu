@@ -36,8 +36,6 @@ constexpr int kHashBits = 9;
 constexpr int kIdBatch = 16;       // sample ids taken per work-cursor atomic
 constexpr uint32_t kArenaChunk = 2048;        // entries reserved per arena atomic (warp tier)
 constexpr uint32_t kLaneArenaChunk = 512;     // entries reserved per arena atomic (lane tiers)
-constexpr int kCtaThreads = 512;
-constexpr int kCtaWin = 2 * kCtaThreads;  // queued vertices per load-balanced CTA-tier window
 constexpr int kCtaGroupLog2 = 2;
 constexpr int kCtaGroup = 1 << kCtaGroupLog2;  // edge quads of a long row a CTA-tier lane draws per step
 constexpr int kCtaLongRow = 64;            // quads that make a row long
@@ -55,12 +53,14 @@ struct SampleArgs {
     uint32_t max_steps;                // thread tier: edge quads per sample before handing it on
     uint32_t max_retries;              // thread tier: rejected rounds before handing it on
     uint32_t warp_max_coins;           // warp tier: in-edges a BFS may draw before handing it on
+    uint32_t cta_hub_quads;            // CTA tier: edge quads that make a row a hub (0 = no hub loop)
     int ris;                           // plain RIS: uniform source, one unconditioned round
     // input ids: first_id + t (ids == nullptr) or ids[t], t < count (or
     // t < *count_dev when the list was filled by the previous tier)
     const uint64_t* ids;
     uint64_t first_id, count;
     const unsigned long long* count_dev;
+    uint64_t id_base;                  // sample id of the sketch's first header (headers are indexed j - id_base)
     unsigned long long* work;          // id cursor of this launch
     uint64_t* out_ids;                 // samples handed to the next tier
     unsigned long long* out_count;
@@ -78,6 +78,8 @@ struct SampleArgs {
     uint32_t* bitmaps;
     int32_t* queues;
     uint64_t bitmap_words;
+    uint32_t queue_cap;      // CTA tier: entries of a slot's queue (also the slots' stride); a sample
+                             // with more members is handed to a pass with n-entry queues
     const uint4* srcrec;  // lane tier: source record per input t (k_sources)
     const uint2* srcpick; // lane tier, bucket form: (picked in-edge, its source) per input t
     const uint64_t* lt_cum;  // LT graphs with per-edge thresholds: running weight sums, else nullptr
@@ -208,12 +210,28 @@ struct WarpInserter {
     }
 };
 
+// CTA tier, one lane alone (divergent code): test-and-set in the global
+// bitmap, append to the global queue through the shared counter. A vertex
+// past the queue's capacity gets its bit back, so that the bitmap always
+// holds exactly the queued vertices (the counter still counts it: the sample
+// is then known to have outgrown the slot).
+__device__ __forceinline__ void cta_insert_one(uint32_t* bitmap, int32_t* queue, uint32_t* qlen, uint32_t cap,
+                                               int32_t u) {
+    const uint32_t bit = 1u << (u & 31);
+    if ((atomicOr(&bitmap[u >> 5], bit) & bit) == 0) {
+        const uint32_t pos = atomicAdd(qlen, 1u);
+        if (pos < cap) queue[pos] = u;
+        else atomicAnd(&bitmap[u >> 5], ~bit);
+    }
+}
+
 // CTA tier: global bitmap (test-and-set) + global queue with a shared counter.
 struct CtaInserter {
     uint32_t* bitmap;
     int32_t* queue;
     uint32_t* qlen;  // shared
-    bool overflow;   // never set
+    uint32_t cap;    // queue capacity (see cta_insert_one)
+    bool overflow;   // never set: the CTA tier checks the count between levels
 
     __device__ __forceinline__ void insert(int32_t u) {
         bool fresh = false;
@@ -226,7 +244,11 @@ struct CtaInserter {
             uint32_t base = 0;
             if ((threadIdx.x & 31) == 0) base = atomicAdd(qlen, (uint32_t)__popc(m));
             base = __shfl_sync(kFull, base, 0);
-            if (fresh) queue[base + __popc(m & lanemask_lt())] = u;
+            if (fresh) {
+                const uint32_t pos = base + __popc(m & lanemask_lt());
+                if (pos < cap) queue[pos] = u;
+                else atomicAnd(&bitmap[u >> 5], ~(1u << (u & 31)));
+            }
         }
     }
 };
@@ -382,11 +404,11 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 
 __device__ __forceinline__ void record_retry_failure(const SampleArgs& a, uint64_t j, uint32_t v, uint32_t r,
                                                      uint32_t deg) {
-    a.h_off[j] = 0;
-    a.h_len[j] = 0;
-    a.h_src[j] = v;
-    a.h_retries[j] = r;
-    a.h_coins[j] = (uint64_t)deg * r;
+    a.h_off[j - a.id_base] = 0;
+    a.h_len[j - a.id_base] = 0;
+    a.h_src[j - a.id_base] = v;
+    a.h_retries[j - a.id_base] = r;
+    a.h_coins[j - a.id_base] = (uint64_t)deg * r;
     atomicOr(&a.status->flags, kStRetry);
     atomicMin(&a.status->first_bad, (unsigned long long)j);
 }
@@ -484,11 +506,11 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                 const uint64_t at = chunk_pos + (incl - mylen);
                 if (done) {
                     if (fits) {
-                        a.h_off[j] = at;
-                        a.h_len[j] = len;
-                        a.h_src[j] = v;
-                        a.h_retries[j] = r;
-                        a.h_coins[j] = coins;
+                        a.h_off[j - a.id_base] = at;
+                        a.h_len[j - a.id_base] = len;
+                        a.h_src[j - a.id_base] = v;
+                        a.h_retries[j - a.id_base] = r;
+                        a.h_coins[j - a.id_base] = coins;
                     } else {
                         arena_overflow(a, j);
                     }
@@ -779,11 +801,11 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
                 count_member(a, queue[i]);
             }
             if (lane == 0) {
-                a.h_off[j] = chunk_pos;
-                a.h_len[j] = len;
-                a.h_src[j] = v;
-                a.h_retries[j] = r;
-                a.h_coins[j] = coins;
+                a.h_off[j - a.id_base] = chunk_pos;
+                a.h_len[j - a.id_base] = len;
+                a.h_src[j - a.id_base] = v;
+                a.h_retries[j - a.id_base] = r;
+                a.h_coins[j - a.id_base] = coins;
             }
             chunk_pos += len;
             __syncwarp();
@@ -792,20 +814,27 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
 }
 
 // -------------------------------------------------------------- CTA tier
-__global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
+// One block of kCtaThreads threads per sample, 1024 threads of such blocks per
+// SM (two of 512 or four of 256: the option SKIS_OPT_CTA_THREADS).
+template <int kCtaThreads>
+__global__ void __launch_bounds__(kCtaThreads, 1024 / kCtaThreads) k_iis_cta(SampleArgs a) {
+    constexpr int kCtaWin = 2 * kCtaThreads;  // queued vertices per load-balanced window
     __shared__ unsigned long long s_j;
     __shared__ uint32_t s_qlen;
     __shared__ unsigned long long s_coins;
     __shared__ unsigned long long s_base;
     __shared__ uint32_t s_r, s_failed;
     __shared__ uint32_t s_pre[kCtaWin], s_lo[kCtaWin], s_hi[kCtaWin], s_tau[kCtaWin];
+    __shared__ uint32_t s_hub[kCtaWin];  // window rows taken by the hub loop
+    __shared__ uint32_t s_nhub;
     __shared__ uint32_t s_wsum[kCtaThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int kWarps = kCtaThreads / 32;
     static_assert(kCtaWin == 2 * kCtaThreads, "two window rows per thread");
     uint32_t* bitmap = a.bitmaps + (uint64_t)blockIdx.x * a.bitmap_words;
-    int32_t* queue = a.queues + (uint64_t)blockIdx.x * a.n;
+    int32_t* queue = a.queues + (uint64_t)blockIdx.x * a.queue_cap;
     const uint64_t count = input_count(a);
+    if (threadIdx.x == 0) s_nhub = 0;
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -827,7 +856,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
             s_coins = 0;
         }
         __syncthreads();
-        CtaInserter ins{bitmap, queue, &s_qlen, false};
+        CtaInserter ins{bitmap, queue, &s_qlen, a.queue_cap, false};
 
         // first step: a short source row is searched by warp 0, several
         // rounds per pass; a long one is split over the warps in whole quads
@@ -879,7 +908,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
             __syncthreads();
             const uint32_t tail = s_qlen;
             __syncthreads();
-            if (head >= tail) break;
+            if (head >= tail || tail > a.queue_cap) break;  // done, or the sample outgrew the slot
             for (uint32_t w0 = head; w0 < tail; w0 += kCtaWin) {
                 const uint32_t nw = min((uint32_t)kCtaWin, tail - w0);
                 uint32_t nq2[2];
@@ -895,6 +924,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                         s_hi[i] = hi;
                         s_tau[i] = rw.tau;
                         nq2[h] = rw.deg ? ((hi - 1) >> 2) - (lo >> 2) + 1 : 0u;  // edge quads
+                        if (a.cta_hub_quads && nq2[h] >= a.cta_hub_quads) {  // the hub loop takes it
+                            s_hub[atomicAdd(&s_nhub, 1u)] = i;
+                            nq2[h] = 0;
+                        }
                     }
                 }
                 // a window with a long row (a hub) deals its quads kCtaGroup at
@@ -916,6 +949,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                 }
                 if (lane == 31) s_wsum[wid] = x;
                 __syncthreads();
+                // every thread reads the hub count between these two barriers,
+                // and it is cleared after the second, before any thread can
+                // classify the next window's rows
+                const uint32_t nhub = s_nhub;
                 if (wid == 0) {
                     uint32_t w = lane < kWarps ? s_wsum[lane] : 0u;
 #pragma unroll
@@ -926,6 +963,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                     if (lane < kWarps) s_wsum[lane] = w;
                 }
                 __syncthreads();
+                if (threadIdx.x == 0) s_nhub = 0;
                 const uint32_t before = (wid ? s_wsum[wid - 1] : 0u) + x - pair;
                 if (2u * threadIdx.x < nw) s_pre[2u * threadIdx.x] = before + nq2[0];
                 if (2u * threadIdx.x + 1 < nw) s_pre[2u * threadIdx.x + 1] = before + pair;
@@ -991,6 +1029,44 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
                         }
                     }
                 }
+                // hub rows: their quads laid end to end and strided over the
+                // block, so a thread runs straight down a row with no search
+                // and no per-edge bounds; a live coin is rare there (WC: one
+                // expected per row) and is inserted by its lane alone
+                if (nhub) {
+                    const SampleBlock blk(a.rk, j, kDomBfs);
+                    const uint4* __restrict__ tau4 = reinterpret_cast<const uint4*>(a.tau);
+                    uint32_t g = threadIdx.x;
+                    for (uint32_t h = 0; h < nhub; ++h) {
+                        const uint32_t i = s_hub[h];
+                        const uint32_t lo = s_lo[i], hi = s_hi[i], tr = s_tau[i];
+                        const uint32_t qf = lo >> 2, nq = ((hi - 1) >> 2) - qf + 1;
+                        for (; g < nq; g += kCtaThreads) {
+                            const uint32_t q = qf + g;
+                            const uint4 x = blk(q, a.rk);
+                            const uint4 t4 = tau4 ? __ldg(tau4 + q) : make_uint4(tr, tr, tr, tr);
+                            const bool maybe = tau4 ? coin_live(x.x, t4.x) | coin_live(x.y, t4.y) |
+                                                          coin_live(x.z, t4.z) | coin_live(x.w, t4.w)
+                                                    : (min(min(x.x, x.y), min(x.z, x.w)) < tr) | (tr == kSentinel);
+                            if (maybe) {
+                                const uint32_t e0 = q << 2;
+                                unsigned l4 = 0;
+                                l4 |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
+                                l4 |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
+                                l4 |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
+                                l4 |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
+                                if (l4) {
+                                    const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
+                                    if (l4 & 1u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.x);
+                                    if (l4 & 2u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.y);
+                                    if (l4 & 4u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.z);
+                                    if (l4 & 8u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.w);
+                                }
+                            }
+                        }
+                        g -= nq;
+                    }
+                }
                 __syncthreads();  // the window's shared arrays are reused
             }
             head = tail;
@@ -999,23 +1075,28 @@ __global__ void __launch_bounds__(kCtaThreads) k_iis_cta(SampleArgs a) {
         if (lane == 0 && coins) atomicAdd(&s_coins, (unsigned long long)coins);
         __syncthreads();
         const uint32_t len = s_qlen;
+        const bool outgrown = len > a.queue_cap;  // the queue kept its first queue_cap members only
         if (threadIdx.x == 0) {
-            const unsigned long long base = atomicAdd(a.arena_cursor, (unsigned long long)len);
-            if (base + len > a.arena_cap) {
+            const unsigned long long base = outgrown ? 0ull : atomicAdd(a.arena_cursor, (unsigned long long)len);
+            if (outgrown) {  // to the pass whose slots hold n-entry queues
+                if (a.out_ids) hand_on(a, j);
+                else atomicOr(&a.status->flags, kStListFull);
+                s_base = ~0ull;
+            } else if (base + len > a.arena_cap) {
                 arena_overflow(a, j);
                 s_base = ~0ull;
             } else {
                 s_base = base;
-                a.h_off[j] = base;
-                a.h_len[j] = len;
-                a.h_src[j] = v;
-                a.h_retries[j] = r;
-                a.h_coins[j] = (uint64_t)rv.deg * (r + 1) + s_coins;
+                a.h_off[j - a.id_base] = base;
+                a.h_len[j - a.id_base] = len;
+                a.h_src[j - a.id_base] = v;
+                a.h_retries[j - a.id_base] = r;
+                a.h_coins[j - a.id_base] = (uint64_t)rv.deg * (r + 1) + s_coins;
             }
         }
         __syncthreads();
         const unsigned long long base = s_base;
-        for (uint32_t i = threadIdx.x; i < len; i += kCtaThreads) {
+        for (uint32_t i = threadIdx.x; i < min(len, a.queue_cap); i += kCtaThreads) {
             const int32_t u = queue[i];
             if (base != ~0ull) {
                 a.arena[base + i] = u;
@@ -1164,11 +1245,11 @@ __global__ void __launch_bounds__(kLtBlock) k_lt_walk(SampleArgs a) {
                         a.arena[at + i] = mq[i][lane];
                         count_member(a, mq[i][lane]);
                     }
-                    a.h_off[j] = at;
-                    a.h_len[j] = len;
-                    a.h_src[j] = v;
-                    a.h_retries[j] = 0;
-                    a.h_coins[j] = coins;
+                    a.h_off[j - a.id_base] = at;
+                    a.h_len[j - a.id_base] = len;
+                    a.h_src[j - a.id_base] = v;
+                    a.h_retries[j - a.id_base] = 0;
+                    a.h_coins[j - a.id_base] = coins;
                 } else {
                     arena_overflow(a, j);
                 }
@@ -1239,11 +1320,11 @@ __global__ void __launch_bounds__(kLtMidBlock) k_lt_mid(SampleArgs a, uint32_t* 
                     a.arena[base + i] = list[i];
                     count_member(a, list[i]);
                 }
-                a.h_off[j] = base;
-                a.h_len[j] = len;
-                a.h_src[j] = v;
-                a.h_retries[j] = 0;
-                a.h_coins[j] = coins;
+                a.h_off[j - a.id_base] = base;
+                a.h_len[j - a.id_base] = len;
+                a.h_src[j - a.id_base] = v;
+                a.h_retries[j - a.id_base] = 0;
+                a.h_coins[j - a.id_base] = coins;
             } else {
                 arena_overflow(a, j);
             }
@@ -1258,7 +1339,7 @@ __global__ void __launch_bounds__(kLtMidBlock) k_lt_mid(SampleArgs a, uint32_t* 
 __global__ void __launch_bounds__(32) k_lt_long(SampleArgs a) {
     const int lane = threadIdx.x & 31;
     uint32_t* bitmap = a.bitmaps + (uint64_t)blockIdx.x * a.bitmap_words;
-    int32_t* queue = a.queues + (uint64_t)blockIdx.x * a.n;
+    int32_t* queue = a.queues + (uint64_t)blockIdx.x * a.queue_cap;
     const uint64_t count = input_count(a);
     for (;;) {
         unsigned long long ti = 0;
@@ -1266,7 +1347,7 @@ __global__ void __launch_bounds__(32) k_lt_long(SampleArgs a) {
         ti = __shfl_sync(kFull, ti, 0);
         if (ti >= count) break;
         const uint64_t j = input_id(a, ti);
-        uint32_t len = 0, v = 0;
+        uint32_t len = 0, v = 0, outgrown = 0;
         uint64_t coins = 0;
         if (lane == 0) {
             v = draw_source(a, j);
@@ -1281,6 +1362,10 @@ __global__ void __launch_bounds__(32) k_lt_long(SampleArgs a) {
                 if (u < 0) break;
                 const uint32_t bit = 1u << (u & 31);
                 if (bitmap[(uint32_t)u >> 5] & bit) break;
+                if (len == a.queue_cap) {  // the walk outgrew the slot's queue
+                    outgrown = 1;
+                    break;
+                }
                 bitmap[(uint32_t)u >> 5] |= bit;
                 queue[len++] = u;
                 x = u;
@@ -1290,10 +1375,11 @@ __global__ void __launch_bounds__(32) k_lt_long(SampleArgs a) {
         len = __shfl_sync(kFull, len, 0);
         v = __shfl_sync(kFull, v, 0);
         coins = __shfl_sync(kFull, coins, 0);
+        outgrown = __shfl_sync(kFull, outgrown, 0);
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(a.arena_cursor, (unsigned long long)len);
+        if (lane == 0 && !outgrown) base = atomicAdd(a.arena_cursor, (unsigned long long)len);
         base = __shfl_sync(kFull, base, 0);
-        const bool fits = base + len <= a.arena_cap;
+        const bool fits = !outgrown && base + len <= a.arena_cap;
         for (uint32_t i = lane; i < len; i += 32) {
             const int32_t u = queue[i];
             if (fits) {
@@ -1304,11 +1390,14 @@ __global__ void __launch_bounds__(32) k_lt_long(SampleArgs a) {
         }
         if (lane == 0) {
             if (fits) {
-                a.h_off[j] = base;
-                a.h_len[j] = len;
-                a.h_src[j] = v;
-                a.h_retries[j] = 0;
-                a.h_coins[j] = coins;
+                a.h_off[j - a.id_base] = base;
+                a.h_len[j - a.id_base] = len;
+                a.h_src[j - a.id_base] = v;
+                a.h_retries[j - a.id_base] = 0;
+                a.h_coins[j - a.id_base] = coins;
+            } else if (outgrown) {  // to the pass whose slots hold n-entry queues
+                if (a.out_ids) hand_on(a, j);
+                else atomicOr(&a.status->flags, kStListFull);
             } else {
                 arena_overflow(a, j);
             }
@@ -1362,11 +1451,13 @@ static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st
     if (count > s->list_cap) {
         dev_free(s->to_warp_ids, st);
         dev_free(s->to_cta_ids, st);
+        dev_free(s->big_ids, st);
         dev_free(s->ovf_ids[0], st);
         dev_free(s->ovf_ids[1], st);
-        s->to_warp_ids = s->to_cta_ids = s->ovf_ids[0] = s->ovf_ids[1] = nullptr;
+        s->to_warp_ids = s->to_cta_ids = s->big_ids = s->ovf_ids[0] = s->ovf_ids[1] = nullptr;
         SK_CUDA(dev_alloc_t(&s->to_warp_ids, (size_t)count, st));
         SK_CUDA(dev_alloc_t(&s->to_cta_ids, (size_t)count, st));
+        SK_CUDA(dev_alloc_t(&s->big_ids, (size_t)count, st));
         SK_CUDA(dev_alloc_t(&s->ovf_ids[0], (size_t)count, st));
         SK_CUDA(dev_alloc_t(&s->ovf_ids[1], (size_t)count, st));
         dev_free(s->srcrec, st);
@@ -1389,14 +1480,18 @@ static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st
         SK_CUDA(dev_alloc_t(&s->lt_list, (size_t)(s->lt_mid_lanes * kLtMidCap), st));
         SK_CUDA(dev_alloc_t(&s->lt_slot, (size_t)(s->lt_mid_lanes * kLtMidCap), st));
     }
+    // CTA-tier slots: an n-bit visited bitmap and a queue of min(n, cta_queue_cap)
+    // entries each (a sample with more members moves to a pass over slots with
+    // n-entry queues), 1024 threads of blocks per SM within ~8 GB
+    const uint32_t qcap = (uint32_t)std::min<uint64_t>((uint64_t)g->n, s->cta_queue_cap);
     int slots = s->cta_slots;
     if (slots <= 0) {
-        // two blocks per SM, within ~8 GB of per-slot bitmaps and queues
-        const uint64_t per_slot = (uint64_t)g->n * 4 + ((uint64_t)g->n + 31) / 32 * 4;
+        const uint64_t per_slot = (uint64_t)qcap * 4 + ((uint64_t)g->n + 31) / 32 * 4;
         const uint64_t budget = 8ull << 30;
-        slots = (int)std::min<uint64_t>((uint64_t)sm_count() * 2, std::max<uint64_t>(1, budget / per_slot));
+        const uint64_t per_sm = g->lt ? 2 : 1024 / s->cta_threads;
+        slots = (int)std::min<uint64_t>((uint64_t)sm_count() * per_sm, std::max<uint64_t>(1, budget / per_slot));
     }
-    if (slots != s->cta_slots_alloc) {
+    if (slots != s->cta_slots_alloc || qcap != s->queue_cap) {
         dev_free(s->bitmaps, st);
         dev_free(s->queues, st);
         s->bitmaps = nullptr;
@@ -1404,9 +1499,23 @@ static int ensure_sample_buffers(skis_sketch* s, uint64_t count, cudaStream_t st
         s->bitmap_words = ((uint64_t)g->n + 31) / 32;
         SK_CUDA(dev_alloc_t(&s->bitmaps, (size_t)(s->bitmap_words * slots), st));
         SK_CUDA(cudaMemsetAsync(s->bitmaps, 0, s->bitmap_words * slots * sizeof(uint32_t), st));
-        SK_CUDA(dev_alloc_t(&s->queues, (size_t)((uint64_t)g->n * slots), st));
+        SK_CUDA(dev_alloc_t(&s->queues, (size_t)((uint64_t)qcap * slots), st));
         s->cta_slots_alloc = slots;
+        s->queue_cap = qcap;
     }
+    return SKIS_OK;
+}
+
+// The pass over samples that outgrew a CTA-tier slot's queue: slots with
+// n-entry queues (their bitmaps are the first slots' of the CTA tier, all
+// zero between launches), allocated on first use within ~8 GB.
+static int ensure_big_slots(skis_sketch* s, cudaStream_t st, std::string* err) {
+    if (s->big_queues) return SKIS_OK;
+    const uint64_t n = (uint64_t)s->g->n;
+    const uint64_t budget = 8ull << 30;
+    const int slots = (int)std::min<uint64_t>((uint64_t)s->cta_slots_alloc, std::max<uint64_t>(1, budget / (n * 4)));
+    SK_CUDA(dev_alloc_t(&s->big_queues, (size_t)(n * slots), st));
+    s->big_slots = slots;
     return SKIS_OK;
 }
 
@@ -1454,9 +1563,11 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.max_steps = s->thread_max_steps;
     base.max_retries = s->thread_max_retries;
     base.warp_max_coins = s->warp_max_coins;
+    base.cta_hub_quads = s->cta_hub_quads;
     base.ris = s->ris;
     base.ids = nullptr;
-    base.first_id = s->T;
+    base.first_id = s->id_base + s->T;
+    base.id_base = s->id_base;
     base.count = count;
     base.count_dev = nullptr;
     base.arena_cursor = &s->ctr->arena;
@@ -1472,6 +1583,7 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     base.bitmaps = s->bitmaps;
     base.queues = s->queues;
     base.bitmap_words = s->bitmap_words;
+    base.queue_cap = s->queue_cap;
     base.srcrec = nullptr;
     base.srcpick = nullptr;
     base.up_rec = nullptr;
@@ -1533,8 +1645,8 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
         ac.ids = s->to_cta_ids;
         ac.count_dev = &s->ctr->n_to_cta;
         ac.work = &s->ctr->work_cta;
-        ac.out_ids = nullptr;
-        ac.out_count = nullptr;
+        ac.out_ids = s->big_ids;  // samples that outgrow a slot's queue
+        ac.out_count = &s->ctr->n_big;
 
         SK_CUDA(cudaEventRecord(s->ev[0], st));
         if (g->lt) {  // LT: lane-per-sample walks, lane-per-walk medium walks, long walks on the slots
@@ -1570,17 +1682,46 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
             k_iis_warp<<<warp_blocks, kWarpThreads, 0, st>>>(aw); note_launch();
             SK_CUDA(cudaGetLastError());
             SK_CUDA(cudaEventRecord(s->ev[2], st));
-            k_iis_cta<<<s->cta_slots_alloc, kCtaThreads, 0, st>>>(ac); note_launch();
+            if (s->cta_threads == 256) k_iis_cta<256><<<s->cta_slots_alloc, 256, 0, st>>>(ac);
+            else k_iis_cta<512><<<s->cta_slots_alloc, 512, 0, st>>>(ac);
+            note_launch();
             SK_CUDA(cudaGetLastError());
             SK_CUDA(cudaEventRecord(s->ev[3], st));
         }
         SK_CUDA(cudaMemcpyAsync(&hc, s->ctr, sizeof(SampleCounters), cudaMemcpyDeviceToHost, st));
         SK_CUDA(cudaMemcpyAsync(&hst, s->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
         SK_CUDA(cudaStreamSynchronize(st));
-        float ms_t = 0, ms_w = 0, ms_c = 0;
+        float ms_t = 0, ms_w = 0, ms_c = 0, ms_b = 0;
         cudaEventElapsedTime(&ms_t, s->ev[0], s->ev[1]);
         cudaEventElapsedTime(&ms_w, s->ev[1], s->ev[2]);
         cudaEventElapsedTime(&ms_c, s->ev[2], s->ev[3]);
+        if (hc.n_big > 0) {  // samples that outgrew a slot's queue, on slots with n-entry queues
+            rc = ensure_big_slots(s, st, err);
+            if (rc != SKIS_OK) return rc;
+            SampleArgs ab = ac;
+            ab.ids = s->big_ids;
+            ab.count_dev = &s->ctr->n_big;
+            ab.work = &s->ctr->work_big;
+            ab.queues = s->big_queues;
+            ab.queue_cap = (uint32_t)g->n;
+            ab.out_ids = nullptr;
+            ab.out_count = nullptr;
+            SK_CUDA(cudaEventRecord(s->ev[2], st));
+            if (g->lt) {
+                k_lt_long<<<s->big_slots, 32, 0, st>>>(ab); note_launch();
+            } else {
+                if (s->cta_threads == 256) k_iis_cta<256><<<s->big_slots, 256, 0, st>>>(ab);
+                else k_iis_cta<512><<<s->big_slots, 512, 0, st>>>(ab);
+                note_launch();
+            }
+            SK_CUDA(cudaGetLastError());
+            SK_CUDA(cudaEventRecord(s->ev[3], st));
+            SK_CUDA(cudaMemcpyAsync(&hc, s->ctr, sizeof(SampleCounters), cudaMemcpyDeviceToHost, st));
+            SK_CUDA(cudaMemcpyAsync(&hst, s->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+            SK_CUDA(cudaStreamSynchronize(st));
+            cudaEventElapsedTime(&ms_b, s->ev[2], s->ev[3]);
+            ms_c += ms_b;
+        }
         s->last_thread_ms += ms_t;
         s->last_warp_ms += ms_w;
         s->last_cta_ms += ms_c;
@@ -1618,6 +1759,10 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
     if (counting) {
         s->vcount_ok = true;
         s->vcount_T = s->T;
+    }
+    if (hst.flags & kStListFull) {
+        *err = "skis_sample: internal error: a sample outgrew a queue of n entries";
+        return SKIS_ERR_INTERNAL;
     }
     if (hst.flags & kStRetry) {
         *err = "skis_sample: a conditioned first step reached the retry cap (" + std::to_string(s->retry_cap) +
@@ -1711,6 +1856,9 @@ int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* can
     tmp.bucket = s->bucket;
     tmp.thread_max_retries = s->thread_max_retries;
     tmp.warp_max_coins = s->warp_max_coins;
+    tmp.cta_hub_quads = s->cta_hub_quads;
+    tmp.cta_queue_cap = s->cta_queue_cap;
+    tmp.cta_threads = s->cta_threads;
     tmp.cta_slots = s->cta_slots;
     tmp.warp_blocks = s->warp_blocks;
     tmp.thread_blocks = s->thread_blocks;

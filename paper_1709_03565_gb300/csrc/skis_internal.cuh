@@ -119,6 +119,50 @@ __device__ __forceinline__ uint4 coin_block(const PhiloxKeys& rk, uint64_t q, ui
     return philox10(c, rk);
 }
 
+// coin_block(rk, q, 0, dom, j) for one sample j and many edge quads q < 2^32
+// (every CSR position is below 2^32, so the counter's second word is dom << 28
+// alone). Of the first two rounds' four products, two depend only on (j, dom):
+// round 0 multiplies word 2 (the low id word) and round 1 multiplies word 0,
+// which round 0 made from the id alone. Those two and the key terms that meet
+// them are formed once per sample, leaving 18 products per block instead of
+// 20; the block is bit-identical to philox10's.
+struct SampleBlock {
+    uint32_t a0;   // word 0 after round 0
+    uint32_t c1;   // word 1 after round 0, xor round 1's key 0
+    uint32_t c2;   // high half of round 1's word-0 product, xor round 1's key 1
+    uint32_t c3;   // low half of that product (word 3 after round 1), xor round 2's key 1
+    uint32_t k1j;  // round 0's key 1 xor the high id word
+
+    __device__ __forceinline__ SampleBlock(const PhiloxKeys& rk, uint64_t j, uint32_t dom) {
+        const uint64_t pb = (uint64_t)0xCD9E8D57u * (uint32_t)j;
+        a0 = (uint32_t)(pb >> 32) ^ (dom << 28) ^ rk.k[0];
+        c1 = (uint32_t)pb ^ rk.k[2];
+        const uint64_t pa = (uint64_t)0xD2511F53u * a0;
+        c2 = (uint32_t)(pa >> 32) ^ rk.k[3];
+        c3 = (uint32_t)pa ^ rk.k[5];
+        k1j = (uint32_t)(j >> 32) ^ rk.k[1];
+    }
+
+    __device__ __forceinline__ uint4 operator()(uint32_t q, const PhiloxKeys& rk) const {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * q;             // round 0, word 0
+        const uint32_t x2 = (uint32_t)(p0 >> 32) ^ k1j, x3 = (uint32_t)p0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;            // round 1, word 2
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ c1, y1 = (uint32_t)p1, y2 = x3 ^ c2;
+        const uint64_t p2a = (uint64_t)0xD2511F53u * y0;           // round 2
+        const uint64_t p2b = (uint64_t)0xCD9E8D57u * y2;
+        uint4 c = make_uint4((uint32_t)(p2b >> 32) ^ y1 ^ rk.k[4], (uint32_t)p2b, (uint32_t)(p2a >> 32) ^ c3,
+                             (uint32_t)p2a);
+#pragma unroll
+        for (int i = 3; i < 10; ++i) {
+            const uint64_t pa = (uint64_t)0xD2511F53u * c.x;
+            const uint64_t pb = (uint64_t)0xCD9E8D57u * c.z;
+            c = make_uint4((uint32_t)(pb >> 32) ^ c.y ^ rk.k[2 * i], (uint32_t)pb,
+                           (uint32_t)(pa >> 32) ^ c.w ^ rk.k[2 * i + 1], (uint32_t)pa);
+        }
+        return c;
+    }
+};
+
 __device__ __forceinline__ uint32_t word_of(const uint4& x, int k) {
     return k == 0 ? x.x : k == 1 ? x.y : k == 2 ? x.z : x.w;
 }
@@ -225,7 +269,8 @@ struct SampleCounters {
     unsigned long long work_cta;
     unsigned long long n_to_warp;    // samples handed from the thread tier to the warp tier
     unsigned long long n_to_cta;     // samples handed from the warp tier to the CTA tier
-    unsigned long long pad;
+    unsigned long long n_big;        // CTA-tier samples that outgrew a slot's queue
+    unsigned long long work_big;     // id cursor of the pass over them
 };
 }  // namespace skis
 
@@ -252,7 +297,13 @@ struct skis_sketch {
     uint2* srcpick = nullptr;            // lane tier, bucket form: prepared first-step picks
     uint64_t list_cap = 0;
     uint32_t* bitmaps = nullptr;         // CTA tier: one n-bit visited bitmap per slot
-    int32_t* queues = nullptr;           // CTA tier: one n-entry queue per slot
+    int32_t* queues = nullptr;           // CTA tier: one queue_cap-entry queue per slot
+    uint32_t queue_cap = 0;              // entries of each slot's queue: min(n, cta_queue_cap)
+    uint32_t cta_queue_cap = 1u << 20;   // option: queue entries per CTA-tier slot
+    int cta_threads = 512;               // option: threads of a CTA-tier block (256 or 512)
+    uint64_t* big_ids = nullptr;         // CTA tier -> the pass with n-entry queues
+    int32_t* big_queues = nullptr;       // that pass's queues (n entries each), allocated on first use
+    int big_slots = 0;
     uint32_t* lt_hash = nullptr;         // LT medium walks: visited table per lane
     int32_t* lt_list = nullptr;          // LT medium walks: member list per lane
     uint32_t* lt_slot = nullptr;         // LT medium walks: table slot of each listed member
@@ -268,6 +319,8 @@ struct skis_sketch {
     uint32_t thread_max_steps = 256;     // edge quads per sample in the thread tier
     uint32_t thread_max_retries = 32;    // rejected rounds in the thread tier before the warp tier
     uint32_t warp_max_coins = 65536;     // in-edges a sample may draw in the warp tier before the CTA tier
+    uint32_t cta_hub_quads = 256;        // CTA tier: rows of at least this many edge quads take the hub loop
+    uint64_t id_base = 0;                // sample id of header 0: the sketch holds ids [id_base, id_base + T)
     // last-call statistics
     uint64_t last_to_warp = 0, last_deferred = 0, last_passes = 0;
     double last_thread_ms = 0, last_warp_ms = 0, last_cta_ms = 0, last_sample_ms = 0;

@@ -97,6 +97,16 @@ def test_lt_samples_match_oracle_in_walk_order(name, ris):
         assert st["to_warp"] > 0 and dev["len"].max() > 48  # the lane-per-walk tier took part
     if name == "path-long-wc":
         assert st["deferred"] > 0 and dev["len"].max() > 1024  # the slot tier took part
+        # slot queues of 32 entries: the long walks move to the pass with n-entry queues
+        s2 = skis.skis_sketch_create(g, seed)
+        if ris:
+            skis.skis_sketch_set_option(s2, skis.SKIS_OPT_SAMPLER, 1)
+        skis.skis_sketch_set_option(s2, skis.SKIS_OPT_CTA_QUEUE_CAP, 32)
+        skis.skis_sample(s2, T)
+        dev2 = skis.skis_sketch_export(s2, 0, T)
+        for k in ("src", "len", "coins", "members"):
+            assert np.array_equal(dev2[k], dev[k]), k
+        s2.close()
     s.close()
     g.close()
 

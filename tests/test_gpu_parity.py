@@ -247,13 +247,19 @@ def test_always_live_giant_samples_take_the_cta_tier():
     src, dst = synth.er(n, m, 21)
     tau = np.full(m, 0xFFFFFFFF, np.uint32)
     g, o = _pair(n, src, dst, "tau", tau)
-    s = skis.skis_sketch_create(g, 77, 1 << 16)
-    T = 300
-    skis.skis_sample(s, T)
-    st = skis.skis_sketch_stats(s)
-    assert st["deferred"] > 0 and st["arena_capacity"] > (1 << 16)  # the arena grew
-    assert_samples_equal(skis.skis_sketch_export(s, 0, T), o.sample_ids(77, np.arange(T, dtype=np.uint64)))
-    s.close()
+    ora = o.sample_ids(77, np.arange(T := 300, dtype=np.uint64))
+    assert ora["len"].max() > 1000
+    # default slot queues, then queues of 32 and 1000 entries per CTA-tier slot: the
+    # samples that outgrow them move to the pass with n-entry queues
+    for cap in (None, 32, 1000):
+        s = skis.skis_sketch_create(g, 77, 1 << 16)
+        if cap:
+            skis.skis_sketch_set_option(s, skis.SKIS_OPT_CTA_QUEUE_CAP, cap)
+        skis.skis_sample(s, T)
+        st = skis.skis_sketch_stats(s)
+        assert st["deferred"] > 0 and st["arena_capacity"] > (1 << 16)  # the arena grew
+        assert_samples_equal(skis.skis_sketch_export(s, 0, T), ora)
+        s.close()
     g.close()
 
 
@@ -472,8 +478,11 @@ def test_hub_rows_on_every_tier_match_oracle(bucket):
     seed, T = 0x5EED0017, 600
     ora = o.sample_ids(seed, np.arange(T, dtype=np.uint64), bucket=bucket)
     assert np.bincount(dst, minlength=n).max() >= 4 * 64  # rows of 64+ quads exist
-    configs = ({}, {skis.SKIS_OPT_THREAD_MAX_DEG: 0},
-               {skis.SKIS_OPT_THREAD_MAX_DEG: 0, skis.SKIS_OPT_WARP_MAX_COINS: 1})
+    cta = {skis.SKIS_OPT_THREAD_MAX_DEG: 0, skis.SKIS_OPT_WARP_MAX_COINS: 1}
+    # on the CTA tier: the default hub threshold, no hub loop, every row
+    # through the hub loop, and a low threshold mixing both in one window
+    configs = ({}, {skis.SKIS_OPT_THREAD_MAX_DEG: 0}, cta, {**cta, skis.SKIS_OPT_CTA_HUB_QUADS: 0},
+               {**cta, skis.SKIS_OPT_CTA_HUB_QUADS: 1}, {**cta, skis.SKIS_OPT_CTA_HUB_QUADS: 3})
     for opts in configs:
         s = skis.skis_sketch_create(g, seed)
         skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, 1 if bucket else 0)
@@ -484,4 +493,53 @@ def test_hub_rows_on_every_tier_match_oracle(bucket):
         if skis.SKIS_OPT_WARP_MAX_COINS in opts:
             assert skis.skis_sketch_stats(s)["deferred"] > T // 4  # most samples ran on the CTA tier
         s.close()
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["rmat-tau", "chunglu-p", "tiny-ragged"])
+def test_cta_hub_loop_with_per_edge_thresholds(name):
+    # every sample on the CTA tier and every row through its hub loop, with a
+    # threshold per edge (sentinels and zero thresholds in tiny-ragged)
+    n, src, dst, model, w = GRAPHS[name]()
+    g, o = _pair(n, src, dst, model, w, weight_seed=5)
+    T, seed = 3000, 0x4B0B
+    ora = o.sample_ids(seed, np.arange(T, dtype=np.uint64))
+    for hub in (1, 2):
+        s = skis.skis_sketch_create(g, seed)
+        for k, v in ((skis.SKIS_OPT_THREAD_MAX_DEG, 0), (skis.SKIS_OPT_WARP_MAX_COINS, 1),
+                     (skis.SKIS_OPT_CTA_HUB_QUADS, hub)):
+            skis.skis_sketch_set_option(s, k, v)
+        skis.skis_sample(s, T)
+        assert skis.skis_sketch_stats(s)["cta_hub_quads"] == hub
+        assert_samples_equal(skis.skis_sketch_export(s, 0, T), ora)
+        s.close()
+    g.close()
+
+
+@pytest.mark.parametrize("first_id", [1, 123_456_789, (1 << 40) + 17])
+def test_first_id_places_the_samples_of_one_sketch(first_id):
+    # a sketch whose first sample id is F holds exactly samples F, F+1, ...
+    # of the one sketch the seed defines (its id-range shard)
+    n, src, dst, model, w = GRAPHS["chunglu-p"]()
+    g, o = _pair(n, src, dst, model, w)
+    seed, T = 0x5A4D, 20000
+    s = skis.skis_sketch_create(g, seed)
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_ID, first_id)
+    assert skis.skis_sample(s, T // 4) == first_id + T // 4
+    assert skis.skis_sample(s, T - T // 4) == first_id + T
+    with pytest.raises(skis.SkisError):
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_ID, 0)  # fixed once samples exist
+    st = skis.skis_sketch_stats(s)
+    assert st["T"] == T and st["first_id"] == first_id
+    ids = np.arange(first_id, first_id + T, dtype=np.uint64)
+    assert_samples_equal(skis.skis_sketch_export(s, first_id, T), o.sample_ids(seed, ids))
+    with pytest.raises(skis.SkisError):
+        skis.skis_sketch_export(s, first_id - 1, 2)  # below the sketch's ids
+    osk_ids = o.sample_ids(seed, ids)
+    off, seeds = synth.seed_sets(n, [10] * 20, 5)
+    cov, _ = skis.skis_estimate(s, off, seeds)
+    member = [set(osk_ids["members"][osk_ids["member_off"][t]:osk_ids["member_off"][t + 1]]) for t in range(T)]
+    want = [sum(1 for mset in member if mset.intersection(seeds[off[b]:off[b + 1]])) for b in range(20)]
+    assert cov.tolist() == want
+    s.close()
     g.close()
