@@ -186,17 +186,6 @@ typedef struct orc_graph {
     uint32_t *alias; /* n alias targets */
 } orc_graph;
 
-typedef struct { int32_t dst, src; int64_t idx; } edge_rec;
-
-static int edge_cmp(const void *a, const void *b)
-{
-    const edge_rec *x = (const edge_rec *)a, *y = (const edge_rec *)b;
-    if (x->dst != y->dst) return x->dst < y->dst ? -1 : 1;
-    if (x->src != y->src) return x->src < y->src ? -1 : 1;
-    if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
-    return 0;
-}
-
 static int ceil_log2(int64_t n)
 {
     int c = 0;
@@ -297,21 +286,42 @@ int orc_graph_build_model(int64_t n, int64_t m, const int32_t *src, const int32_
     g->w = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
     g->prob = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
     g->alias = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
-    edge_rec *rec = (edge_rec *)malloc(mm * sizeof(edge_rec));
-    if (!g->off || !g->src || !g->tau || !g->perm || !g->w || !g->prob || !g->alias || !rec) {
-        free(rec); orc_graph_free(g); return ORC_ENOMEM;
+    uint64_t *key = (uint64_t *)malloc(mm * sizeof(uint64_t));
+    uint64_t *key2 = (uint64_t *)malloc(mm * sizeof(uint64_t));
+    int64_t *idx = (int64_t *)malloc(mm * sizeof(int64_t));
+    int64_t *idx2 = (int64_t *)malloc(mm * sizeof(int64_t));
+    if (!g->off || !g->src || !g->tau || !g->perm || !g->w || !g->prob || !g->alias || !key || !key2 || !idx ||
+        !idx2) {
+        free(key); free(key2); free(idx); free(idx2); orc_graph_free(g); return ORC_ENOMEM;
     }
 
-    /* canonical in-CSR */
-    for (int64_t e = 0; e < m; e++) { rec[e].dst = dst[e]; rec[e].src = src[e]; rec[e].idx = e; }
-    qsort(rec, (size_t)m, sizeof(edge_rec), edge_cmp);
+    /* canonical in-CSR: rows by destination, each row by (source, input
+     * index). The key dst * n + src of every input edge is sorted with a
+     * stable least-significant-digit radix sort (11-bit digits) that carries
+     * the input index; stability keeps equal keys in input order. */
+    for (int64_t e = 0; e < m; e++) { key[e] = (uint64_t)dst[e] * (uint64_t)n + (uint64_t)src[e]; idx[e] = e; }
+    int key_bits = 0;
+    while (key_bits < 64 && ((uint64_t)n * (uint64_t)n - 1) >> key_bits) key_bits++;
+    for (int shift = 0; shift < key_bits; shift += 11) {
+        int64_t count[2049];
+        memset(count, 0, sizeof(count));
+        for (int64_t e = 0; e < m; e++) count[((key[e] >> shift) & 2047) + 1]++;
+        for (int d = 0; d < 2048; d++) count[d + 1] += count[d];
+        for (int64_t e = 0; e < m; e++) {
+            int64_t pos = count[(key[e] >> shift) & 2047]++;
+            key2[pos] = key[e];
+            idx2[pos] = idx[e];
+        }
+        uint64_t *tk = key; key = key2; key2 = tk;
+        int64_t *ti = idx; idx = idx2; idx2 = ti;
+    }
     for (int64_t e = 0; e < m; e++) {
-        g->src[e] = rec[e].src;
-        g->perm[e] = rec[e].idx;
-        g->off[rec[e].dst + 1]++;
+        g->src[e] = (int32_t)(key[e] % (uint64_t)n);
+        g->perm[e] = idx[e];
+        g->off[key[e] / (uint64_t)n + 1]++;
     }
     for (int64_t v = 0; v < n; v++) g->off[v + 1] += g->off[v];
-    free(rec);
+    free(key); free(key2); free(idx); free(idx2);
 
     /* thresholds (R1, R2) */
     static const double tri_levels[3] = {0.1, 0.01, 0.001};
