@@ -51,7 +51,8 @@ typedef enum skis_status {
     SKIS_ERR_CUDA = 3,         /* a CUDA call failed (message has the CUDA error) */
     SKIS_ERR_RETRY_LIMIT = 4,  /* a conditioned first step hit the retry cap */
     SKIS_ERR_ARENA_FULL = 5,   /* the sketch arena could not be grown */
-    SKIS_ERR_INTERNAL = 6      /* a library invariant failed on the device (a bug: the message says which) */
+    SKIS_ERR_INTERNAL = 6,     /* a library invariant failed on the device (a bug: the message says which) */
+    SKIS_ERR_EXCHANGE = 7      /* the caller's all-reduce callback reported a failure */
 } skis_status;
 
 /* Edge-probability models (Sec. II-A; Sec. VI "Weight Settings"). Every
@@ -315,6 +316,50 @@ int skis_estimate_noalloc(const skis_sketch *s, int32_t num_queries, const int64
                           const int32_t *seeds, int64_t *coverage_out, double *estimate_out,
                           char *error_buf, uint64_t error_len, void *cuda_stream);
 
+/* A sketch sharded by sample id over ranks (processes, usually one per GPU).
+ * The samples of Alg. 2's sketch R are independent and keyed by id, so rank
+ * r of N can hold the ids [F_r, F_r + T_r) of one seed's sketch
+ * (SKIS_OPT_FIRST_ID) with disjoint ranges whose union is R. Coverage counts
+ * (Eq. 21) and the greedy's marginal counts Delta (Alg. 3, Eq. margin) are
+ * sums over the ranks' samples, so the two entry points below write each
+ * rank's values into `exchange` and call the caller's all-reduce:
+ *
+ *   allreduce(ctx, buf, count, cuda_stream) must replace buf[0, count)
+ *   (int64, DEVICE memory) on every rank by its sum over all ranks and
+ *   return 0 (non-zero: failure, reported as SKIS_ERR_EXCHANGE). The library
+ *   has synchronised cuda_stream before the call; when the callback returns,
+ *   the sums must be in buf or be ordered before later work on cuda_stream
+ *   (an NCCL all-reduce on that stream, or a host-side reduction followed by
+ *   a copy back).
+ *
+ * `exchange` is a caller-owned DEVICE buffer (so that the caller's
+ * communication library can own or register it), int64 entries as stated
+ * below. Every rank makes the same calls with the same arguments (queries,
+ * k); each rank's sketch must be made with the same graph and seed. Results
+ * equal those of skis_estimate / skis_greedy_maxcover on one sketch holding
+ * the union of the ranks' samples, bit for bit. A rank that fails before an
+ * exchange leaves the others waiting in theirs: give the process group a
+ * timeout.
+ *
+ * skis_estimate_sharded: as skis_estimate (outputs on every rank);
+ * exchange holds num_queries + 1 entries; every rank's sketch holds at
+ * least one sample. Two exchanges per call. */
+typedef int (*skis_allreduce_fn)(void *ctx, int64_t *buf, int64_t count, void *cuda_stream);
+int skis_estimate_sharded(skis_sketch *s, int32_t num_queries, const int64_t *seed_offsets, const int32_t *seeds,
+                          int64_t *coverage_out, double *estimate_out, int mem_space, int64_t *exchange,
+                          skis_allreduce_fn allreduce, void *ctx, void *cuda_stream);
+
+/* skis_greedy_maxcover_sharded: as skis_greedy_maxcover (host outputs on
+ * every rank); exchange holds n + 1 entries. The ranks sum their sample
+ * counts, then their per-vertex list lengths (Delta at S = {}); each round
+ * every rank takes the same exact argmax, covers its own samples of the
+ * winner and the per-vertex decrements (and the number of newly covered
+ * samples, entry n) are summed: k + 2 exchanges, the per-round ones of
+ * 8 (n + 1) bytes. */
+int skis_greedy_maxcover_sharded(skis_sketch *s, int32_t k, int32_t *seeds_out, int64_t *coverage_out,
+                                 double *estimate_out, int64_t *exchange, skis_allreduce_fn allreduce, void *ctx,
+                                 void *cuda_stream);
+
 /* Influence maximisation with DSSA-style doubling over SKIS sketches
  * (Sec. V-B; the appendix "Improvements of SSA/DSSA using SKIS sketch"):
  * two independent sketches R (Philox key seed_r) and R^c (seed_rc) start with
@@ -376,6 +421,10 @@ void skis_server_free(skis_server *srv);
 /* Number of CUDA kernel launches the library has made in this process
  * (diagnostic; counts every launch of every entry point). */
 uint64_t skis_kernel_launches(void);
+
+/* Number of device memory allocations the library has made in this
+ * process (diagnostic; every entry point's, whatever the allocator). */
+uint64_t skis_device_allocations(void);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *skis_last_error(void);

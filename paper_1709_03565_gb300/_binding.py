@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libskis.so")
 
 SKIS_OK, SKIS_EINVAL, SKIS_ENOMEM, SKIS_ERR_CUDA = 0, 1, 2, 3
-SKIS_ERR_RETRY_LIMIT, SKIS_ERR_ARENA_FULL, SKIS_ERR_INTERNAL = 4, 5, 6
+SKIS_ERR_RETRY_LIMIT, SKIS_ERR_ARENA_FULL, SKIS_ERR_INTERNAL, SKIS_ERR_EXCHANGE = 4, 5, 6, 7
 SKIS_W_EXPLICIT_P, SKIS_W_EXPLICIT_TAU, SKIS_W_WC, SKIS_W_TRI = 0, 1, 2, 3
 SKIS_MEM_HOST, SKIS_MEM_DEVICE = 0, 1
 SKIS_OPT_RETRY_CAP, SKIS_OPT_CTA_SLOTS, SKIS_OPT_WARP_BLOCKS = 0, 1, 2
@@ -88,7 +88,10 @@ _SIGNATURES = [
     ("skis_server_poll", _INT, [_P, _U64, _P, _P, _P]),
     ("skis_server_counts", _INT, [_P, _P, _P, _P, _P]),
     ("skis_server_free", None, [_P]),
+    ("skis_estimate_sharded", _INT, [_P, _I32, _P, _P, _P, _P, _INT, _P, _P, _P, _P]),
+    ("skis_greedy_maxcover_sharded", _INT, [_P, _I32, _P, _P, _P, _P, _P, _P, _P]),
     ("skis_kernel_launches", ctypes.c_uint64, []),
+    ("skis_device_allocations", ctypes.c_uint64, []),
     ("skis_last_error", ctypes.c_char_p, []),
 ]
 
@@ -134,6 +137,42 @@ def _ptr(x, dtype):
     if not isinstance(x, np.ndarray) or x.dtype != np.dtype(dtype) or not x.flags["C_CONTIGUOUS"]:
         raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
     return ctypes.c_void_p(x.ctypes.data), SKIS_MEM_HOST
+
+
+def _numel(x) -> int:
+    return int(x.numel()) if _is_torch(x) else int(np.size(x))
+
+
+def _last(x) -> int:
+    return int(x[-1].item()) if _is_torch(x) else int(x[-1])
+
+
+def _check_queries(seed_offsets, seeds, coverage_out, estimate_out) -> int:
+    """Sizes of a query batch against its outputs, before any launch: the
+    library writes q coverage counts and estimates and reads seeds
+    [0, seed_offsets[q]); CUDA tensors must be on the current device."""
+    q = _numel(seed_offsets) - 1
+    if q < 0:
+        raise ValueError("seed_offsets needs q + 1 >= 1 entries")
+    if estimate_out is not None and _numel(estimate_out) < q:
+        raise ValueError(f"estimate_out holds {_numel(estimate_out)} entries, {q} queries need {q}")
+    if coverage_out is not None and _numel(coverage_out) < q:
+        raise ValueError(f"coverage_out holds {_numel(coverage_out)} entries, {q} queries need {q}")
+    need = _last(seed_offsets) if q > 0 else 0
+    have = 0 if seeds is None else _numel(seeds)
+    if need > have:
+        raise ValueError(f"seed_offsets[-1] = {need} but seeds holds {have} entries")
+    _check_current_device(seed_offsets, seeds, coverage_out, estimate_out)
+    return q
+
+
+def _check_current_device(*xs):
+    for x in xs:
+        if x is not None and _is_torch(x) and x.is_cuda:
+            import torch
+
+            if x.device.index != torch.cuda.current_device():
+                raise ValueError(f"tensor on {x.device}, the current device is cuda:{torch.cuda.current_device()}")
 
 
 def _space(*spaces):
@@ -284,7 +323,7 @@ def skis_estimate(s: Sketch, seed_offsets, seeds, coverage_out=None, estimate_ou
     device tensors in -> the caller's device output tensors are filled."""
     po, so = _ptr(seed_offsets, np.int64)
     pz, sz = _ptr(seeds, np.int32)
-    q = int(seed_offsets.shape[0]) - 1
+    q = _check_queries(seed_offsets, seeds, coverage_out, estimate_out)
     space = _space(so, sz)
     if estimate_out is None:
         if space == SKIS_MEM_DEVICE:
@@ -342,9 +381,11 @@ def skis_estimate_noalloc(s: Sketch, seed_offsets, seeds, coverage_out, estimate
     pz, sz = _ptr(seeds, np.int32)
     pc, sc = _ptr(coverage_out, np.int64)
     pe, se = _ptr(estimate_out, np.float64)
+    if estimate_out is None:
+        raise ValueError("skis_estimate_noalloc needs an estimate_out tensor")
+    q = _check_queries(seed_offsets, seeds, coverage_out, estimate_out)
     if _space(so, sz, sc, se) != SKIS_MEM_DEVICE:
         raise ValueError("skis_estimate_noalloc takes device tensors only")
-    q = int(seed_offsets.shape[0]) - 1
     buf = ctypes.create_string_buffer(256)
     rc = lib().skis_estimate_noalloc(s.ptr, q, po, pz, pc, pe, buf, 256, _stream(stream))
     if rc != SKIS_OK:
@@ -403,8 +444,78 @@ def skis_server_free(srv: Server):
     srv.close()
 
 
+# ----------------------------------------------------------- sharded sketch
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p)
+
+
+def _allreduce_cb(allreduce):
+    """C callback around allreduce(count): it must sum the caller's exchange
+    tensor's first count entries over the ranks in place; an exception is
+    reported to the library as a failure."""
+
+    def cb(ctx, buf, count, stream):
+        try:
+            allreduce(int(count))
+            return 0
+        except Exception:  # noqa: BLE001 - any failure of the caller's collective
+            return 1
+
+    return ALLREDUCE_FN(cb)
+
+
+def _check_exchange(exchange, need: int):
+    if not _is_torch(exchange) or not exchange.is_cuda or exchange.dtype.itemsize != 8 or not exchange.is_contiguous():
+        raise TypeError("exchange must be a contiguous int64 CUDA tensor")
+    if exchange.numel() < need:
+        raise ValueError(f"exchange holds {exchange.numel()} entries, {need} are needed")
+    _check_current_device(exchange)
+
+
+def skis_estimate_sharded(s: Sketch, seed_offsets, seeds, exchange, allreduce, coverage_out=None,
+                          estimate_out=None, stream=None):
+    """Eq. 21 over a sketch split by sample id across ranks; exchange: int64
+    CUDA tensor of >= q + 1 entries that allreduce(count) sums in place."""
+    po, so = _ptr(seed_offsets, np.int64)
+    pz, sz = _ptr(seeds, np.int32)
+    q = _check_queries(seed_offsets, seeds, coverage_out, estimate_out)
+    _check_exchange(exchange, q + 1)
+    space = _space(so, sz)
+    if estimate_out is None:
+        if space == SKIS_MEM_DEVICE:
+            raise ValueError("device queries need device output tensors")
+        estimate_out = np.empty(q, np.float64)
+        coverage_out = np.empty(q, np.int64) if coverage_out is None else coverage_out
+    pe, se = _ptr(estimate_out, np.float64)
+    pc, sc = _ptr(coverage_out, np.int64)
+    if _space(space, se, sc) != space:
+        raise ValueError("outputs must be in the memory space of the queries")
+    cb = _allreduce_cb(allreduce)
+    _check(lib().skis_estimate_sharded(s.ptr, q, po, pz, pc, pe, space, ctypes.c_void_p(exchange.data_ptr()), cb,
+                                       None, _stream(stream)))
+    return coverage_out, estimate_out
+
+
+def skis_greedy_maxcover_sharded(s: Sketch, k: int, exchange, allreduce, stream=None):
+    """Alg. 3 over a sketch split by sample id across ranks; exchange: int64
+    CUDA tensor of >= n + 1 entries that allreduce(count) sums in place."""
+    n = skis_graph_get_info(s._keep)["n"]
+    _check_exchange(exchange, n + 1)
+    seeds = np.empty(k, np.int32)
+    cov = np.empty(k, np.int64)
+    est = np.empty(k, np.float64)
+    cb = _allreduce_cb(allreduce)
+    _check(lib().skis_greedy_maxcover_sharded(s.ptr, int(k), ctypes.c_void_p(seeds.ctypes.data),
+                                              ctypes.c_void_p(cov.ctypes.data), ctypes.c_void_p(est.ctypes.data),
+                                              ctypes.c_void_p(exchange.data_ptr()), cb, None, _stream(stream)))
+    return seeds, cov, est
+
+
 def skis_kernel_launches() -> int:
     return int(lib().skis_kernel_launches())
+
+
+def skis_device_allocations() -> int:
+    return int(lib().skis_device_allocations())
 
 
 def skis_last_error() -> str:

@@ -311,13 +311,15 @@ extern "C" int skis_sketch_autotune(skis_sketch* s, uint64_t pilot_samples, uint
     API_CATCH
 }
 
-extern "C" int skis_estimate(skis_sketch* s, int32_t num_queries, const int64_t* seed_offsets, const int32_t* seeds,
-                             int64_t* coverage_out, double* estimate_out, int mem_space, void* cuda_stream) {
-    API_TRY
-    if (!s || !seed_offsets || !estimate_out) return fail(SKIS_EINVAL, "skis_estimate: NULL argument");
-    if (num_queries < 0) return fail(SKIS_EINVAL, "skis_estimate: negative query count");
-    if (mem_space != SKIS_MEM_HOST && mem_space != SKIS_MEM_DEVICE)
-        return fail(SKIS_EINVAL, "skis_estimate: bad mem_space");
+// skis_estimate and skis_estimate_sharded (exch != NULL): argument checks
+// and host <-> device marshalling around the device computation.
+static int estimate_call(const char* name, skis_sketch* s, int32_t num_queries, const int64_t* seed_offsets,
+                         const int32_t* seeds, int64_t* coverage_out, double* estimate_out, int mem_space,
+                         int64_t* exch, skis_allreduce_fn fn, void* ctx, void* cuda_stream) {
+    const std::string where(name);
+    if (!s || !seed_offsets || !estimate_out) return fail(SKIS_EINVAL, where + ": NULL argument");
+    if (num_queries < 0) return fail(SKIS_EINVAL, where + ": negative query count");
+    if (mem_space != SKIS_MEM_HOST && mem_space != SKIS_MEM_DEVICE) return fail(SKIS_EINVAL, where + ": bad mem_space");
     if (num_queries == 0) return SKIS_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     s->stream = st;
@@ -326,38 +328,40 @@ extern "C" int skis_estimate(skis_sketch* s, int32_t num_queries, const int64_t*
     if (mem_space == SKIS_MEM_HOST) {
         std::copy(seed_offsets, seed_offsets + num_queries + 1, off.begin());
     } else {
-        API_CUDA("skis_estimate", cudaMemcpyAsync(off.data(), seed_offsets, (num_queries + 1) * 8,
-                                                  cudaMemcpyDeviceToHost, st));
-        API_CUDA("skis_estimate", cudaStreamSynchronize(st));
+        API_CUDA(name, cudaMemcpyAsync(off.data(), seed_offsets, (num_queries + 1) * 8, cudaMemcpyDeviceToHost, st));
+        API_CUDA(name, cudaStreamSynchronize(st));
     }
-    if (off[0] < 0) return fail(SKIS_EINVAL, "skis_estimate: negative seed offset");
+    if (off[0] < 0) return fail(SKIS_EINVAL, where + ": negative seed offset");
     for (int32_t b = 0; b < num_queries; ++b)
-        if (off[b + 1] < off[b]) return fail(SKIS_EINVAL, "skis_estimate: seed offsets decrease");
-    if (off[num_queries] > 0 && !seeds) return fail(SKIS_EINVAL, "skis_estimate: seeds is NULL");
+        if (off[b + 1] < off[b]) return fail(SKIS_EINVAL, where + ": seed offsets decrease");
+    if (off[num_queries] > 0 && !seeds) return fail(SKIS_EINVAL, where + ": seeds is NULL");
     std::string err;
+    auto run = [&](const int64_t* d_off, const int32_t* d_seeds, int64_t* d_cov, double* d_est) {
+        return exch ? sketch_estimate_sharded(s, num_queries, d_off, d_seeds, off.data(), d_cov, d_est, exch, fn, ctx,
+                                              st, &err)
+                    : sketch_estimate(s, num_queries, d_off, d_seeds, off.data(), d_cov, d_est, st, &err);
+    };
     int rc;
     if (mem_space == SKIS_MEM_DEVICE) {
-        rc = sketch_estimate(s, num_queries, seed_offsets, seeds, off.data(), coverage_out, estimate_out, st, &err);
+        rc = run(seed_offsets, seeds, coverage_out, estimate_out);
     } else {
         const int64_t nseeds = off[num_queries];
         int64_t* d_off = nullptr;
         int32_t* d_seeds = nullptr;
         int64_t* d_cov = nullptr;
         double* d_est = nullptr;
-        API_CUDA("skis_estimate", dev_alloc_t(&d_off, (size_t)num_queries + 1, st));
-        API_CUDA("skis_estimate", dev_alloc_t(&d_seeds, (size_t)std::max<int64_t>(nseeds, 1), st));
-        API_CUDA("skis_estimate", dev_alloc_t(&d_cov, (size_t)num_queries, st));
-        API_CUDA("skis_estimate", dev_alloc_t(&d_est, (size_t)num_queries, st));
-        API_CUDA("skis_estimate", cudaMemcpyAsync(d_off, off.data(), (num_queries + 1) * 8, cudaMemcpyHostToDevice, st));
-        if (nseeds)
-            API_CUDA("skis_estimate", cudaMemcpyAsync(d_seeds, seeds, nseeds * 4, cudaMemcpyHostToDevice, st));
-        rc = sketch_estimate(s, num_queries, d_off, d_seeds, off.data(), d_cov, d_est, st, &err);
+        API_CUDA(name, dev_alloc_t(&d_off, (size_t)num_queries + 1, st));
+        API_CUDA(name, dev_alloc_t(&d_seeds, (size_t)std::max<int64_t>(nseeds, 1), st));
+        API_CUDA(name, dev_alloc_t(&d_cov, (size_t)num_queries, st));
+        API_CUDA(name, dev_alloc_t(&d_est, (size_t)num_queries, st));
+        API_CUDA(name, cudaMemcpyAsync(d_off, off.data(), (num_queries + 1) * 8, cudaMemcpyHostToDevice, st));
+        if (nseeds) API_CUDA(name, cudaMemcpyAsync(d_seeds, seeds, nseeds * 4, cudaMemcpyHostToDevice, st));
+        rc = run(d_off, d_seeds, d_cov, d_est);
         if (rc == SKIS_OK) {
             if (coverage_out)
-                API_CUDA("skis_estimate",
-                         cudaMemcpyAsync(coverage_out, d_cov, num_queries * 8, cudaMemcpyDeviceToHost, st));
-            API_CUDA("skis_estimate", cudaMemcpyAsync(estimate_out, d_est, num_queries * 8, cudaMemcpyDeviceToHost, st));
-            API_CUDA("skis_estimate", cudaStreamSynchronize(st));
+                API_CUDA(name, cudaMemcpyAsync(coverage_out, d_cov, num_queries * 8, cudaMemcpyDeviceToHost, st));
+            API_CUDA(name, cudaMemcpyAsync(estimate_out, d_est, num_queries * 8, cudaMemcpyDeviceToHost, st));
+            API_CUDA(name, cudaStreamSynchronize(st));
         }
         dev_free(d_off, st);
         dev_free(d_seeds, st);
@@ -366,6 +370,25 @@ extern "C" int skis_estimate(skis_sketch* s, int32_t num_queries, const int64_t*
     }
     if (rc != SKIS_OK) return fail(rc, err);
     return SKIS_OK;
+}
+
+extern "C" int skis_estimate(skis_sketch* s, int32_t num_queries, const int64_t* seed_offsets, const int32_t* seeds,
+                             int64_t* coverage_out, double* estimate_out, int mem_space, void* cuda_stream) {
+    API_TRY
+    return estimate_call("skis_estimate", s, num_queries, seed_offsets, seeds, coverage_out, estimate_out, mem_space,
+                         nullptr, nullptr, nullptr, cuda_stream);
+    API_CATCH
+}
+
+extern "C" int skis_estimate_sharded(skis_sketch* s, int32_t num_queries, const int64_t* seed_offsets,
+                                     const int32_t* seeds, int64_t* coverage_out, double* estimate_out, int mem_space,
+                                     int64_t* exchange, skis_allreduce_fn allreduce, void* ctx, void* cuda_stream) {
+    API_TRY
+    if (!exchange || !allreduce) return fail(SKIS_EINVAL, "skis_estimate_sharded: NULL exchange or all-reduce");
+    if (s && num_queries > 0 && s->T == 0)
+        return fail(SKIS_EINVAL, "skis_estimate_sharded: every rank's sketch must hold a sample");
+    return estimate_call("skis_estimate_sharded", s, num_queries, seed_offsets, seeds, coverage_out, estimate_out,
+                         mem_space, exchange, allreduce, ctx, cuda_stream);
     API_CATCH
 }
 
@@ -377,6 +400,21 @@ extern "C" int skis_greedy_maxcover(skis_sketch* s, int32_t k, int32_t* seeds_ou
     s->stream = st;
     std::string err;
     const int rc = sketch_greedy(s, k, seeds_out, coverage_out, estimate_out, st, &err);
+    if (rc != SKIS_OK) return fail(rc, err);
+    return SKIS_OK;
+    API_CATCH
+}
+
+extern "C" int skis_greedy_maxcover_sharded(skis_sketch* s, int32_t k, int32_t* seeds_out, int64_t* coverage_out,
+                                            double* estimate_out, int64_t* exchange, skis_allreduce_fn allreduce,
+                                            void* ctx, void* cuda_stream) {
+    API_TRY
+    if (!s || (k > 0 && !seeds_out)) return fail(SKIS_EINVAL, "skis_greedy_maxcover_sharded: NULL argument");
+    if (!exchange || !allreduce) return fail(SKIS_EINVAL, "skis_greedy_maxcover_sharded: NULL exchange or all-reduce");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    s->stream = st;
+    std::string err;
+    const int rc = sketch_greedy_sharded(s, k, seeds_out, coverage_out, estimate_out, exchange, allreduce, ctx, st, &err);
     if (rc != SKIS_OK) return fail(rc, err);
     return SKIS_OK;
     API_CATCH
@@ -549,3 +587,5 @@ extern "C" void skis_sketch_free(skis_sketch* s) {
 extern "C" const char* skis_last_error(void) { return g_err.c_str(); }
 
 extern "C" uint64_t skis_kernel_launches(void) { return launches(); }
+
+extern "C" uint64_t skis_device_allocations(void) { return allocations(); }

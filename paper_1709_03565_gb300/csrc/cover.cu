@@ -803,3 +803,244 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
 }
 
 }  // namespace skis
+
+// ------------------------------------------------------ sharded sketch
+// A sketch split by sample id over ranks (every rank holds the samples of
+// one id range of one seed's sketch). Coverage counts and Delta are sums
+// over the ranks' samples, so the per-rank values are summed through the
+// caller's all-reduce in a caller-owned device buffer, and every rank then
+// takes the same decisions as one process holding the union sketch.
+namespace skis {
+
+__global__ void k_shard_delta0(const uint64_t* __restrict__ inv_off, int64_t n, int64_t* __restrict__ x) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += (int64_t)gridDim.x * blockDim.x)
+        x[v] = v < n ? (int64_t)(inv_off[v + 1] - inv_off[v]) : 0;
+}
+
+// Block bests of the exact key Delta W + T (2^f - w_v) (RIS: Delta) over v
+// outside S, ties to the lowest id.
+__global__ void __launch_bounds__(256) k_shard_argmax(const int64_t* __restrict__ delta, const uint64_t* __restrict__ w,
+                                                      const uint8_t* __restrict__ inS, int64_t n, uint64_t W,
+                                                      uint64_t T, int f, int ris, KeyId* __restrict__ partial) {
+    __shared__ KeyId s_part[256 / 32];
+    const uint64_t one_f = 1ull << f;
+    KeyId best{0, 0xFFFFFFFFu, 0};
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (inS[v]) continue;
+        const u128 dv = (u128)(uint64_t)delta[v];
+        const KeyId c{ris ? dv : dv * W + (u128)T * (one_f - w[v]), (uint32_t)v, 1u, 0u, 0u};
+        if (better(c, best)) best = c;
+    }
+    best = block_best(best, s_part);
+    if (threadIdx.x == 0) partial[blockIdx.x] = best;
+}
+
+// The round's winner from the block bests: joins S; recorded as seed r.
+__global__ void k_shard_commit(const KeyId* __restrict__ partial, int nparts, uint8_t* __restrict__ inS,
+                               int32_t* __restrict__ seeds, int32_t r, uint32_t* __restrict__ win) {
+    const int lane = threadIdx.x & 31;
+    KeyId b{0, 0xFFFFFFFFu, 0};
+    for (int i = lane; i < nparts; i += 32)
+        if (better(partial[i], b)) b = partial[i];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const KeyId o = shfl_down_keyid(b, d);
+        if (better(o, b)) b = o;
+    }
+    if (lane == 0) {  // a valid winner exists: k <= n and each round adds one vertex
+        inS[b.id] = 1;
+        seeds[r] = (int32_t)b.id;
+        *win = b.id;
+    }
+}
+
+// Cover this rank's uncovered samples of the winner: x[u] += 1 for every
+// member u of each, x[n] += the number of them.
+__global__ void __launch_bounds__(256) k_shard_cover(const uint32_t* __restrict__ win,
+                                                     const uint64_t* __restrict__ inv_off,
+                                                     const uint32_t* __restrict__ inv,
+                                                     const uint64_t* __restrict__ h_off,
+                                                     const uint32_t* __restrict__ h_len,
+                                                     const int32_t* __restrict__ arena, uint32_t* __restrict__ covered,
+                                                     int64_t n, int64_t* __restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t v = *win;
+    const uint64_t lo = inv_off[v], cnt = inv_off[v + 1] - lo;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    unsigned long long* xc = reinterpret_cast<unsigned long long*>(x);
+    for (uint64_t base = ((uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; base < cnt;
+         base += nwarps * 32) {
+        uint64_t off = 0;
+        uint32_t len = 0;
+        if (base + lane < cnt) {
+            const uint32_t j = inv[lo + base + lane];
+            const uint32_t bit = 1u << (j & 31);
+            if ((atomicOr(&covered[j >> 5], bit) & bit) == 0) {
+                off = h_off[j];
+                len = h_len[j];
+                atomicAdd(xc + n, 1ull);
+            }
+        }
+        warp_members(off, len, arena, [&](int, int32_t u) { atomicAdd(xc + u, 1ull); });
+    }
+}
+
+// Delta -= the summed decrements; the running coverage and Eq. 21 of the
+// prefix S (thread 0; acc = {Cov, sum over S of 2^f - w_v}).
+__global__ void k_shard_update(int64_t* __restrict__ delta, const int64_t* __restrict__ x, int64_t n,
+                               const uint32_t* __restrict__ win, const uint64_t* __restrict__ w, uint64_t W,
+                               uint64_t T, int f, int ris, int32_t r, uint64_t* __restrict__ acc,
+                               int64_t* __restrict__ cov_out, double* __restrict__ est_out) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        delta[v] -= x[v];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint64_t cov = acc[0] + (uint64_t)x[n];
+        const uint64_t sum_c = acc[1] + ((1ull << f) - w[*win]);
+        acc[0] = cov;
+        acc[1] = sum_c;
+        cov_out[r] = (int64_t)cov;
+        const u128 N = ris ? (u128)cov * (uint64_t)n : (u128)cov * W + (u128)T * sum_c;
+        const u128 D = ris ? (u128)T : (u128)T << f;
+        est_out[r] = u128_to_double(N) / u128_to_double(D);
+    }
+}
+
+// The caller's all-reduce of buf[0, count), after the work that wrote it.
+static int exchange(skis_allreduce_fn fn, void* ctx, int64_t* buf, int64_t count, cudaStream_t st, const char* where,
+                    std::string* err) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        *err = std::string(where) + ": CUDA error: " + cudaGetErrorString(e);
+        return SKIS_ERR_CUDA;
+    }
+    if (fn(ctx, buf, count, (void*)st) != 0) {
+        *err = std::string(where) + ": the all-reduce callback failed";
+        return SKIS_ERR_EXCHANGE;
+    }
+    return SKIS_OK;
+}
+
+int sketch_estimate_sharded(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds,
+                            const int64_t* h_off, int64_t* d_cov, double* d_est, int64_t* exch, skis_allreduce_fn fn,
+                            void* ctx, cudaStream_t st, std::string* err) {
+    const char* where = "skis_estimate_sharded";
+    const skis_graph* g = s->g;
+    double* tmp = nullptr;
+    CV_CUDA(dev_alloc_t(&tmp, (size_t)q, st));
+    // this rank's counts into exch[0, q) (validating the queries), its T into exch[q]
+    int rc = sketch_estimate(s, q, d_off, d_seeds, h_off, exch, tmp, st, err);
+    dev_free(tmp, st);
+    if (rc != SKIS_OK) return rc;
+    const int64_t T_rank = (int64_t)s->T;
+    CV_CUDA(cudaMemcpyAsync(exch + q, &T_rank, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    rc = exchange(fn, ctx, exch, (int64_t)q + 1, st, where, err);
+    if (rc != SKIS_OK) return rc;
+    int64_t T = 0;
+    CV_CUDA(cudaMemcpyAsync(&T, exch + q, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CV_CUDA(cudaStreamSynchronize(st));
+    for (int32_t q0 = 0; q0 < q; q0 += 64) {
+        const int32_t qn = std::min<int32_t>(64, q - q0);
+        k_estimate<<<div_up((int64_t)qn * 32, 256), 256, 0, st>>>(
+            d_off, d_seeds, q0, qn, g->n, g->w, g->f, g->W, (uint64_t)T,
+            reinterpret_cast<const unsigned long long*>(exch + q0), d_cov, d_est, s->ris);
+        note_launch();
+        CV_CUDA(cudaGetLastError());
+    }
+    CV_CUDA(cudaStreamSynchronize(st));
+    return SKIS_OK;
+}
+
+int sketch_greedy_sharded(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, double* h_est, int64_t* exch,
+                          skis_allreduce_fn fn, void* ctx, cudaStream_t st, std::string* err) {
+    const char* where = "skis_greedy_maxcover_sharded";
+    const skis_graph* g = s->g;
+    const int64_t n = g->n;
+    if (k < 0 || k > n) {
+        *err = "skis_greedy_maxcover_sharded: k must be in [0, n]";
+        return SKIS_EINVAL;
+    }
+    if (s->T >= (1ull << 32)) {
+        *err = "skis_greedy_maxcover_sharded: a rank's sketch must hold fewer than 2^32 samples";
+        return SKIS_EINVAL;
+    }
+    if (k == 0) return SKIS_OK;
+    // the union sketch's T
+    const int64_t T_rank = (int64_t)s->T;
+    CV_CUDA(cudaMemcpyAsync(exch, &T_rank, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    int rc = exchange(fn, ctx, exch, 1, st, where, err);
+    if (rc != SKIS_OK) return rc;
+    int64_t T = 0;
+    CV_CUDA(cudaMemcpyAsync(&T, exch, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CV_CUDA(cudaStreamSynchronize(st));
+    if (T <= 0) {
+        *err = "skis_greedy_maxcover_sharded: the ranks' sketches hold no samples";
+        return SKIS_EINVAL;
+    }
+    rc = sketch_inverted(s, st, err);
+    if (rc != SKIS_OK) return rc;
+    int64_t* delta = nullptr;
+    uint8_t* inS = nullptr;
+    uint32_t *covered = nullptr, *win = nullptr;
+    KeyId* partial = nullptr;
+    int32_t* d_seeds = nullptr;
+    int64_t* d_cov = nullptr;
+    double* d_est = nullptr;
+    uint64_t* acc = nullptr;
+    const int nb = sm_count() * 4;
+    const uint64_t cwords = std::max<uint64_t>(1, (s->T + 31) / 32);
+    auto body = [&]() -> int {
+        CV_CUDA(dev_alloc_t(&delta, (size_t)n, st));
+        CV_CUDA(dev_alloc_t(&inS, (size_t)n, st));
+        CV_CUDA(dev_alloc_t(&covered, (size_t)cwords, st));
+        CV_CUDA(dev_alloc_t(&win, 1, st));
+        CV_CUDA(dev_alloc_t(&partial, (size_t)nb, st));
+        CV_CUDA(dev_alloc_t(&d_seeds, (size_t)k, st));
+        CV_CUDA(dev_alloc_t(&d_cov, (size_t)k, st));
+        CV_CUDA(dev_alloc_t(&d_est, (size_t)k, st));
+        CV_CUDA(dev_alloc_t(&acc, 2, st));
+        CV_CUDA(cudaMemsetAsync(inS, 0, (size_t)n, st));
+        CV_CUDA(cudaMemsetAsync(covered, 0, cwords * sizeof(uint32_t), st));
+        CV_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(uint64_t), st));
+        // Delta_R(v, {}) over the union: the ranks' list lengths summed
+        const int b1 = (int)std::max<int64_t>(1, std::min<int64_t>((n + 256) / 256, (int64_t)sm_count() * 8));
+        k_shard_delta0<<<b1, 256, 0, st>>>(s->inv_off, n, exch); note_launch();
+        CV_CUDA(cudaGetLastError());
+        int e = exchange(fn, ctx, exch, n + 1, st, where, err);
+        if (e != SKIS_OK) return e;
+        CV_CUDA(cudaMemcpyAsync(delta, exch, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+        const int cb = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * 8, (s->T + 255) / 256));
+        for (int32_t r = 0; r < k; ++r) {
+            k_shard_argmax<<<nb, 256, 0, st>>>(delta, g->w, inS, n, g->W, (uint64_t)T, g->f, s->ris, partial);
+            note_launch();
+            k_shard_commit<<<1, 32, 0, st>>>(partial, nb, inS, d_seeds, r, win); note_launch();
+            CV_CUDA(cudaMemsetAsync(exch, 0, (size_t)(n + 1) * sizeof(int64_t), st));
+            k_shard_cover<<<cb, 256, 0, st>>>(win, s->inv_off, s->inv, s->h_off, s->h_len, s->arena, covered, n, exch);
+            note_launch();
+            CV_CUDA(cudaGetLastError());
+            e = exchange(fn, ctx, exch, n + 1, st, where, err);
+            if (e != SKIS_OK) return e;
+            k_shard_update<<<b1, 256, 0, st>>>(delta, exch, n, win, g->w, g->W, (uint64_t)T, g->f, s->ris, r, acc,
+                                               d_cov, d_est);
+            note_launch();
+            CV_CUDA(cudaGetLastError());
+        }
+        CV_CUDA(cudaMemcpyAsync(h_seeds, d_seeds, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if (h_cov) CV_CUDA(cudaMemcpyAsync(h_cov, d_cov, (size_t)k * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        if (h_est) CV_CUDA(cudaMemcpyAsync(h_est, d_est, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CV_CUDA(cudaStreamSynchronize(st));
+        return SKIS_OK;
+    };
+    rc = body();
+    dev_free(delta, st);
+    dev_free(inS, st);
+    dev_free(covered, st);
+    dev_free(win, st);
+    dev_free(partial, st);
+    dev_free(d_seeds, st);
+    dev_free(d_cov, st);
+    dev_free(d_est, st);
+    dev_free(acc, st);
+    return rc;
+}
+
+}  // namespace skis

@@ -123,8 +123,25 @@ extern "C" int skis_estimate_noalloc(const skis_sketch* s, int32_t num_queries, 
     e = cudaMemcpyAsync(&h, status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return noalloc_fail(error_buf, error_len, SKIS_ERR_CUDA, "skis_estimate_noalloc: ", cudaGetErrorString(e));
-    if (h.flags & kStInval)
-        return noalloc_fail(error_buf, error_len, SKIS_EINVAL,
-                            "skis_estimate_noalloc: a query is empty, has a seed outside [0, n) or repeats a seed");
+    if (h.flags & kStInval) {
+        // the message names the failing query as skis_estimate's does, its
+        // index written out in a stack buffer (no allocation)
+        char msg[160];
+        const char* head = "skis_estimate_noalloc: query ";
+        const char* tail = " is empty, has a seed outside [0, n) or repeats a seed";
+        char digits[24];
+        int nd = 0;
+        unsigned long long q = h.first_bad;
+        do {
+            digits[nd++] = (char)('0' + q % 10);
+            q /= 10;
+        } while (q && nd < 20);
+        int i = 0;
+        for (int k = 0; head[k]; ++k) msg[i++] = head[k];
+        while (nd) msg[i++] = digits[--nd];
+        for (int k = 0; tail[k] && i + 1 < (int)sizeof(msg); ++k) msg[i++] = tail[k];
+        msg[i] = 0;
+        return noalloc_fail(error_buf, error_len, SKIS_EINVAL, msg);
+    }
     return SKIS_OK;
 }

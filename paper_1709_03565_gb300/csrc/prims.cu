@@ -16,6 +16,13 @@ uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
 // ------------------------------------------------------------- allocation
 static std::once_flag g_pool_once;
+static std::atomic<uint64_t> g_allocs{0};
+uint64_t allocations() { return g_allocs.load(std::memory_order_relaxed); }
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    return cudaMalloc(p, bytes);
+}
 
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
     std::call_once(g_pool_once, [] {
@@ -31,6 +38,7 @@ cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st) {
     });
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     return cudaMallocAsync(p, bytes, st);
 }
 

@@ -142,15 +142,15 @@ extern "C" int skis_server_create(skis_server** out, skis_sketch* s, int32_t slo
             chk(cudaMallocHost((void**)&sl.h_cov, 64 * sizeof(int64_t)));
             chk(cudaMallocHost((void**)&sl.h_est, 64 * sizeof(double)));
             chk(cudaMallocHost((void**)&sl.h_status, sizeof(DevStatus)));
-            chk(cudaMalloc((void**)&sl.d_off, 65 * sizeof(int64_t)));
-            chk(cudaMalloc((void**)&sl.d_seeds, seed_capacity * sizeof(int32_t)));
-            chk(cudaMalloc((void**)&sl.d_cov, 64 * sizeof(int64_t)));
-            chk(cudaMalloc((void**)&sl.d_est, 64 * sizeof(double)));
-            chk(cudaMalloc((void**)&sl.d_smask, (size_t)s->T * sizeof(uint64_t)));
-            chk(cudaMalloc((void**)&sl.d_chunk_cnt, seed_capacity * sizeof(uint32_t)));
-            chk(cudaMalloc((void**)&sl.d_chunk_off, (seed_capacity + 1) * sizeof(uint64_t)));
-            chk(cudaMalloc((void**)&sl.d_qcov, 64 * sizeof(unsigned long long)));
-            chk(cudaMalloc((void**)&sl.d_status, sizeof(DevStatus)));
+            chk(dev_malloc((void**)&sl.d_off, 65 * sizeof(int64_t)));
+            chk(dev_malloc((void**)&sl.d_seeds, seed_capacity * sizeof(int32_t)));
+            chk(dev_malloc((void**)&sl.d_cov, 64 * sizeof(int64_t)));
+            chk(dev_malloc((void**)&sl.d_est, 64 * sizeof(double)));
+            chk(dev_malloc((void**)&sl.d_smask, (size_t)s->T * sizeof(uint64_t)));
+            chk(dev_malloc((void**)&sl.d_chunk_cnt, seed_capacity * sizeof(uint32_t)));
+            chk(dev_malloc((void**)&sl.d_chunk_off, (seed_capacity + 1) * sizeof(uint64_t)));
+            chk(dev_malloc((void**)&sl.d_qcov, 64 * sizeof(unsigned long long)));
+            chk(dev_malloc((void**)&sl.d_status, sizeof(DevStatus)));
             if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_smask, 0, (size_t)s->T * sizeof(uint64_t), sl.stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(sl.stream);
             if (e != cudaSuccess) {

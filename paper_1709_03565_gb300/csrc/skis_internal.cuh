@@ -8,6 +8,8 @@
 
 #include <string>
 
+#include "../../include/skis.h"
+
 namespace skis {
 
 typedef unsigned __int128 u128;
@@ -205,6 +207,10 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // Stream-ordered allocation helpers (cudaMallocAsync / cudaFreeAsync).
 cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
 void dev_free(void* p, cudaStream_t st);
+// Synchronous allocation (cudaMalloc), for long-lived buffers.
+cudaError_t dev_malloc(void** p, size_t bytes);
+// Process-wide count of device allocations made through dev_alloc / dev_malloc.
+uint64_t allocations();
 
 template <typename T>
 cudaError_t dev_alloc_t(T** p, size_t count, cudaStream_t st) {
@@ -353,6 +359,13 @@ int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32
                     int64_t* d_cov, double* d_est, cudaStream_t st, std::string* err);
 int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, double* h_est, cudaStream_t st,
                   std::string* err);
+// Eq. 21 and Alg. 3 over a sketch split by sample id across ranks; exch is
+// the caller's device buffer that fn sums over the ranks in place.
+int sketch_estimate_sharded(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds,
+                            const int64_t* h_off, int64_t* d_cov, double* d_est, int64_t* exch, skis_allreduce_fn fn,
+                            void* ctx, cudaStream_t st, std::string* err);
+int sketch_greedy_sharded(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, double* h_est, int64_t* exch,
+                          skis_allreduce_fn fn, void* ctx, cudaStream_t st, std::string* err);
 // Builds (or reuses) the inverted index of the current T samples.
 int sketch_inverted(skis_sketch* s, cudaStream_t st, std::string* err);
 // Coverage of queries [q0, q0 + qn) of a CSR batch through the inverted

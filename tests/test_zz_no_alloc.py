@@ -59,6 +59,22 @@ def test_noalloc_matches_estimate_on_two_calls_in_a_row(sketch):
         np.testing.assert_allclose(d_est.cpu().numpy(), est_ref, rtol=REL, atol=0)
 
 
+def test_noalloc_makes_no_device_allocation(sketch):
+    # the library counts every device allocation it makes: a warm call of the
+    # entry point adds none (skis_estimate, for comparison, does)
+    torch, n, g, s = sketch
+    off, seeds, d_off, d_seeds = _device_queries(torch, n, [10] * 16, 9)
+    d_cov = torch.empty(16, dtype=torch.int64, device="cuda")
+    d_est = torch.empty(16, dtype=torch.float64, device="cuda")
+    skis.skis_estimate_noalloc(s, d_off, d_seeds, d_cov, d_est)  # warm: the array's address is looked up
+    before = skis.skis_device_allocations()
+    for _ in range(3):
+        skis.skis_estimate_noalloc(s, d_off, d_seeds, d_cov, d_est)
+    assert skis.skis_device_allocations() == before
+    skis.skis_estimate(s, off, seeds)
+    assert skis.skis_device_allocations() > before
+
+
 def test_noalloc_limits_are_rejected_with_a_message(sketch):
     torch, n, g, s = sketch
     off, seeds, d_off, d_seeds = _device_queries(torch, n, [3] * 65, 7)
@@ -72,7 +88,15 @@ def test_noalloc_limits_are_rejected_with_a_message(sketch):
     bad_seeds = torch.tensor([4, 4], dtype=torch.int32, device="cuda")
     with pytest.raises(skis.SkisError) as e:
         skis.skis_estimate_noalloc(s, bad_off, bad_seeds, d_cov[:1], d_est[:1])
-    assert e.value.code == skis.SKIS_EINVAL
+    assert e.value.code == skis.SKIS_EINVAL and "query 0 " in str(e.value)
+    # the same message as skis_estimate's, naming the failing query
+    two_off = torch.tensor([0, 1, 3], dtype=torch.int64, device="cuda")
+    two_seeds = torch.tensor([1, 7, 7], dtype=torch.int32, device="cuda")
+    with pytest.raises(skis.SkisError) as e:
+        skis.skis_estimate_noalloc(s, two_off, two_seeds, d_cov[:2], d_est[:2])
+    with pytest.raises(skis.SkisError) as e2:
+        skis.skis_estimate(s, two_off, two_seeds, d_cov[:2], d_est[:2])
+    assert "query 1 " in str(e.value) and str(e.value).split(": ", 1)[1] == str(e2.value).split(": ", 1)[1]
     # graphs above 2^20 vertices exceed the static scratch
     big_n = (1 << 20) + 1
     g2 = skis.skis_load_graph(big_n, np.array([1, 2], np.int32), np.array([0, 0], np.int32))
