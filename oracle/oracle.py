@@ -129,14 +129,13 @@ class OracleGraph:
             _lib().orc_graph_free(h)
             self._h = None
 
-    def arrays(self) -> dict:
+    def arrays(self, keys=("off", "src", "tau", "perm", "w", "prob", "alias")) -> dict:
+        """The graph's arrays (those named in keys)."""
         n, m = self.n, self.m
-        a = dict(off=np.empty(n + 1, np.int64), src=np.empty(m, np.int32),
-                 tau=np.empty(m, np.uint32), perm=np.empty(m, np.int64),
-                 w=np.empty(n, np.uint64), prob=np.empty(n, np.uint64),
-                 alias=np.empty(n, np.uint32))
-        _lib().orc_graph_arrays(self._h, _p(a["off"]), _p(a["src"]), _p(a["tau"]), _p(a["perm"]),
-                                _p(a["w"]), _p(a["prob"]), _p(a["alias"]))
+        shapes = dict(off=(n + 1, np.int64), src=(m, np.int32), tau=(m, np.uint32), perm=(m, np.int64),
+                      w=(n, np.uint64), prob=(n, np.uint64), alias=(n, np.uint32))
+        a = {k: np.empty(shapes[k][0], shapes[k][1]) for k in keys}
+        _lib().orc_graph_arrays(self._h, *[_p(a.get(k)) for k in ("off", "src", "tau", "perm", "w", "prob", "alias")])
         return a
 
     def sample_ids(self, seed, ids, retry_cap=1 << 24, members_cap=None, ris=False, bucket=False):

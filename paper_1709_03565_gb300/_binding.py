@@ -266,15 +266,18 @@ def skis_graph_get_info(g: Graph) -> dict:
     return {k: getattr(info, k) for k, _ in info._fields_}
 
 
-def skis_graph_export(g: Graph, stream=None) -> dict:
+_GRAPH_ARRAYS = ("off", "src", "tau", "perm", "w", "prob", "alias")
+
+
+def skis_graph_export(g: Graph, stream=None, keys=_GRAPH_ARRAYS) -> dict:
+    """The graph's arrays (those named in keys) as host numpy arrays."""
     info = skis_graph_get_info(g)
     n, m = info["n"], info["m"]
-    a = dict(off=np.empty(n + 1, np.int64), src=np.empty(m, np.int32), tau=np.empty(m, np.uint32),
-             perm=np.empty(m, np.int64), w=np.empty(n, np.uint64), prob=np.empty(n, np.uint64),
-             alias=np.empty(n, np.uint32))
-    P = lambda k: ctypes.c_void_p(a[k].ctypes.data)  # noqa: E731
-    _check(lib().skis_graph_export(g.ptr, P("off"), P("src"), P("tau"), P("perm"), P("w"), P("prob"),
-                                   P("alias"), _stream(stream)))
+    shapes = dict(off=(n + 1, np.int64), src=(m, np.int32), tau=(m, np.uint32), perm=(m, np.int64),
+                  w=(n, np.uint64), prob=(n, np.uint64), alias=(n, np.uint32))
+    a = {k: np.empty(shapes[k][0], shapes[k][1]) for k in keys}
+    P = lambda k: ctypes.c_void_p(a[k].ctypes.data) if k in a else None  # noqa: E731
+    _check(lib().skis_graph_export(g.ptr, *[P(k) for k in _GRAPH_ARRAYS], _stream(stream)))
     return a
 
 

@@ -16,6 +16,18 @@ def test_algorithmic_bytes_is_32T_68E_4C():
         assert bench.algorithmic_bytes(T, E, C, False) == 32 * T + 68 * E
 
 
+def test_step_ids_partition_the_id_stream():
+    # step i on rank r of N: block i N + r; blocks are disjoint and consecutive
+    for world in (1, 2, 3, 8):
+        firsts = [bench.step_first_id(i, r, world, 1000) for i in range(4) for r in range(world)]
+        assert firsts == [1000 * b for b in range(4 * world)]
+
+
+def test_alu_peak_derivation():
+    # 152 SMs x 64 multiply-adds per clock / 40 per Philox block x 2.07 GHz
+    assert abs(bench.alu_peak_blocks_per_s(152, 2070.0) - 503.424e9) < 1e3
+
+
 def _fake_root(tmp_path, src: bytes, record: dict):
     os.makedirs(tmp_path / "profiles")
     os.makedirs(tmp_path / "paper_1709_03565_gb300" / "csrc")
@@ -26,7 +38,7 @@ def _fake_root(tmp_path, src: bytes, record: dict):
 def test_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
     src = b"// sampler source\n"
     record = {"sample_cu_sha256": hashlib.sha256(src).hexdigest(), "first_step": "bucket",
-              "dram_bytes_per_sample": 497.5}
+              "dram_bytes_per_sample": 497.5, "workload_key": bench.C2_WORKLOAD}
     _fake_root(tmp_path, src, record)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench._traffic_per_sample("bucket") == 497.5

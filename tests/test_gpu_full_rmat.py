@@ -1,0 +1,110 @@
+"""Full-size parity on the benchmark workload: the R-MAT graph with 2^25
+vertices and 2^30 edges (a, b, c, d = 0.57, 0.19, 0.19, 0.05, seed 3),
+weighted cascade, loaded by the library and by the oracle.
+
+- Graph structures (Sec. II-A canonical in-CSR, Eq. gamma_v, Eq. probu):
+  offsets, CSR sources, thresholds, the CSR -> input permutation, w, the
+  alias table, W and f, all bit-exact. The CSR source array is 4 GiB, the
+  permutation 4 GiB and, for the bucket form, the per-edge gamma chain 8 GiB
+  on the device, so device offsets past 2^32 bytes are read.
+- Samples (Alg. 1) through the tier split the benchmark's autotuner picks,
+  in both forms of the first step: ids [0, 400) and blocks of 4 ids at
+  every 2,000,000th id of the 10^8-id stream (and, bucket form, all of ids
+  [0, 1000) below), each sample's (src, retries, |R|, coins, member set)
+  bit-exact.
+- Greedy max-coverage (Alg. 3, k = 50) and 64 queries (Eq. 21) on the
+  sketch of ids [0, 1000): seeds and coverages bit-exact, estimates to a
+  relative 1e-12."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1709_03565_gb300 as skis
+import synth
+
+from test_gpu_parity import REL, assert_samples_equal
+
+pytestmark = pytest.mark.gpu
+SEED = 0x5EED0003  # the benchmark's sketch seed
+PREFIX = 1000
+BLOCK, STRIDE, NBLOCKS = 4, 2_000_000, 49
+
+
+@pytest.fixture(scope="module")
+def rmat():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    skis.build()
+    spec, src, dst, _ = synth.workload("rmat-2^25-wc")
+    g = skis.skis_load_graph(spec["n"], src, dst, None, skis.SKIS_W_WC)  # host arrays, copied by the library
+    o = oracle.OracleGraph(spec["n"], src, dst, model=oracle.W_WC)
+    del src, dst
+    # the tier split the benchmark's autotuner picks on this graph
+    s = skis.skis_sketch_create(g, SEED)
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, 1)
+    tune = skis.skis_sketch_autotune(s, 20_000)
+    s.close()
+    split = ((skis.SKIS_OPT_THREAD_MAX_DEG, tune["max_deg"]), (skis.SKIS_OPT_THREAD_MAX_STEPS, tune["max_steps"]),
+             (skis.SKIS_OPT_WARP_MAX_COINS, tune["warp_max_coins"]))
+    yield spec, g, o, split
+    g.close()
+
+
+def _sketch(g, split, bucket, first, count):
+    s = skis.skis_sketch_create(g, SEED)
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, 1 if bucket else 0)
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_ID, first)
+    for opt, val in split:
+        skis.skis_sketch_set_option(s, opt, val)
+    skis.skis_sample(s, count)
+    return s
+
+
+def test_full_rmat_graph_structures(rmat):
+    spec, g, o, split = rmat
+    info = skis.skis_graph_get_info(g)
+    assert (info["n"], info["m"]) == (1 << 25, 1 << 30)
+    assert info["W"] == o.W and info["f"] == o.f and info["row_uniform_tau"] == 1
+    for k in ("off", "src", "tau", "perm", "w", "prob", "alias"):  # one array at a time (up to 8 GiB each)
+        a, b = skis.skis_graph_export(g, keys=(k,))[k], o.arrays(keys=(k,))[k]
+        assert a.shape == b.shape and np.array_equal(a, b), k
+        del a, b
+
+
+@pytest.mark.parametrize("bucket", [True, False])
+def test_full_rmat_samples_on_id_subset(rmat, bucket):
+    spec, g, o, split = rmat
+    ranges = [(0, 400)] + [(i * STRIDE, BLOCK) for i in range(1, NBLOCKS + 1)]
+    retried = 0
+    for first, count in ranges:
+        s = _sketch(g, split, bucket, first, count)
+        dev = skis.skis_sketch_export(s, first, count)
+        ora = o.sample_ids(SEED, np.arange(first, first + count, dtype=np.uint64), bucket=bucket)
+        assert_samples_equal(dev, ora)
+        retried += int((ora["retries"] > 0).sum())
+        s.close()
+    assert (retried > 0) != bucket  # rejection rounds happen in the rejection form only
+    assert ranges[-1][0] + BLOCK <= 100_000_000  # every block lies in the benchmark's id stream
+
+
+def test_full_rmat_greedy_and_queries(rmat):
+    spec, g, o, split = rmat
+    s = _sketch(g, split, True, 0, PREFIX)
+    st = skis.skis_sketch_stats(s)
+    assert st["deferred"] > 0  # the CTA tier (hub rows) took part
+    osk = oracle.OracleSketch(o, SEED, PREFIX, bucket=True)
+    a = osk.arrays()
+    dev = skis.skis_sketch_export(s, 0, PREFIX)
+    assert_samples_equal(dev, dict(src=a["src"], retries=a["retries"], len=np.diff(a["off"]), coins=a["coins"],
+                                   member_off=a["off"], members=a["mem"]))
+    sd, sc, se = skis.skis_greedy_maxcover(s, 50)
+    od, oc, oe = osk.greedy(50)
+    assert np.array_equal(sd, od) and np.array_equal(sc, oc)
+    np.testing.assert_allclose(se, oe, rtol=REL, atol=0)
+    off, seeds = synth.seed_sets(spec["n"], [10] * 64, 13)
+    cov, est = skis.skis_estimate(s, off, seeds)
+    ocov, oest = osk.coverage(off, seeds)
+    assert np.array_equal(cov, ocov)
+    np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
+    s.close()
