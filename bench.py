@@ -660,6 +660,23 @@ def main():
     stream = torch.cuda.current_stream(dev)
     peak, peak_kind = _peaks()
 
+    if args.workload == C2_WORKLOAD and args.profile_step:  # one Chung-Lu step (the command profiled with ncu)
+        import synth
+
+        spec, src, dst, p = synth.workload(C2_WORKLOAD)
+        d_src, d_dst, d_p = (torch.from_numpy(x).to(dev) for x in (src, dst, p))
+        q_off, q_seeds = synth.seed_sets(spec["n"], [QUERY_SIZE] * QUERIES, 11)
+        g = skis.skis_load_graph(spec["n"], d_src, d_dst, d_p, skis.SKIS_W_EXPLICIT_P, stream=stream)
+        s = skis.skis_sketch_create(g, C2_SEED, int(spec["samples"] * 5.5), stream=stream)
+        skis.skis_sketch_set_option(s, skis.SKIS_OPT_FIRST_STEP, 1 if bucket else 0)
+        skis.skis_sample(s, spec["samples"], stream=stream)
+        skis.skis_greedy_maxcover(s, spec["k"], stream=stream)
+        skis.skis_estimate(s, q_off, q_seeds, stream=stream)
+        st = skis.skis_sketch_stats(s)
+        print(json.dumps({"profile_step": C2_WORKLOAD, "samples": spec["samples"], "entries": st["entries"],
+                          "coins": st["coins"], "sample_ms": st["last_sample_ms"],
+                          "launches": skis.skis_kernel_launches()}))
+        return
     if args.workload == C2_WORKLOAD:  # the Chung-Lu step loop as its own line
         line = chunglu_line(skis, torch, dev, stream, args, peak)
         line.update({"metric": METRIC, "n_gpus": 1, "higher_is_better": True, "dtype": "u32", "data": "synthetic"})

@@ -67,3 +67,7 @@ def test_profile_summaries_name_commands_on_committed_files():
         for c in cmds:
             assert "--clock-control none" in c, f
             assert " python bench.py" in c and "_work" not in c, f
+            if "--set" in c or "--section" in c:  # full captures: one kernel, a few launches
+                k = c.split(" -k ", 1)[1].split()[0] if " -k " in c else ""
+                assert k and "|" not in k, f
+                assert " -c " in c and int(c.split(" -c ", 1)[1].split()[0]) <= 3, f
