@@ -114,7 +114,7 @@ typedef struct skis_stats {
  * never change the samples. */
 typedef enum skis_option {
     SKIS_OPT_RETRY_CAP = 0,      /* cap on rejected first-step rounds (default 2^24) */
-    SKIS_OPT_CTA_SLOTS = 1,      /* CTAs of the CTA tier (default 2 per SM) */
+    SKIS_OPT_CTA_SLOTS = 1,      /* CTAs of the CTA tier (default: 1024 threads of them per SM) */
     SKIS_OPT_WARP_BLOCKS = 2,    /* CTAs of the warp tier (default: full occupancy) */
     SKIS_OPT_THREAD_MAX_DEG = 3, /* longest in-row the thread tier expands (default 192; 0 = tier off) */
     SKIS_OPT_THREAD_BLOCKS = 4,  /* CTAs of the thread tier (default: full occupancy) */
@@ -153,8 +153,8 @@ typedef enum skis_option {
     SKIS_OPT_CTA_QUEUE_CAP = 13,   /* member queue entries of a CTA-tier slot (default 2^20, at most n;
                                       in [32, 2^31]): a sample with more members moves to a second
                                       pass over fewer slots with n-entry queues */
-    SKIS_OPT_CTA_THREADS = 14      /* threads of a CTA-tier block: 512 (default; two per SM) or 256
-                                      (four per SM) */
+    SKIS_OPT_CTA_THREADS = 14      /* threads of a CTA-tier block: 256 (default; four per SM) or 512
+                                      (two per SM) */
 } skis_option;
 
 /* Load G = (V, E, w) (Sec. II-A) and build the device structures every later

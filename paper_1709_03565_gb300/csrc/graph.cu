@@ -53,9 +53,17 @@ __global__ void k_make_keys(const int32_t* __restrict__ src, const int32_t* __re
     }
 }
 
-__global__ void k_degree(const int32_t* __restrict__ dst, int64_t m, uint32_t* __restrict__ cnt) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[dst[e]], 1u);
+// Row offsets of the canonical CSR from the sorted keys: off[v] is the first
+// position whose destination is >= v. Position e writes off[v] for the
+// destinations v in (dst(e - 1), dst(e)], and the last position the ones
+// after its destination, so every entry of off[0 .. n] is written once.
+__global__ void k_offsets_from_keys(const uint64_t* __restrict__ keys, int64_t m, int64_t n, int src_bits,
+                                    uint64_t* __restrict__ off) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t prev = e > 0 ? (int64_t)(keys[e - 1] >> src_bits) : -1;
+        const int64_t cur = e < m ? (int64_t)(keys[e] >> src_bits) : n;
+        for (int64_t v = prev + 1; v <= cur; ++v) off[v] = (uint64_t)e;
+    }
 }
 
 // CSR arrays from the sorted pairs; per-edge thresholds by model. Padding
@@ -103,6 +111,18 @@ __global__ void k_rows(const uint64_t* __restrict__ off, int64_t n, int wc, RowI
 // Eq. gamma_v in fixed point: Q = 2^62; Q <- floor(Q (2^32 - tau) / 2^32) for
 // each in-edge in CSR order (0 on a sentinel); w_v = (2^62 - Q) >> s. With
 // chain != nullptr the running Q after every in-edge is kept as well.
+// One step of the fixed-point chain, Q <- floor(Q (2^32 - t) / 2^32) for
+// Q < 2^62 (0 for the sentinel). With Q = qh 2^32 + ql and c = 2^32 - t,
+// the floor is exactly qh c + floor(ql c / 2^32): two independent 32-bit
+// products (qh < 2^30, so qh c < 2^62) instead of a 128-bit one, which
+// shortens the dependent chain a long row walks edge by edge.
+__device__ __forceinline__ uint64_t chain_step(uint64_t Q, uint32_t t) {
+    if (t == kSentinel) return 0;
+    if (t == 0) return Q;  // c = 2^32
+    const uint32_t c = (uint32_t)(0x100000000ull - t);
+    return (uint64_t)(uint32_t)(Q >> 32) * c + __umulhi((uint32_t)Q, c);
+}
+
 __global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __restrict__ csr_tau, int64_t n, int s,
                         uint64_t* __restrict__ w, uint64_t* __restrict__ chain) {
     const uint64_t one62 = 1ull << 62;
@@ -110,22 +130,26 @@ __global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __rest
         const RowInfo r = rows[v];
         uint64_t Q = one62;
         uint32_t k = 0;
-        for (; k + 8 <= r.deg && (Q != 0 || chain); k += 8) {
-            uint32_t t[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) t[i] = csr_tau ? csr_tau[r.off + k + i] : r.tau;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (t[i] == kSentinel) Q = 0;
-                else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t[i])) >> 32);
-                if (chain) chain[r.off + k + i] = Q;
+        if (!csr_tau) {  // one threshold for the row (weighted cascade)
+            for (; k < r.deg && (Q != 0 || chain); ++k) {
+                Q = chain_step(Q, r.tau);
+                if (chain) chain[r.off + k] = Q;
             }
-        }
-        for (; k < r.deg && (Q != 0 || chain); ++k) {
-            const uint32_t t = csr_tau ? csr_tau[r.off + k] : r.tau;
-            if (t == kSentinel) Q = 0;
-            else Q = (uint64_t)(((u128)Q * (u128)((1ull << 32) - t)) >> 32);
-            if (chain) chain[r.off + k] = Q;
+        } else {
+            for (; k + 8 <= r.deg && (Q != 0 || chain); k += 8) {
+                uint32_t t[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) t[i] = csr_tau[r.off + k + i];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    Q = chain_step(Q, t[i]);
+                    if (chain) chain[r.off + k + i] = Q;
+                }
+            }
+            for (; k < r.deg && (Q != 0 || chain); ++k) {
+                Q = chain_step(Q, csr_tau[r.off + k]);
+                if (chain) chain[r.off + k] = Q;
+            }
         }
         w[v] = (one62 - Q) >> s;
     }
@@ -295,7 +319,7 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     DevStatus* d_status = nullptr;
     unsigned long long* d_W = nullptr;
     uint64_t *keys = nullptr, *keys_s = nullptr, *keys_alt = nullptr;
-    uint32_t *vals = nullptr, *vals_s = nullptr, *vals_alt = nullptr, *cnt = nullptr;
+    uint32_t *vals = nullptr, *vals_s = nullptr, *vals_alt = nullptr;
     uint32_t *is_light = nullptr, *light_ids = nullptr, *heavy_ids = nullptr;
     uint64_t* light_idx = nullptr;
     u128 *deficit = nullptr, *excess = nullptr, *D = nullptr, *Ex = nullptr;
@@ -337,8 +361,6 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     if (!g->row_uniform) GB_CUDA(dev_alloc_t(&g->tau, (size_t)g->m_pad, st));
     GB_CUDA(dev_alloc_t(&g->w, (size_t)n, st));
     GB_CUDA(dev_alloc_t(&g->alias, (size_t)n, st));
-    GB_CUDA(dev_alloc_t(&cnt, (size_t)n, st));
-    GB_CUDA(cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(uint32_t), st));
     if (m > 0) {
         GB_CUDA(dev_alloc_t(&keys, (size_t)m, st));
         GB_CUDA(dev_alloc_t(&keys_s, (size_t)m, st));
@@ -349,10 +371,9 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
         k_make_keys<<<grid, block, 0, st>>>(d_src, d_dst, m, src_bits, keys, vals); note_launch();
         GB_CUDA(cudaGetLastError());
         GB_CUDA(radix_sort_pairs(keys, vals, keys_s, vals_s, keys_alt, vals_alt, m, key_bits, st));
-        k_degree<<<grid, block, 0, st>>>(d_dst, m, cnt); note_launch();
-        GB_CUDA(cudaGetLastError());
     }
-    GB_CUDA(scan_u32_to_u64(cnt, g->off, n, st));
+    k_offsets_from_keys<<<grid, block, 0, st>>>(keys_s, m, n, src_bits, g->off); note_launch();
+    GB_CUDA(cudaGetLastError());
     k_gather_edges<<<grid, block, 0, st>>>(keys_s, vals_s, m, g->m_pad, src_bits, model, d_weights, weight_seed,
                                            g->src, g->tau, g->perm); note_launch();
     GB_CUDA(cudaGetLastError());
@@ -430,7 +451,6 @@ cleanup:
     dev_free(vals, st);
     dev_free(vals_s, st);
     dev_free(vals_alt, st);
-    dev_free(cnt, st);
     dev_free(is_light, st);
     dev_free(light_idx, st);
     dev_free(light_ids, st);

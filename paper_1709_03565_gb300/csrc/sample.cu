@@ -815,7 +815,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
 
 // -------------------------------------------------------------- CTA tier
 // One block of kCtaThreads threads per sample, 1024 threads of such blocks per
-// SM (two of 512 or four of 256: the option SKIS_OPT_CTA_THREADS).
+// SM (four of 256 by default, or two of 512: the option SKIS_OPT_CTA_THREADS).
 template <int kCtaThreads>
 __global__ void __launch_bounds__(kCtaThreads, 1024 / kCtaThreads) k_iis_cta(SampleArgs a) {
     constexpr int kCtaWin = 2 * kCtaThreads;  // queued vertices per load-balanced window
@@ -1036,32 +1036,53 @@ __global__ void __launch_bounds__(kCtaThreads, 1024 / kCtaThreads) k_iis_cta(Sam
                 if (nhub) {
                     const SampleBlock blk(a.rk, j, kDomBfs);
                     const uint4* __restrict__ tau4 = reinterpret_cast<const uint4*>(a.tau);
+                    // the live coins of quad q (Philox block x) within [lo, hi) join the sample
+                    auto take = [&](uint32_t q, const uint4& x, const uint4& t4, uint32_t lo, uint32_t hi) {
+                        const uint32_t e0 = q << 2;
+                        unsigned l4 = 0;
+                        l4 |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
+                        l4 |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
+                        l4 |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
+                        l4 |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
+                        if (l4) {
+                            const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
+                            if (l4 & 1u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.x);
+                            if (l4 & 2u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.y);
+                            if (l4 & 4u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.z);
+                            if (l4 & 8u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.w);
+                        }
+                    };
+                    auto min4 = [](const uint4& x) { return min(min(x.x, x.y), min(x.z, x.w)); };
                     uint32_t g = threadIdx.x;
                     for (uint32_t h = 0; h < nhub; ++h) {
                         const uint32_t i = s_hub[h];
                         const uint32_t lo = s_lo[i], hi = s_hi[i], tr = s_tau[i];
                         const uint32_t qf = lo >> 2, nq = ((hi - 1) >> 2) - qf + 1;
-                        for (; g < nq; g += kCtaThreads) {
-                            const uint32_t q = qf + g;
-                            const uint4 x = blk(q, a.rk);
-                            const uint4 t4 = tau4 ? __ldg(tau4 + q) : make_uint4(tr, tr, tr, tr);
-                            const bool maybe = tau4 ? coin_live(x.x, t4.x) | coin_live(x.y, t4.y) |
-                                                          coin_live(x.z, t4.z) | coin_live(x.w, t4.w)
-                                                    : (min(min(x.x, x.y), min(x.z, x.w)) < tr) | (tr == kSentinel);
-                            if (maybe) {
-                                const uint32_t e0 = q << 2;
-                                unsigned l4 = 0;
-                                l4 |= (e0 + 0 >= lo && e0 + 0 < hi && coin_live(x.x, t4.x)) ? 1u : 0u;
-                                l4 |= (e0 + 1 >= lo && e0 + 1 < hi && coin_live(x.y, t4.y)) ? 2u : 0u;
-                                l4 |= (e0 + 2 >= lo && e0 + 2 < hi && coin_live(x.z, t4.z)) ? 4u : 0u;
-                                l4 |= (e0 + 3 >= lo && e0 + 3 < hi && coin_live(x.w, t4.w)) ? 8u : 0u;
-                                if (l4) {
-                                    const int4 s4 = __ldg(reinterpret_cast<const int4*>(a.src) + q);
-                                    if (l4 & 1u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.x);
-                                    if (l4 & 2u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.y);
-                                    if (l4 & 4u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.z);
-                                    if (l4 & 8u) cta_insert_one(bitmap, queue, &s_qlen, a.queue_cap, s4.w);
+                        if (!tau4) {
+                            // one threshold for the row (never the sentinel: a hub row has many
+                            // edges): two independent blocks a step, one compare of their minimum
+                            const uint4 tr4 = make_uint4(tr, tr, tr, tr);
+                            for (; g + kCtaThreads < nq; g += 2 * kCtaThreads) {
+                                const uint32_t q0 = qf + g, q1 = q0 + kCtaThreads;
+                                const uint4 x0 = blk(q0, a.rk), x1 = blk(q1, a.rk);
+                                if (min(min4(x0), min4(x1)) < tr || tr == kSentinel) {
+                                    take(q0, x0, tr4, lo, hi);
+                                    take(q1, x1, tr4, lo, hi);
                                 }
+                            }
+                            for (; g < nq; g += kCtaThreads) {
+                                const uint32_t q = qf + g;
+                                const uint4 x = blk(q, a.rk);
+                                if (min4(x) < tr || tr == kSentinel) take(q, x, tr4, lo, hi);
+                            }
+                        } else {
+                            for (; g < nq; g += kCtaThreads) {
+                                const uint32_t q = qf + g;
+                                const uint4 x = blk(q, a.rk);
+                                const uint4 t4 = __ldg(tau4 + q);
+                                if (coin_live(x.x, t4.x) | coin_live(x.y, t4.y) | coin_live(x.z, t4.z) |
+                                    coin_live(x.w, t4.w))
+                                    take(q, x, t4, lo, hi);
                             }
                         }
                         g -= nq;
@@ -1682,8 +1703,8 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
             k_iis_warp<<<warp_blocks, kWarpThreads, 0, st>>>(aw); note_launch();
             SK_CUDA(cudaGetLastError());
             SK_CUDA(cudaEventRecord(s->ev[2], st));
-            if (s->cta_threads == 256) k_iis_cta<256><<<s->cta_slots_alloc, 256, 0, st>>>(ac);
-            else k_iis_cta<512><<<s->cta_slots_alloc, 512, 0, st>>>(ac);
+            if (s->cta_threads == 512) k_iis_cta<512><<<s->cta_slots_alloc, 512, 0, st>>>(ac);
+            else k_iis_cta<256><<<s->cta_slots_alloc, 256, 0, st>>>(ac);
             note_launch();
             SK_CUDA(cudaGetLastError());
             SK_CUDA(cudaEventRecord(s->ev[3], st));
@@ -1710,8 +1731,8 @@ int sketch_sample(skis_sketch* s, uint64_t count, cudaStream_t st, std::string* 
             if (g->lt) {
                 k_lt_long<<<s->big_slots, 32, 0, st>>>(ab); note_launch();
             } else {
-                if (s->cta_threads == 256) k_iis_cta<256><<<s->big_slots, 256, 0, st>>>(ab);
-                else k_iis_cta<512><<<s->big_slots, 512, 0, st>>>(ab);
+                if (s->cta_threads == 512) k_iis_cta<512><<<s->big_slots, 512, 0, st>>>(ab);
+                else k_iis_cta<256><<<s->big_slots, 256, 0, st>>>(ab);
                 note_launch();
             }
             SK_CUDA(cudaGetLastError());

@@ -306,7 +306,7 @@ struct skis_sketch {
     int32_t* queues = nullptr;           // CTA tier: one queue_cap-entry queue per slot
     uint32_t queue_cap = 0;              // entries of each slot's queue: min(n, cta_queue_cap)
     uint32_t cta_queue_cap = 1u << 20;   // option: queue entries per CTA-tier slot
-    int cta_threads = 512;               // option: threads of a CTA-tier block (256 or 512)
+    int cta_threads = 256;               // option: threads of a CTA-tier block (256 or 512)
     uint64_t* big_ids = nullptr;         // CTA tier -> the pass with n-entry queues
     int32_t* big_queues = nullptr;       // that pass's queues (n entries each), allocated on first use
     int big_slots = 0;
