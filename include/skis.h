@@ -22,6 +22,10 @@
  *     host (statuses, counts, host outputs) synchronise that stream.
  *     skis_graph_free / skis_sketch_free release memory on the stream of the
  *     handle's last call, which must still exist.
+ *   - Member layout: the first sketch scan of skis_estimate after new
+ *     samples moves their members into sample-id order in the sketch's
+ *     storage. Only the layout changes, never a sample; do not overlap such a
+ *     call with other work on the same sketch (a server included).
  *   - Memory spaces: where a call takes SKIS_MEM_HOST or SKIS_MEM_DEVICE,
  *     the pointers it names are host or device pointers accordingly.
  *   - Determinism: sample j of a sketch is a pure function of (graph, seed,
@@ -104,6 +108,8 @@ typedef struct skis_stats {
     uint64_t warp_max_coins;
     uint64_t cta_hub_quads;
     uint64_t first_id;       /* sample id of the sketch's first sample (SKIS_OPT_FIRST_ID) */
+    double last_query_ms;    /* device time of the coverage launches of the last skis_estimate of at most
+                                64 queries (scan or inverted-index walk) */
 } skis_stats;
 
 /* Sampling runs in three tiers chained by sample id: one lane per sample

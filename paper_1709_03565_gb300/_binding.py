@@ -46,7 +46,7 @@ class skis_stats(ctypes.Structure):
                 ("last_sample_ms", ctypes.c_double), ("last_passes", ctypes.c_uint64),
                 ("thread_max_deg", ctypes.c_uint64), ("thread_max_steps", ctypes.c_uint64),
                 ("warp_max_coins", ctypes.c_uint64), ("cta_hub_quads", ctypes.c_uint64),
-                ("first_id", ctypes.c_uint64)]
+                ("first_id", ctypes.c_uint64), ("last_query_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

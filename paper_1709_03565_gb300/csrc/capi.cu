@@ -460,6 +460,7 @@ extern "C" int skis_sketch_stats(const skis_sketch* s, skis_stats* out) {
     out->warp_max_coins = s->warp_max_coins;
     out->cta_hub_quads = s->cta_hub_quads;
     out->first_id = s->id_base;
+    out->last_query_ms = s->last_query_ms;
     if (s->T == 0) return SKIS_OK;
     cudaStream_t st = s->stream;
     unsigned long long* d = nullptr;
@@ -574,6 +575,11 @@ void skis::sketch_release(skis_sketch* s) {
     dev_free(s->vcount, st);
     dev_free(s->qcov, st);
     dev_free(s->qstatus, st);
+    dev_free(s->touched, st);
+    dev_free(s->ntouched, st);
+    dev_free(s->hits, st);
+    for (int i = 0; i < 2; ++i)
+        if (s->qev[i]) cudaEventDestroy(s->qev[i]);
     for (int i = 0; i < 4; ++i)
         if (s->ev[i]) cudaEventDestroy(s->ev[i]);
 }

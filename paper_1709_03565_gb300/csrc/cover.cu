@@ -109,9 +109,21 @@ __device__ __forceinline__ void sub_merged(uint32_t* counter, int32_t u, uint32_
 }
 
 // ------------------------------------------------------------- coverage
-// qbits (nullable): one bit per vertex, set for the batch's seeds, so that
-// the sketch scan gathers a vertex's 8-byte mask only when the vertex is a
-// seed (the bit array is small enough to stay in L1 and L2).
+// qbits (nullable): a filter of the batch's seeds, one bit per vertex for
+// graphs of at most 2^20 vertices, else 2^20 bits indexed by a multiplicative
+// hash, so that the sketch scan gathers a vertex's 8-byte mask only when the
+// vertex may be a seed (false positives have an all-zero mask). At most
+// 128 KiB: it fits in one block's shared memory.
+constexpr int kFilterLog2 = 20;
+constexpr uint32_t kFilterMaxWords = 1u << (kFilterLog2 - 5);
+
+__host__ __device__ __forceinline__ uint32_t filter_words(int64_t n) {  // n in [1, 2^31]
+    return n > ((int64_t)1 << kFilterLog2) ? kFilterMaxWords : (uint32_t)((n + 31) / 32);
+}
+
+__device__ __forceinline__ uint32_t filter_index(uint32_t v, int hashed) {
+    return hashed ? (v * 2654435761u) >> (32 - kFilterLog2) : v;
+}
 __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
                             int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits,
                             DevStatus* st) {
@@ -128,7 +140,10 @@ __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __re
         const int32_t v = seeds[i];
         bool bad = v < 0 || v >= n;
         if (!bad) bad = (atomicOr((unsigned long long*)&qmask[v], (unsigned long long)bit) & bit) != 0;
-        if (!bad && qbits) atomicOr(&qbits[v >> 5], 1u << (v & 31));
+        if (!bad && qbits) {
+            const uint32_t f = filter_index((uint32_t)v, n > ((int64_t)1 << kFilterLog2));
+            atomicOr(&qbits[f >> 5], 1u << (f & 31));
+        }
         if (bad) {
             atomicOr(&st->flags, kStInval);
             atomicMin(&st->first_bad, (unsigned long long)b);
@@ -137,15 +152,18 @@ __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __re
 }
 
 __global__ void k_qmask_clear(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
-                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits) {
+                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits,
+                              unsigned long long* __restrict__ reset2) {
     const int lane = threadIdx.x & 31;
+    if (reset2 && blockIdx.x == 0 && threadIdx.x < 3) reset2[threadIdx.x] = 0;  // the ordered scan's counters
     const int32_t b = q0 + (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (b >= q0 + qn) return;
     for (int64_t i = off[b] + lane; i < off[b + 1]; i += 32) {
         const int32_t v = seeds[i];
         if (v >= 0 && v < n) {
             qmask[v] = 0;
-            if (qbits) qbits[v >> 5] = 0;  // every bit set in the array is a seed of this batch
+            // every bit set in the filter belongs to a seed of this batch
+            if (qbits) qbits[filter_index((uint32_t)v, n > ((int64_t)1 << kFilterLog2)) >> 5] = 0;
         }
     }
 }
@@ -154,7 +172,7 @@ __global__ void __launch_bounds__(kCovThreads) k_coverage(const uint64_t* __rest
                                                           const uint32_t* __restrict__ h_len, uint64_t T,
                                                           const int32_t* __restrict__ arena,
                                                           const uint64_t* __restrict__ qmask,
-                                                          const uint32_t* __restrict__ qbits,
+                                                          const uint32_t* __restrict__ qbits, int hashed,
                                                           unsigned long long* __restrict__ cov) {
     __shared__ unsigned long long s_acc[kCovThreads / 32][32];
     __shared__ unsigned long long s_cnt[64];
@@ -173,7 +191,10 @@ __global__ void __launch_bounds__(kCovThreads) k_coverage(const uint64_t* __rest
         __syncwarp();
         unsigned long long* acc_row = s_acc[wib];
         warp_members(off, len, arena, [&](int owner, int32_t u) {
-            if (qbits && !((__ldg(qbits + (u >> 5)) >> (u & 31)) & 1u)) return;  // not a seed
+            if (qbits) {  // not a seed
+                const uint32_t f = filter_index((uint32_t)u, hashed);
+                if (!((__ldg(qbits + (f >> 5)) >> (f & 31)) & 1u)) return;
+            }
             const uint64_t msk = qmask[u];
             if (msk) atomicOr(&acc_row[owner], (unsigned long long)msk);
         });
@@ -196,6 +217,150 @@ __global__ void __launch_bounds__(kCovThreads) k_coverage(const uint64_t* __rest
     if (c_hi) atomicAdd(&s_cnt[lane + 32], c_hi);
     __syncthreads();
     if (threadIdx.x < 64 && s_cnt[threadIdx.x]) atomicAdd(&cov[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+// The scan of a sketch whose members are in sample-id order (arena
+// positions [h_off[0], ...) contiguous): the seed filter sits in shared
+// memory; a warp takes 1024 consecutive samples at a time (from an atomic
+// cursor, so that warps meeting large samples or many seeds take fewer), whose
+// members are one run, and streams it as 16-byte vectors testing each member
+// against the filter. Only a member that is a seed (rare) looks up its
+// sample, by a binary search over the task's 1024 offsets, and ORs its query
+// mask into the sample's
+// word of smask; the first setter of a (sample, query) bit counts it, and the
+// first setter of a sample's word lists the sample for the reset.
+constexpr int kScanThreads = 1024;
+
+// Asynchronous bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned,
+// bytes a multiple of 16): no register waits for it.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+constexpr uint32_t kScanSamples = 1024;
+constexpr int kScanUnroll = 4;
+constexpr uint64_t kScanAhead = 4;  // warp steps prefetched ahead
+constexpr unsigned long long kHitCap = 1ull << 22;  // hits listed per query chunk (32 MiB); more are resolved in the scan
+
+__global__ void __launch_bounds__(kScanThreads, 1) k_scan_ordered(
+    const uint64_t* __restrict__ h_off, const uint32_t* __restrict__ h_len, uint64_t T,
+    const int32_t* __restrict__ arena, const uint32_t* __restrict__ qbits, uint32_t fwords, int hashed,
+    const uint64_t* __restrict__ qmask, unsigned long long* __restrict__ smask, uint32_t* __restrict__ touched,
+    unsigned long long* __restrict__ ntouched, unsigned long long* __restrict__ cursor,
+    unsigned long long* __restrict__ hits, unsigned long long* __restrict__ nhits, unsigned long long hit_cap,
+    unsigned long long* __restrict__ cov) {
+    extern __shared__ uint32_t s_f[];
+    __shared__ unsigned int s_cnt[64];
+    for (uint32_t i = threadIdx.x; i < fwords; i += blockDim.x) s_f[i] = qbits[i];
+    if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint64_t ntask = (T + kScanSamples - 1) / kScanSamples;
+    unsigned long long claim = 0;
+    if (lane == 0) claim = atomicAdd(cursor, 1ull);
+    for (;;) {
+        const unsigned long long task = __shfl_sync(kFull, claim, 0);
+        if (task >= ntask) break;
+        if (lane == 0) claim = atomicAdd(cursor, 1ull);  // the next task, claimed while this one streams
+        const uint64_t j0 = task * kScanSamples, j1 = min(T, j0 + kScanSamples);
+        const uint64_t p0 = h_off[j0], p1 = h_off[j1 - 1] + h_len[j1 - 1];
+        auto member = [&](uint64_t pos, int32_t u) {
+            const uint32_t f = filter_index((uint32_t)u, hashed);
+            if (!((s_f[f >> 5] >> (f & 31)) & 1u)) return;
+            // a possible seed: its (task, position) goes to the hit list for
+            // k_scan_hits; only when the list is full is it resolved here
+            const unsigned long long slot = atomicAdd(nhits, 1ull);
+            if (slot < hit_cap) {
+                hits[slot] = ((unsigned long long)task << 40) | pos;
+                return;
+            }
+            const uint64_t msk = qmask[u];
+            if (!msk) return;  // a filter collision
+            uint64_t lo = j0, hi = j1 - 1;  // the last sample whose run starts at or before pos
+            while (lo < hi) {
+                const uint64_t mid = (lo + hi + 1) >> 1;
+                if (h_off[mid] <= pos) lo = mid;
+                else hi = mid - 1;
+            }
+            const unsigned long long old = atomicOr(smask + lo, (unsigned long long)msk);
+            if (old == 0) touched[atomicAdd(ntouched, 1ull)] = (uint32_t)lo;
+            for (uint64_t nb = msk & ~old; nb; nb &= nb - 1) atomicAdd(&s_cnt[__ffsll((long long)nb) - 1], 1u);
+        };
+        const uint64_t up = (p0 + 3) & ~(uint64_t)3, down = p1 & ~(uint64_t)3;
+        const uint64_t ph = p1 < up ? p1 : up, pt = down > ph ? down : ph;
+        if (p0 + lane < ph) member(p0 + lane, arena[p0 + lane]);
+        const int4* a4 = reinterpret_cast<const int4*>(arena);
+        const uint64_t v_end = pt / 4, v0 = ph / 4;
+        // the task's first steps, then each step the one kScanAhead steps on, are
+        // prefetched into L2 by one lane, so that the lanes' loads find them there
+        constexpr uint64_t kStep = 32 * kScanUnroll;  // 16-byte vectors a warp step loads
+        if (lane == 0 && v0 < v_end)
+            prefetch_l2(a4 + v0, (uint32_t)(min(v_end - v0, kStep * kScanAhead) * 16));
+        uint64_t v = v0 + lane;
+        // kScanUnroll 16-byte loads in flight a lane before any member is tested
+        // (the last step of a task predicated, not a step per load)
+        for (; v < v_end; v += 32 * kScanUnroll) {
+            const uint64_t ahead = (v - lane) + kStep * kScanAhead;
+            if (lane == 0 && ahead < v_end) prefetch_l2(a4 + ahead, (uint32_t)(min(v_end - ahead, kStep) * 16));
+            int4 m[kScanUnroll];
+#pragma unroll
+            for (int k = 0; k < kScanUnroll; ++k)
+                if (v + 32 * k < v_end) m[k] = __ldcs(a4 + v + 32 * k);
+#pragma unroll
+            for (int k = 0; k < kScanUnroll; ++k) {
+                if (v + 32 * k >= v_end) break;
+                const uint64_t pos = (v + 32 * k) * 4;
+                member(pos, m[k].x);
+                member(pos + 1, m[k].y);
+                member(pos + 2, m[k].z);
+                member(pos + 3, m[k].w);
+            }
+        }
+        if (pt + lane < p1) member(pt + lane, arena[pt + lane]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 64 && s_cnt[threadIdx.x]) atomicAdd(&cov[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+// The hits the scan listed: each (task, position) resolves to its member,
+// the member's query mask, and its sample by a binary search over the task's
+// offsets; the first setter of a (sample, query) bit counts it.
+__global__ void __launch_bounds__(256) k_scan_hits(const unsigned long long* __restrict__ hits,
+                                                   const unsigned long long* __restrict__ nhits,
+                                                   unsigned long long hit_cap, const uint64_t* __restrict__ h_off,
+                                                   uint64_t T, const int32_t* __restrict__ arena,
+                                                   const uint64_t* __restrict__ qmask,
+                                                   unsigned long long* __restrict__ smask,
+                                                   uint32_t* __restrict__ touched,
+                                                   unsigned long long* __restrict__ ntouched,
+                                                   unsigned long long* __restrict__ cov) {
+    __shared__ unsigned int s_cnt[64];
+    if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t cnt = min((uint64_t)*nhits, (uint64_t)hit_cap);
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long h = hits[k];
+        const uint64_t pos = h & ((1ull << 40) - 1), task = h >> 40;
+        const uint64_t msk = qmask[arena[pos]];
+        if (!msk) continue;  // a filter collision
+        uint64_t lo = task * kScanSamples, hi = min(T, lo + kScanSamples) - 1;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi + 1) >> 1;
+            if (h_off[mid] <= pos) lo = mid;
+            else hi = mid - 1;
+        }
+        const unsigned long long old = atomicOr(smask + lo, (unsigned long long)msk);
+        if (old == 0) touched[atomicAdd(ntouched, 1ull)] = (uint32_t)lo;
+        for (uint64_t nb = msk & ~old; nb; nb &= nb - 1) atomicAdd(&s_cnt[__ffsll((long long)nb) - 1], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 64 && s_cnt[threadIdx.x]) atomicAdd(&cov[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
+}
+
+__global__ void k_unmark(const uint32_t* __restrict__ touched, const unsigned long long* __restrict__ ntouched,
+                         unsigned long long* __restrict__ smask) {
+    const uint64_t cnt = *ntouched;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += (uint64_t)gridDim.x * blockDim.x)
+        smask[touched[k]] = 0;
 }
 
 // Eq. 21 with exact integers: N = Cov W + T sum_{v in S} (2^f - w_v),
@@ -322,6 +487,88 @@ cudaError_t coverage_by_index(const skis_sketch* s, const int64_t* off, const in
     return cudaGetLastError();
 }
 
+// Members of samples [0, cnt) (headers off/len) copied to out in sample
+// order at their exclusive prefix pre: a warp takes 32 consecutive samples
+// and spreads their members over its lanes, so the writes are one
+// contiguous run.
+__global__ void __launch_bounds__(kCovThreads) k_order_members(const uint64_t* __restrict__ off,
+                                                               const uint32_t* __restrict__ len, uint64_t cnt,
+                                                               const uint64_t* __restrict__ pre,
+                                                               const int32_t* __restrict__ arena,
+                                                               int32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (kCovThreads / 32);
+    for (uint64_t gi = ((uint64_t)blockIdx.x * kCovThreads + threadIdx.x) / 32; gi * 32 < cnt; gi += nwarps) {
+        const uint64_t j = gi * 32 + lane;
+        const uint64_t o = j < cnt ? off[j] : 0;
+        const uint32_t l = j < cnt ? len[j] : 0u;
+        uint32_t incl = l;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const uint32_t total = __shfl_sync(kFull, incl, 31), excl = incl - l;
+        const uint64_t dst0 = pre[gi * 32];
+        for (uint32_t base = 0; base < total; base += 32) {  // warp-uniform: every lane shuffles
+            const uint32_t p = base + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const uint32_t v = __shfl_sync(kFull, incl, owner + step - 1);
+                if (v <= p) owner += step;
+            }
+            const uint64_t oo = __shfl_sync(kFull, o, owner);
+            const uint32_t oe = __shfl_sync(kFull, excl, owner);
+            if (p < total) out[dst0 + p] = arena[oo + (p - oe)];
+        }
+    }
+}
+
+__global__ void k_rebase_offsets(uint64_t* __restrict__ off, const uint64_t* __restrict__ pre, uint64_t cnt,
+                                 uint64_t base) {
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += (uint64_t)gridDim.x * blockDim.x)
+        off[j] = base + pre[j];
+}
+
+int sketch_order_arena(skis_sketch* s, cudaStream_t st, std::string* err) {
+    const char* where = "member layout";
+    if (s->ordered_T == s->T) return SKIS_OK;
+    const uint64_t T0 = s->ordered_T, cnt = s->T - T0, E0 = s->ordered_E;
+    uint64_t* pre = nullptr;
+    int32_t* tmp = nullptr;
+    uint64_t E1 = 0;
+    auto body = [&]() -> int {
+        CV_CUDA(dev_alloc_t(&pre, (size_t)cnt + 1, st));
+        CV_CUDA(scan_u32_to_u64(s->h_len + T0, pre, (int64_t)cnt, st));
+        CV_CUDA(cudaMemcpyAsync(&E1, pre + cnt, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        CV_CUDA(cudaStreamSynchronize(st));
+        CV_CUDA(dev_alloc_t(&tmp, (size_t)std::max<uint64_t>(E1, 1), st));
+        const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sm_count() * 8,
+                                                                         (cnt + kCovThreads - 1) / kCovThreads));
+        k_order_members<<<blocks, kCovThreads, 0, st>>>(s->h_off + T0, s->h_len + T0, cnt, pre, s->arena, tmp);
+        note_launch();
+        CV_CUDA(cudaGetLastError());
+        if (E1) CV_CUDA(cudaMemcpyAsync(s->arena + E0, tmp, E1 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+        k_rebase_offsets<<<blocks, kCovThreads, 0, st>>>(s->h_off + T0, pre, cnt, E0); note_launch();
+        CV_CUDA(cudaGetLastError());
+        if (s->ctr) {  // later samples are appended right after the ordered ones
+            const unsigned long long cur = E0 + E1;
+            CV_CUDA(cudaMemcpyAsync(&s->ctr->arena, &cur, sizeof(cur), cudaMemcpyHostToDevice, st));
+        }
+        CV_CUDA(cudaStreamSynchronize(st));
+        return SKIS_OK;
+    };
+    const int rc = body();
+    dev_free(pre, st);
+    dev_free(tmp, st);
+    if (rc == SKIS_OK) {
+        s->ordered_T = s->T;
+        s->ordered_E = E0 + E1;
+    }
+    return rc;
+}
+
 int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32_t* d_seeds, const int64_t* h_off,
                     int64_t* d_cov, double* d_est, cudaStream_t st, std::string* err) {
     const char* where = "skis_estimate";
@@ -335,17 +582,38 @@ int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32
         if (rc != SKIS_OK) return rc;
     }
     const bool by_index = s->query_index != 2 && s->inv && s->inv_T == s->T;
+    // the scan streams the members in sample-id order (samples below 2^32)
+    const bool ordered_scan = !by_index && s->T < (1ull << 32);
+    if (ordered_scan) {
+        const int rc = sketch_order_arena(s, st, err);
+        if (rc != SKIS_OK) return rc;
+    }
+    const uint32_t fwords = filter_words(g->n);
+    const int hashed = g->n > ((int64_t)1 << kFilterLog2);
     if (!s->qmask) {
         CV_CUDA(dev_alloc_t(&s->qmask, (size_t)g->n, st));
         CV_CUDA(cudaMemsetAsync(s->qmask, 0, (size_t)g->n * sizeof(uint64_t), st));
-        CV_CUDA(dev_alloc_t(&s->qbits, (size_t)((g->n + 31) / 32), st));
-        CV_CUDA(cudaMemsetAsync(s->qbits, 0, (size_t)((g->n + 31) / 32) * sizeof(uint32_t), st));
+        CV_CUDA(dev_alloc_t(&s->qbits, (size_t)fwords, st));
+        CV_CUDA(cudaMemsetAsync(s->qbits, 0, (size_t)fwords * sizeof(uint32_t), st));
         CV_CUDA(dev_alloc_t(&s->qcov, 64, st));
         CV_CUDA(dev_alloc_t(&s->qstatus, 1, st));
+        CV_CUDA(cudaEventCreate(&s->qev[0]));
+        CV_CUDA(cudaEventCreate(&s->qev[1]));
     }
     uint32_t* chunk_cnt = nullptr;
     uint64_t* chunk_off = nullptr;
-    if (by_index) {
+    if (ordered_scan && s->touched_cap < s->T) {
+        dev_free(s->touched, st);
+        s->touched = nullptr;
+        CV_CUDA(dev_alloc_t(&s->touched, (size_t)s->T, st));
+        if (!s->ntouched) {  // list count, task cursor and hit count, zero between calls (k_qmask_clear resets them)
+            CV_CUDA(dev_alloc_t(&s->ntouched, 3, st));
+            CV_CUDA(cudaMemsetAsync(s->ntouched, 0, 3 * sizeof(unsigned long long), st));
+            CV_CUDA(dev_alloc_t(&s->hits, (size_t)kHitCap, st));
+        }
+        s->touched_cap = s->T;
+    }
+    if (by_index || ordered_scan) {
         if (s->smask_cap < s->T) {
             dev_free(s->smask, st);
             s->smask = nullptr;
@@ -353,33 +621,59 @@ int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32
             CV_CUDA(cudaMemsetAsync(s->smask, 0, (size_t)s->T * sizeof(uint64_t), st));
             s->smask_cap = s->T;
         }
+    }
+    if (by_index) {
         int64_t most = 1;
         for (int32_t q0 = 0; q0 < q; q0 += 64)
             most = std::max<int64_t>(most, h_off[std::min<int32_t>(q, q0 + 64)] - h_off[q0]);
         CV_CUDA(dev_alloc_t(&chunk_cnt, (size_t)most, st));
         CV_CUDA(dev_alloc_t(&chunk_off, (size_t)most + 1, st));
     }
+    if (ordered_scan)  // the filter takes up to 128 KiB of dynamic shared memory
+        CV_CUDA(cudaFuncSetAttribute(k_scan_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(kFilterMaxWords * sizeof(uint32_t))));
     CV_CUDA(cudaMemsetAsync(s->qstatus, 0, sizeof(DevStatus), st));
     CV_CUDA(cudaMemsetAsync(&s->qstatus->first_bad, 0xFF, sizeof(unsigned long long), st));
     const int cblocks = coverage_blocks(s->T);
+    float query_ms = 0;
     for (int32_t q0 = 0; q0 < q; q0 += 64) {
         const int32_t qn = std::min<int32_t>(64, q - q0);
         const int wb = div_up((int64_t)qn * 32, 256);
         CV_CUDA(cudaMemsetAsync(s->qcov, 0, 64 * sizeof(unsigned long long), st));
         k_qmask_set<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask, s->qbits, s->qstatus); note_launch();
         CV_CUDA(cudaGetLastError());
+        CV_CUDA(cudaEventRecord(s->qev[0], st));
         if (by_index) {
             CV_CUDA(coverage_by_index(s, d_off, d_seeds, q0, qn, h_off[q0], h_off[q0 + qn] - h_off[q0], chunk_cnt,
                                       chunk_off, s->smask, s->qcov, st));
+        } else if (ordered_scan) {
+            k_scan_ordered<<<sm_count(), kScanThreads, fwords * sizeof(uint32_t), st>>>(
+                s->h_off, s->h_len, s->T, s->arena, s->qbits, fwords, hashed, s->qmask,
+                reinterpret_cast<unsigned long long*>(s->smask), s->touched, s->ntouched, s->ntouched + 1, s->hits,
+                s->ntouched + 2, kHitCap, s->qcov);
+            note_launch();
+            CV_CUDA(cudaGetLastError());
+            k_scan_hits<<<sm_count() * 8, 256, 0, st>>>(s->hits, s->ntouched + 2, kHitCap, s->h_off, s->T, s->arena,
+                                                        s->qmask, reinterpret_cast<unsigned long long*>(s->smask),
+                                                        s->touched, s->ntouched, s->qcov);
+            note_launch();
+            CV_CUDA(cudaGetLastError());
+            k_unmark<<<sm_count() * 4, 256, 0, st>>>(s->touched, s->ntouched,
+                                                     reinterpret_cast<unsigned long long*>(s->smask));
+            note_launch();
+            CV_CUDA(cudaGetLastError());
         } else {
-            k_coverage<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, s->qmask, s->qbits, s->qcov);
+            k_coverage<<<cblocks, kCovThreads, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, s->qmask, s->qbits, hashed,
+                                                        s->qcov);
             note_launch();
             CV_CUDA(cudaGetLastError());
         }
+        CV_CUDA(cudaEventRecord(s->qev[1], st));
         k_estimate<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, g->w, g->f, g->W, s->T, s->qcov, d_cov, d_est,
                                        s->ris); note_launch();
         CV_CUDA(cudaGetLastError());
-        k_qmask_clear<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask, s->qbits); note_launch();
+        k_qmask_clear<<<wb, 256, 0, st>>>(d_off, d_seeds, q0, qn, g->n, s->qmask, s->qbits,
+                                          ordered_scan ? s->ntouched : nullptr); note_launch();
         CV_CUDA(cudaGetLastError());
     }
     dev_free(chunk_cnt, st);
@@ -387,6 +681,10 @@ int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32
     DevStatus h;
     CV_CUDA(cudaMemcpyAsync(&h, s->qstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     CV_CUDA(cudaStreamSynchronize(st));
+    if (q > 0 && q <= 64) {  // the device time of the coverage launches (one chunk of queries)
+        cudaEventElapsedTime(&query_ms, s->qev[0], s->qev[1]);
+        s->last_query_ms = query_ms;
+    }
     if (h.flags & kStInval) {
         *err = "skis_estimate: query " + std::to_string(h.first_bad) +
                " is empty, has a seed outside [0, n) or repeats a seed";

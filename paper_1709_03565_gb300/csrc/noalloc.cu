@@ -114,7 +114,7 @@ extern "C" int skis_estimate_noalloc(const skis_sketch* s, int32_t num_queries, 
     if (cb > cap) cb = cap;
     if (cb < 1) cb = 1;
     k_qmask_set<<<wb, 256, 0, st>>>(seed_offsets, seeds, 0, num_queries, g->n, qmask, nullptr, status); note_launch();
-    k_coverage<<<(unsigned)cb, 256, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, qmask, nullptr, qcov); note_launch();
+    k_coverage<<<(unsigned)cb, 256, 0, st>>>(s->h_off, s->h_len, s->T, s->arena, qmask, nullptr, 0, qcov); note_launch();
     k_estimate<<<wb, 256, 0, st>>>(seed_offsets, seeds, 0, num_queries, g->n, g->w, g->f, g->W, s->T, qcov,
                                    coverage_out, estimate_out, s->ris); note_launch();
     e = cudaGetLastError();

@@ -119,9 +119,12 @@ extern "C" int skis_server_create(skis_server** out, skis_sketch* s, int32_t slo
             return serve_fail(SKIS_EINVAL, "skis_server_create: seed_capacity must be in [1, 2^31]");
         if (s->T == 0) return serve_fail(SKIS_EINVAL, "skis_server_create: the sketch has no samples");
         {
-            // requests are answered through the sketch's inverted index
+            // requests are answered through the sketch's inverted index; the
+            // members are laid out in id order now, so that no later scan of
+            // the (unchanged) sketch moves them while the server reads them
             std::string err;
-            const int rc = sketch_inverted(s, s->stream, &err);
+            int rc = sketch_order_arena(s, s->stream, &err);
+            if (rc == SKIS_OK) rc = sketch_inverted(s, s->stream, &err);
             if (rc != SKIS_OK) return serve_fail(rc, err);
             const cudaError_t e = cudaStreamSynchronize(s->stream);
             if (e != cudaSuccess) return serve_fail(SKIS_ERR_CUDA, std::string("skis_server_create: ") + cudaGetErrorString(e));

@@ -332,6 +332,8 @@ struct skis_sketch {
     double last_thread_ms = 0, last_warp_ms = 0, last_cta_ms = 0, last_sample_ms = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // inverted index vertex -> samples (built on demand for the current T)
+    uint64_t ordered_T = 0;              // samples [0, ordered_T) hold arena positions [0, ordered_E) in id order
+    uint64_t ordered_E = 0;
     uint64_t* inv_off = nullptr;         // n+1
     uint32_t* inv = nullptr;             // sample ids, vertex after vertex
     uint64_t inv_T = 0;                  // T when the index was built (0 = none)
@@ -347,6 +349,12 @@ struct skis_sketch {
     uint64_t* qmask = nullptr;           // n per-vertex query bits
     uint32_t* qbits = nullptr;           // n bits: the vertex is a seed of the current batch
     unsigned long long* qcov = nullptr;  // 64 coverage counters
+    uint32_t* touched = nullptr;         // ordered scan: samples whose query word was set (for the reset)
+    unsigned long long* ntouched = nullptr;  // [0] touched count, [1] task cursor, [2] hit count
+    unsigned long long* hits = nullptr;      // ordered scan: (task, position) of members that may be seeds
+    uint64_t touched_cap = 0;
+    cudaEvent_t qev[2] = {nullptr, nullptr};  // around the coverage launches of a query chunk
+    double last_query_ms = 0;            // their device time in the last skis_estimate (<= 64 queries)
     skis::DevStatus* qstatus = nullptr;
     cudaStream_t stream = nullptr;
 };
@@ -366,6 +374,11 @@ int sketch_estimate_sharded(skis_sketch* s, int32_t q, const int64_t* d_off, con
                             void* ctx, cudaStream_t st, std::string* err);
 int sketch_greedy_sharded(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, double* h_est, int64_t* exch,
                           skis_allreduce_fn fn, void* ctx, cudaStream_t st, std::string* err);
+// Lays the members of samples [ordered_T, T) out in sample-id order right
+// after those of the samples before them (headers rebased, arena cursor
+// moved to the end): a warp's consecutive samples then read one contiguous
+// run of members. Only the layout changes, never a sample.
+int sketch_order_arena(skis_sketch* s, cudaStream_t st, std::string* err);
 // Builds (or reuses) the inverted index of the current T samples.
 int sketch_inverted(skis_sketch* s, cudaStream_t st, std::string* err);
 // Coverage of queries [q0, q0 + qn) of a CSR batch through the inverted
@@ -386,11 +399,11 @@ __global__ void k_qmask_set(const int64_t* __restrict__ off, const int32_t* __re
                             int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits,
                             DevStatus* st);
 __global__ void k_qmask_clear(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
-                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits);
+                              int32_t qn, int64_t n, uint64_t* __restrict__ qmask, uint32_t* __restrict__ qbits,
+                              unsigned long long* __restrict__ reset2);
 __global__ void __launch_bounds__(256) k_coverage(const uint64_t* __restrict__ h_off, const uint32_t* __restrict__ h_len, uint64_t T,
                            const int32_t* __restrict__ arena, const uint64_t* __restrict__ qmask,
-                                                 const uint32_t* __restrict__ qbits,
-                           unsigned long long* __restrict__ cov);
+                           const uint32_t* __restrict__ qbits, int hashed, unsigned long long* __restrict__ cov);
 __global__ void k_estimate(const int64_t* __restrict__ off, const int32_t* __restrict__ seeds, int32_t q0,
                            int32_t qn, int64_t n, const uint64_t* __restrict__ w, int f, uint64_t W, uint64_t T,
                            const unsigned long long* __restrict__ cov, int64_t* __restrict__ cov_out,
