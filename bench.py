@@ -598,6 +598,10 @@ def dssa_run(args):
     eps, delta = 0.1, 1.0 / n
     runs = {}
     seeds = None
+    # warm-up: the first run on a graph pays the device memory pool's growth
+    skis.skis_dssa_maxinf(g, SKETCH_SEED + 4, SKETCH_SEED + 5, 1, eps, delta, 0, 1 << 16, args.dssa_max_samples,
+                          stream=stream)
+    torch.cuda.synchronize()
     for k in (1, 100, 1000):
         t2 = time.perf_counter()
         sk, res = skis.skis_dssa_maxinf(g, SKETCH_SEED + 4, SKETCH_SEED + 5, k, eps, delta, 0, 1 << 16,

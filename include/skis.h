@@ -23,8 +23,8 @@
  *     skis_graph_free / skis_sketch_free release memory on the stream of the
  *     handle's last call, which must still exist.
  *   - Member layout: the first sketch scan of skis_estimate after new
- *     samples moves their members into sample-id order in the sketch's
- *     storage. Only the layout changes, never a sample; do not overlap such a
+ *     samples (sketches of 2^20 samples or more) moves their members into
+ *     sample-id order in the sketch's storage. Only the layout changes, never a sample; do not overlap such a
  *     call with other work on the same sketch (a server included).
  *   - Memory spaces: where a call takes SKIS_MEM_HOST or SKIS_MEM_DEVICE,
  *     the pointers it names are host or device pointers accordingly.
@@ -126,7 +126,9 @@ typedef enum skis_option {
     SKIS_OPT_THREAD_BLOCKS = 4,  /* CTAs of the thread tier (default: full occupancy) */
     SKIS_OPT_QUERY_INDEX = 5,    /* skis_estimate: 0 = walk the inverted index (vertex -> samples) when
                                     it is built for the current samples, else scan the sketch (default);
-                                    1 = build it if needed and walk it; 2 = always scan */
+                                    1 = build it if needed and walk it; 2 = always scan; 3 = always scan,
+                                    with the members in sample-id order whatever the sketch's size (the
+                                    scan's layout is otherwise used from 2^20 samples on) */
     SKIS_OPT_THREAD_MAX_STEPS = 6, /* edge quads a sample may take in the thread tier before the warp
                                       tier takes it over (default 256) */
     SKIS_OPT_SAMPLER = 7,         /* 0 = IIS samples (Alg. 1, default); 1 = plain RIS samples (Sec. II-C,

@@ -247,7 +247,7 @@ extern "C" int skis_sketch_set_option(skis_sketch* s, int option, uint64_t value
             s->ris = (int)value;
             return SKIS_OK;
         case SKIS_OPT_QUERY_INDEX:
-            if (value > 2) return fail(SKIS_EINVAL, "query-index mode must be 0, 1 or 2");
+            if (value > 3) return fail(SKIS_EINVAL, "query-index mode must be 0, 1, 2 or 3");
             s->query_index = (int)value;
             return SKIS_OK;
         case SKIS_OPT_THREAD_BLOCKS:

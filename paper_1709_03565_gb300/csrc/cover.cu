@@ -581,9 +581,11 @@ int sketch_estimate(skis_sketch* s, int32_t q, const int64_t* d_off, const int32
         const int rc = sketch_inverted(s, st, err);
         if (rc != SKIS_OK) return rc;
     }
-    const bool by_index = s->query_index != 2 && s->inv && s->inv_T == s->T;
-    // the scan streams the members in sample-id order (samples below 2^32)
-    const bool ordered_scan = !by_index && s->T < (1ull << 32);
+    const bool by_index = s->query_index < 2 && s->inv && s->inv_T == s->T;
+    // a large sketch is scanned with its members in sample-id order (laid out
+    // once per new samples); a small one (below 2^20 samples: doubling rounds,
+    // tests) directly, where that one-time layout would cost more than it saves
+    const bool ordered_scan = !by_index && (s->T >= (1ull << 20) || s->query_index == 3) && s->T < (1ull << 32);
     if (ordered_scan) {
         const int rc = sketch_order_arena(s, st, err);
         if (rc != SKIS_OK) return rc;

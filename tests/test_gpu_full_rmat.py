@@ -107,4 +107,9 @@ def test_full_rmat_greedy_and_queries(rmat):
     ocov, oest = osk.coverage(off, seeds)
     assert np.array_equal(cov, ocov)
     np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
+    # the scan of the members in id order, with the hashed seed filter of a graph above 2^20 vertices
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_QUERY_INDEX, 3)
+    cov2, est2 = skis.skis_estimate(s, off, seeds)
+    assert np.array_equal(cov2, ocov) and np.array_equal(est2, est)
     s.close()
+

@@ -173,7 +173,7 @@ def test_device_queries_and_batches_over_64(er_small):
     d_off = torch.from_numpy(off).cuda()
     d_seeds = torch.from_numpy(seeds).cuda()
     ocov, oest = osk.coverage(off, seeds)
-    for mode in (2, 1, 0):  # scan the sketch; walk the inverted index; automatic
+    for mode in (2, 3, 1, 0):  # scan the sketch; scan it in id order; walk the inverted index; automatic
         skis.skis_sketch_set_option(s, skis.SKIS_OPT_QUERY_INDEX, mode)
         d_cov = torch.empty(len(sizes), dtype=torch.int64, device="cuda")
         d_est = torch.empty(len(sizes), dtype=torch.float64, device="cuda")
@@ -322,6 +322,16 @@ def test_full_size_greedy_and_coverage(chunglu_full):
     ocov, oest = osk.coverage(off, seeds)
     assert np.array_equal(cov, ocov)
     np.testing.assert_allclose(est, oest, rtol=REL, atol=0)
+    # the same queries, and a ragged batch of 150, by the scan of the members in id order
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_QUERY_INDEX, 2)
+    cov2, est2 = skis.skis_estimate(s, off, seeds)
+    assert np.array_equal(cov2, ocov) and np.array_equal(est2, est)
+    off3, seeds3 = synth.seed_sets(spec["n"], synth.log_uniform_sizes(150, 1, 1000, 12), 13)
+    cov3, est3 = skis.skis_estimate(s, off3, seeds3)
+    ocov3, oest3 = osk.coverage(off3, seeds3)
+    assert np.array_equal(cov3, ocov3)
+    np.testing.assert_allclose(est3, oest3, rtol=REL, atol=0)
+    skis.skis_sketch_set_option(s, skis.SKIS_OPT_QUERY_INDEX, 0)
 
 
 def test_autotuned_split_gives_the_same_samples(er_small):
