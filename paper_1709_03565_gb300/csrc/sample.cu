@@ -827,6 +827,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1024 / kCtaThreads) k_iis_cta(Sam
     __shared__ uint32_t s_pre[kCtaWin], s_lo[kCtaWin], s_hi[kCtaWin], s_tau[kCtaWin];
     __shared__ uint32_t s_hub[kCtaWin];  // window rows taken by the hub loop
     __shared__ uint32_t s_nhub;
+    __shared__ uint32_t s_small[3];      // a small window's quad-group shift, quad groups and hub rows
     __shared__ uint32_t s_wsum[kCtaThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     constexpr int kWarps = kCtaThreads / 32;
@@ -904,13 +905,50 @@ __global__ void __launch_bounds__(kCtaThreads, 1024 / kCtaThreads) k_iis_cta(Sam
         // time, so one long in-row (a hub) is shared by every warp.
         uint64_t coins = 0;
         uint32_t head = 1;
+        uint32_t tail = s_qlen;  // after the first step's barrier: its inserts are in
         for (;;) {
-            __syncthreads();
-            const uint32_t tail = s_qlen;
-            __syncthreads();
             if (head >= tail || tail > a.queue_cap) break;  // done, or the sample outgrew the slot
             for (uint32_t w0 = head; w0 < tail; w0 += kCtaWin) {
                 const uint32_t nw = min((uint32_t)kCtaWin, tail - w0);
+                uint32_t gsh, total, nhub;  // quad-group shift, quad groups and hub rows of the window
+                if (nw <= 32) {
+                    // a small window (the narrow frontiers of weighted cascade):
+                    // warp 0 loads, classifies and prefixes its rows, one barrier
+                    if (wid == 0) {
+                        uint32_t nq = 0;
+                        bool hub = false;
+                        if ((uint32_t)lane < nw) {
+                            const RowInfo rw = a.rows[queue[w0 + lane]];
+                            coins += rw.deg;
+                            const uint32_t lo = (uint32_t)rw.off, hi = lo + rw.deg;
+                            s_lo[lane] = lo;
+                            s_hi[lane] = hi;
+                            s_tau[lane] = rw.tau;
+                            nq = rw.deg ? ((hi - 1) >> 2) - (lo >> 2) + 1 : 0u;  // edge quads
+                            hub = a.cta_hub_quads && nq >= a.cta_hub_quads;
+                            if (hub) nq = 0;  // the hub loop takes it
+                        }
+                        const unsigned hb = __ballot_sync(kFull, hub);
+                        if (hub) s_hub[__popc(hb & lanemask_lt())] = (uint32_t)lane;
+                        const uint32_t g = __any_sync(kFull, nq >= (uint32_t)kCtaLongRow) ? (uint32_t)kCtaGroupLog2 : 0u;
+                        uint32_t x = (nq + (1u << g) - 1) >> g;
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const uint32_t y = __shfl_up_sync(kFull, x, d);
+                            if (lane >= d) x += y;
+                        }
+                        if ((uint32_t)lane < nw) s_pre[lane] = x;
+                        if (lane == 31) {
+                            s_small[0] = g;
+                            s_small[1] = x;
+                            s_small[2] = (uint32_t)__popc(hb);
+                        }
+                    }
+                    __syncthreads();
+                    gsh = s_small[0];
+                    total = s_small[1];
+                    nhub = s_small[2];
+                } else {
                 uint32_t nq2[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -933,12 +971,11 @@ __global__ void __launch_bounds__(kCtaThreads, 1024 / kCtaThreads) k_iis_cta(Sam
                 // a window with a long row (a hub) deals its quads kCtaGroup at
                 // a time to amortise the row search; others one at a time, so
                 // that short rows keep every lane busy
-                const uint32_t gsh =
-                    __syncthreads_or(nq2[0] >= (uint32_t)kCtaLongRow || nq2[1] >= (uint32_t)kCtaLongRow)
-                        ? (uint32_t)kCtaGroupLog2 : 0u;  // group of 2^gsh quads
-                const uint32_t grp = 1u << gsh;
+                gsh = __syncthreads_or(nq2[0] >= (uint32_t)kCtaLongRow || nq2[1] >= (uint32_t)kCtaLongRow)
+                          ? (uint32_t)kCtaGroupLog2 : 0u;  // group of 2^gsh quads
+                const uint32_t grp0 = 1u << gsh;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) nq2[h] = (nq2[h] + grp - 1) >> gsh;
+                for (int h = 0; h < 2; ++h) nq2[h] = (nq2[h] + grp0 - 1) >> gsh;
                 // block-wide inclusive prefix of the quad-group counts
                 const uint32_t pair = nq2[0] + nq2[1];
                 uint32_t x = pair;
@@ -952,7 +989,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1024 / kCtaThreads) k_iis_cta(Sam
                 // every thread reads the hub count between these two barriers,
                 // and it is cleared after the second, before any thread can
                 // classify the next window's rows
-                const uint32_t nhub = s_nhub;
+                nhub = s_nhub;
                 if (wid == 0) {
                     uint32_t w = lane < kWarps ? s_wsum[lane] : 0u;
 #pragma unroll
@@ -968,7 +1005,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1024 / kCtaThreads) k_iis_cta(Sam
                 if (2u * threadIdx.x < nw) s_pre[2u * threadIdx.x] = before + nq2[0];
                 if (2u * threadIdx.x + 1 < nw) s_pre[2u * threadIdx.x + 1] = before + pair;
                 __syncthreads();
-                const uint32_t total = s_pre[nw - 1];
+                total = s_pre[nw - 1];
+                }
+                const uint32_t grp = 1u << gsh;
                 // quad group g (nothing when g is past the window): quads q ..
                 // q + grp - 1 of one row, independent Philox blocks; a
                 // quad inside the row skips the edge bounds. Returns the live
@@ -1091,6 +1130,7 @@ __global__ void __launch_bounds__(kCtaThreads, 1024 / kCtaThreads) k_iis_cta(Sam
                 __syncthreads();  // the window's shared arrays are reused
             }
             head = tail;
+            tail = s_qlen;  // after the level's last barrier: every insert of the level is in
         }
         coins = warp_sum_u64(coins);
         if (lane == 0 && coins) atomicAdd(&s_coins, (unsigned long long)coins);
