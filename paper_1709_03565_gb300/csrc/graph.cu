@@ -131,9 +131,36 @@ __global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __rest
         uint64_t Q = one62;
         uint32_t k = 0;
         if (!csr_tau) {  // one threshold for the row (weighted cascade)
-            for (; k < r.deg && (Q != 0 || chain); ++k) {
-                Q = chain_step(Q, r.tau);
-                if (chain) chain[r.off + k] = Q;
+            const uint32_t t = r.tau;
+            if (t == kSentinel || t == 0) {  // every step gives 0, or keeps Q
+                const uint64_t q = (t == kSentinel && r.deg) ? 0 : Q;
+                if (chain)
+                    for (; k < r.deg; ++k) chain[r.off + k] = q;
+                Q = q;
+            } else {
+                // a pure dependent chain of Q <- qh c + hi32(ql c), four steps an
+                // iteration, their values stored two to a 16-byte store when the
+                // position is even (the chain array is 16-byte aligned)
+                const uint32_t c = (uint32_t)(0x100000000ull - t);
+                auto step = [c](uint64_t q) { return (uint64_t)(uint32_t)(q >> 32) * c + __umulhi((uint32_t)q, c); };
+                if (chain && ((r.off + k) & 1) && k < r.deg) {
+                    Q = step(Q);
+                    chain[r.off + k] = Q;
+                    ++k;
+                }
+                for (; k + 4 <= r.deg && (Q != 0 || chain); k += 4) {
+                    const uint64_t q1 = step(Q), q2 = step(q1), q3 = step(q2), q4 = step(q3);
+                    if (chain) {
+                        ulonglong2* p = reinterpret_cast<ulonglong2*>(chain + r.off + k);
+                        p[0] = make_ulonglong2(q1, q2);
+                        p[1] = make_ulonglong2(q3, q4);
+                    }
+                    Q = q4;
+                }
+                for (; k < r.deg && (Q != 0 || chain); ++k) {
+                    Q = step(Q);
+                    if (chain) chain[r.off + k] = Q;
+                }
             }
         } else {
             for (; k + 8 <= r.deg && (Q != 0 || chain); k += 8) {
