@@ -31,6 +31,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -174,9 +175,17 @@ def _peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def code_sha(src: bytes) -> str:
+    """sha256 of a CUDA source's code: comments and blank space removed, so
+    a record stays valid across comment edits but not across code changes
+    (string literals in the sampler hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", " ", src.decode(), flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()
+
+
 def _sampler_sha() -> str:
-    src = open(os.path.join(ROOT, "paper_1709_03565_gb300", "csrc", "sample.cu"), "rb").read()
-    return hashlib.sha256(src).hexdigest()
+    return code_sha(open(os.path.join(ROOT, "paper_1709_03565_gb300", "csrc", "sample.cu"), "rb").read())
 
 
 def _profile_record(name: str, workload: str, first_step: str):
@@ -216,6 +225,26 @@ def alu_peak_blocks_per_s(sms: int, mhz: float) -> float:
     64 32-bit integer multiply-adds per clock per SM, a block's ten rounds of
     two 32x32->64 products counted as 40 of them."""
     return sms * 64.0 / PHILOX_IMAD * mhz * 1e6
+
+
+def measured_alu_ceiling(skis, stream, sms: int, gpu_id: str) -> dict:
+    """The coin generator's measured throughput on this GPU: the probe launch
+    draws only Philox blocks (2048 threads per SM, 4096 blocks each, four
+    independent blocks a step) and counts the words below a threshold, with
+    no memory traffic. Per form (0: every block in full; 1: the hub loop's
+    per-sample hoisting) three warm-up launches, then 40 timed ones: best and
+    median, with the SM clocks sampled over the timed launches."""
+    threads, per = sms * 2048, 4096
+    out = {"threads": threads, "blocks_per_launch": threads * per, "kernel": "k_philox_rate"}
+    for form, name in ((0, "full_blocks"), (1, "hoisted_blocks")):
+        for r in range(3):
+            skis.skis_philox_rate(1 + r, threads, per, 4295, form, stream=stream)
+        clocks = ClockSampler(gpu_id)
+        clocks.start()
+        ms = sorted(skis.skis_philox_rate(1 + r, threads, per, 4295, form, stream=stream)[0] for r in range(40))
+        out[name] = {"blocks_per_s": threads * per / (ms[0] / 1e3), "ms": ms[0],
+                     "median_blocks_per_s": threads * per / (ms[len(ms) // 2] / 1e3), "clocks": clocks.stop()}
+    return out
 
 
 # -------------------------------------------------------------- oracle
@@ -855,6 +884,9 @@ def main():
                 "frac": alu_achieved / alu_peak, "traffic": traffic, "kernel": kernel, "kernel_ms": sample_ms,
                 "peak_kind": f"derived: {sms} SMs x 64 IMAD/clk / {PHILOX_IMAD} per block x {max_mhz:.0f} MHz",
                 "l2": l2}
+    ceiling = measured_alu_ceiling(skis, stream, sms, gpu_uuid)
+    roofline["measured_ceiling"] = ceiling
+    roofline["frac_of_measured_ceiling"] = alu_achieved / ceiling["hoisted_blocks"]["blocks_per_s"]
     alg = algorithmic_bytes(per, entries, coins, per_edge_tau=False)
     roofline_hbm = {"bound": "hbm", "achieved": alg / (sample_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                     "frac": alg / (sample_ms / 1e3) / 1e9 / peak, "traffic": traffic, "algorithmic_bytes": alg,

@@ -238,10 +238,10 @@ int skis_sketch_autotune(skis_sketch *s, uint64_t pilot_samples, uint32_t *chose
  * (F = SKIS_OPT_FIRST_ID, 0 by default). For sample j:
  *   - source: Philox block (key seed, domain SRC, id j) gives col = floor(U1 n)
  *     and y = floor(U2 W); src = col if y < prob[col] else alias[col];
- *   - first step (Alg. 1 lines 2-6, Eq. probn) by rejection: round
+ *   - first step (Alg. 1, Eq. probn) by rejection: round
  *     r = 0, 1, ... flips every in-edge coin of src (domain FIRST, retry r)
  *     until one is live; its live in-neighbours join R_j;
- *   - reverse BFS (Alg. 1 lines 7-11): every in-edge e of every other member
+ *   - reverse BFS (Alg. 1): every in-edge e of every other member
  *     gets the coin (domain BFS, sample j, edge e); live edges add their
  *     source. R_j is the reverse-reachable set of src in that live-edge world.
  * Counters per sample: retries r, coins = d_in(src)(r + 1) + sum of d_in
@@ -264,7 +264,7 @@ int skis_sample(skis_sketch *s, uint64_t count, uint64_t *next_sample_id_out, vo
 int skis_sample_to_size(skis_sketch *s, uint64_t target_entries, uint64_t max_count, uint64_t *appended_out,
                         uint64_t *next_sample_id_out, void *cuda_stream);
 
-/* Influence queries (Alg. 2 line 2, Eq. 21): for each seed set S_b, b <
+/* Influence queries (Alg. 2's estimate step, Eq. 21): for each seed set S_b, b <
  * num_queries, given as CSR (seed_offsets int64[q+1], seeds int32[...]):
  *   coverage_out[b] = Cov_R(S_b) = #{j : R_j meets S_b},
  *   estimate_out[b] = N / D with N = Cov W + T sum_{v in S_b} (2^f - w_v) and
@@ -400,7 +400,7 @@ int skis_dssa_maxinf(const skis_graph *g, uint64_t seed_r, uint64_t seed_rc, int
                      void *cuda_stream);
 
 /* Continuous-batching influence-oracle server over a device-resident sketch
- * (Alg. 2 line 2 for a stream of requests). skis_server_submit validates a
+ * (Alg. 2's estimate step for a stream of requests). skis_server_submit validates a
  * seed set (host array, copied; non-empty, ids in [0, n), no repeats) and
  * queues it, returning a ticket. skis_server_progress retires finished
  * batches and admits queued requests, in arrival order, into every free
@@ -425,6 +425,20 @@ int skis_server_poll(skis_server *srv, uint64_t ticket, int64_t *coverage_out, d
 int skis_server_counts(const skis_server *srv, uint64_t *queued, uint64_t *in_flight, uint64_t *batches,
                        uint64_t *served);
 void skis_server_free(skis_server *srv);
+
+/* The integer-ALU ceiling of the coin generator on this GPU (a measurement
+ * probe, no counterpart in the paper): `threads` threads each draw the
+ * Philox4x32-10 blocks of edge quads [t b, (t + 1) b) of sample id t (BFS
+ * domain, key seed; b = blocks_per_thread), four independent blocks a step,
+ * and count the coin words below tau, in one launch with no memory traffic
+ * but one count per thread: form 0 computes every block as a sampler tier
+ * does (20 products), form 1 as the CTA tier's hub loop does (two products
+ * hoisted per sample, 18). ms_out receives the launch's device time,
+ * live_out the count (it depends on the coins only). threads and
+ * blocks_per_thread in [1, 2^31] with fewer than 2^32 blocks in all, form 0
+ * or 1, else SKIS_EINVAL; synchronises the stream. */
+int skis_philox_rate(uint64_t seed, uint64_t threads, uint64_t blocks_per_thread, uint32_t tau, int form,
+                     double *ms_out, uint64_t *live_out, void *cuda_stream);
 
 /* Number of CUDA kernel launches the library has made in this process
  * (diagnostic; counts every launch of every entry point). */

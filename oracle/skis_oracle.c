@@ -35,12 +35,12 @@
  *      Weighted Random Sampling", ESA 2019) in integer arithmetic: column
  *      capacity W, item mass w_v * n, light items (mass < W) and heavy items
  *      in ascending vertex order.
- *   R5 The conditioned first step (Alg. 1 lines 2-6, Eq. probn) is taken in
+ *   R5 The conditioned first step (Alg. 1, Eq. probn) is taken in
  *      rejection form: all in-edge coins of the source are redrawn, round
  *      r = 0, 1, ..., until at least one is live. This has the law of the
  *      bucket choice of Eq. probn followed by independent coins on the
  *      in-neighbours after the chosen one (the bucket definition excludes
- *      those before it, although Alg. 1 line 4 writes "t != i").
+ *      those before it, although Alg. 1's first-step loop writes "t != i").
  *   R6 Every coin is a Philox4x32-10 word keyed by the sketch seed, with the
  *      counter (edge-quad e>>2, domain, retry, sample id); see coin_word().
  *      The BFS coin of edge e in sample j is fixed, so R_j is the reverse
@@ -462,12 +462,12 @@ static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t re
 {
     const int ris = flags & ORC_F_RIS;
     const int bucket = (flags & ORC_F_BUCKET) && !ris;
-    /* line 1: the source, Eq. probu (RIS: uniform) */
+    /* the source, Eq. probu (RIS: uniform) */
     int64_t v = ris ? draw_source_uniform(g, seed, j) : draw_source(g, seed, j);
     int64_t b = g->off[v], e_end = g->off[v + 1];
     *src_out = (int32_t)v;
 
-    /* lines 2-6 in rejection form (R5): round r flips every in-edge of v
+    /* the conditioned first step in rejection form (R5): round r flips every in-edge of v
      * (RIS: round 0 only, accepted whatever its coins) */
     uint32_t r = 0;
     int64_t picked = -1; /* B1: the bucket's live in-edge */
@@ -487,7 +487,7 @@ static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t re
     }
     *retries_out = r;
 
-    /* line 3: R_j = {v} plus the live in-neighbours of the accepted round;
+    /* R_j = {v} plus the live in-neighbours of the accepted round;
      * the queue Q is members[head .. len) */
     int64_t len = 0;
     visited[v] = 1;
@@ -498,7 +498,7 @@ static int sample_one(const orc_graph *g, uint64_t seed, uint64_t j, uint32_t re
         if (!visited[u]) { visited[u] = 1; members[len++] = u; }
     }
 
-    /* lines 7-11: reverse BFS, FIFO, one coin per in-edge from outside R_j */
+    /* reverse BFS, FIFO, one coin per in-edge from outside R_j */
     uint64_t coins = (uint64_t)(e_end - b) * (r + 1);
     for (int64_t head = 1; head < len; head++) {
         int32_t w = members[head];
@@ -722,7 +722,7 @@ static void estimate_nd(const orc_sketch *s, int64_t cov, u128 sum_c, u128 *N, u
     *D = (u128)(uint64_t)s->T << s->g->f;
 }
 
-/* Influence queries (Alg. 2 line 2): for each seed set S_b (CSR seed_off /
+/* Influence queries (Alg. 2's estimate step): for each seed set S_b (CSR seed_off /
  * seeds), Cov_R(S_b) = #{j : R_j meets S_b} and I_R(S_b) by Eq. 21.
  * num/den receive N and D as (low, high) 64-bit halves (may be NULL).
  * Empty, out-of-range or repeated seeds give ORC_EINVAL. */

@@ -133,7 +133,7 @@ __device__ __forceinline__ uint32_t draw_source(const SampleArgs& a, uint64_t j)
     return y < e.prob ? (uint32_t)col : e.alias;
 }
 
-// The bucket form of Alg. 1 lines 2-6 (Eq. probn): bucket i of the source's
+// The bucket form of Alg. 1's conditioned first step (Eq. probn): bucket i of the source's
 // row is "in-edges before i dead, edge i live", of mass Q_{i-1} - Q_i in the
 // gamma chain (total 2^62 - Q_d); z = floor(U (2^62 - Q_d) / 2^64) from the
 // BUCKET-domain block of sample j picks the first edge e with
@@ -315,7 +315,7 @@ __device__ __forceinline__ bool expand_rows(const SampleArgs& a, uint64_t j, uin
     return __any_sync(kFull, any);
 }
 
-// Alg. 1 lines 2-6 for one warp: the rejection rounds r = 0, 1, ... of the
+// Alg. 1's conditioned first step for one warp: the rejection rounds r = 0, 1, ... of the
 // source row, until one round has a live coin; the live in-neighbours of that
 // round are inserted. Rounds are independent given (j, r), so a short row
 // (nq <= 16 edge quads) is searched 32 / nq rounds per pass: lane g takes
@@ -413,7 +413,7 @@ __device__ __forceinline__ void record_retry_failure(const SampleArgs& a, uint64
     atomicMin(&a.status->first_bad, (unsigned long long)j);
 }
 
-// Alg. 1 line 1 for every input id at once: the source of sample j and its
+// Alg. 1's source draw for every input id at once: the source of sample j and its
 // in-row, as 16 bytes (source, degree, row offset, row threshold), so that a
 // lane-tier lane starting a sample makes one coalesced load; with the bucket
 // form, also the first step's picked in-edge and its source (8 bytes), whose
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                 const uint32_t pk_u = __shfl_sync(kFull, prec.y, from);
                 if (!busy && rank < take) {
                     j = input_id(a, pool_base + pool_used + rank);
-                    v = rv_src;  // Alg. 1 line 1, drawn by k_sources
+                    v = rv_src;  // Alg. 1's source, drawn by k_sources
                     if (rv_deg > a.max_deg) {
                         hand_on(a, j);
                     } else {
@@ -604,8 +604,8 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
         }
         if (!busy || done) continue;  // the lane waits for the next batch
 
-        // ---- one edge quad: coins of lines 4-6 (first step, round r) or
-        // of line 9 (reverse BFS); a RIS source may have no in-edges
+        // ---- one edge quad: coins of the first step (round r) or of the
+        // reverse BFS; a RIS source may have no in-edges
         bool handed = false, failed = false;
         uint32_t qdone = qc;  // the last quad drawn in this step
         if (hi > lo) {
@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                 }
             }
             if (!first && !failed && !handed) {
-                // Alg. 1 lines 7-8: pop the next queued members until one
+                // Alg. 1's reverse BFS: pop the next queued members until one
                 // has in-edges (the first one's row was loaded ahead)
                 bool row = false;
                 while (!row && head < len) {
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
                 reinterpret_cast<uint4*>(hash)[i] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
             __syncwarp();
 
-            // Alg. 1 line 1: the source
+            // Alg. 1: the source
             RowInfo rv;
             int64_t pe;
             int32_t pu;
@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
             WarpInserter ins{hash, queue, 0u, false};
             ins.insert(lane == 0 ? (int32_t)v : -1);
 
-            // lines 2-6 by rejection: all in-edge coins of v, round r
+            // the conditioned first step by rejection: all in-edge coins of v, round r
             bool failed = false;
             const uint32_t r = first_step_warp(a, j, rv, ins, &failed, pe, pu);
             if (failed) {
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_iis_warp(SampleArgs a) {
                 continue;
             }
 
-            // lines 7-11: reverse BFS over the queue, up to 32 vertices at a time
+            // reverse BFS over the queue, up to 32 vertices at a time
             uint64_t coins = lane == 0 ? (uint64_t)rv.deg * (r + 1) : 0;
             uint64_t drawn = 0;  // in-edges of the rows taken so far (warp-uniform)
             bool heavy = false;

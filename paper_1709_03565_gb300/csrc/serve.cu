@@ -1,4 +1,4 @@
-// Continuous-batching influence-oracle server (Alg. 2 line 2, Eq. 21, served
+// Continuous-batching influence-oracle server (Alg. 2's estimate step, Eq. 21, served
 // against a device-resident sketch and its inverted index).
 //
 // Requests (seed sets) are validated and queued on the host at submit time.

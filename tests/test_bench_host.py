@@ -36,14 +36,16 @@ def _fake_root(tmp_path, src: bytes, record: dict):
 
 
 def test_traffic_follows_the_kernel_source(tmp_path, monkeypatch):
-    src = b"// sampler source\n"
-    record = {"sample_cu_sha256": hashlib.sha256(src).hexdigest(), "first_step": "bucket",
+    src = b"// sampler source\n__global__ void k(int* a) { a[0] = 1; }\n"
+    record = {"sample_cu_sha256": bench.code_sha(src), "first_step": "bucket",
               "dram_bytes_per_sample": 497.5, "workload_key": bench.C2_WORKLOAD}
     _fake_root(tmp_path, src, record)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench._traffic_per_sample("bucket") == 497.5
     assert bench._traffic_per_sample("rejection") is None  # captured on the other form
-    (tmp_path / "paper_1709_03565_gb300" / "csrc" / "sample.cu").write_bytes(src + b"// changed\n")
+    (tmp_path / "paper_1709_03565_gb300" / "csrc" / "sample.cu").write_bytes(src + b"/* a comment\n edit */\n")
+    assert bench._traffic_per_sample("bucket") == 497.5  # comments do not change the kernel
+    (tmp_path / "paper_1709_03565_gb300" / "csrc" / "sample.cu").write_bytes(src.replace(b"= 1", b"= 2"))
     assert bench._traffic_per_sample("bucket") is None  # the kernel changed since the capture
 
 
@@ -56,7 +58,8 @@ def test_committed_record_names_its_capture():
 
 def test_profile_summaries_name_commands_on_committed_files():
     """Every ncu summary gives the command that made it; the command runs
-    ncu with --clock-control none on the committed bench, nothing else."""
+    ncu with --clock-control none on the committed bench or the package,
+    nothing else."""
     pdir = os.path.join(bench.ROOT, "profiles")
     mds = [f for f in os.listdir(pdir) if f.endswith(".md")]
     assert mds
@@ -66,7 +69,8 @@ def test_profile_summaries_name_commands_on_committed_files():
         assert cmds, f
         for c in cmds:
             assert "--clock-control none" in c, f
-            assert " python bench.py" in c and "_work" not in c, f
+            assert (" python bench.py" in c or (" python -c " in c and "paper_1709_03565_gb300" in c)), f
+            assert "_work" not in c, f
             if "--set" in c or "--section" in c:  # full captures: one kernel, a few launches
                 k = c.split(" -k ", 1)[1].split()[0] if " -k " in c else ""
                 assert k and "|" not in k, f

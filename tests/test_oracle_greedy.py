@@ -91,8 +91,8 @@ def test_greedy_edge_cases():
     assert sorted(seeds.tolist()) == list(range(n)) and cov[-1] == 100
     with pytest.raises(oracle.OracleError):
         sk.greedy(n + 1)
-    # vertices that appear in no sample still carry gain 1 - gamma_v (Alg. 3
-    # line 3). Edge 1 -> 0 plus isolated vertices 2, 3, 4: every sample is
+    # vertices that appear in no sample still carry gain 1 - gamma_v (Alg. 3's
+    # marginal gain). Edge 1 -> 0 plus isolated vertices 2, 3, 4: every sample is
     # {0, 1}; greedy takes 1 (I = 1 + p'), then the isolated vertices (gain 1
     # each, lowest id first) ahead of 0 (gain 1 - gamma_0).
     g = oracle.OracleGraph(5, [1], [0], weights=np.array([0.25]), model=oracle.W_P)
