@@ -759,6 +759,17 @@ __device__ __forceinline__ KeyId shfl_down_keyid(const KeyId& x, int d) {
     return y;
 }
 
+__device__ __forceinline__ KeyId shfl_keyid(const KeyId& x, int src) {
+    KeyId y;
+    y.key = ((u128)__shfl_sync(kFull, (unsigned long long)(x.key >> 64), src) << 64) |
+            (u128)__shfl_sync(kFull, (unsigned long long)x.key, src);
+    y.id = __shfl_sync(kFull, x.id, src);
+    y.valid = __shfl_sync(kFull, x.valid, src);
+    y.d = __shfl_sync(kFull, x.d, src);
+    y.pad = 0;
+    return y;
+}
+
 __device__ KeyId block_best(KeyId b, KeyId* s_part) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
 #pragma unroll
@@ -794,6 +805,8 @@ struct GreedyArgs {
     const int32_t* arena;
     uint32_t* covered;
     KeyId* partial;
+    KeyId* seg_best;  // per segment of kGreedySeg vertices: its best of the last scan
+    int64_t nseg;
     int32_t* seeds;
     int64_t* cov_out;
     double* est_out;
@@ -824,6 +837,8 @@ __device__ __forceinline__ KeyId ldcg_keyid(const KeyId* p) {
 // other blocks change during the launch (Delta, the block bests) is read
 // through L2 (ld.global.cg), never from a possibly stale L1 line.
 constexpr int kGreedyThreads = 1024;
+constexpr int kGreedySegLog = 8;  // vertices per segment: 256
+constexpr int64_t kGreedySeg = 1ll << kGreedySegLog;
 constexpr uint32_t kBigLen = 256;   // covered samples longer than this are walked by the whole block
 constexpr int kBigQueue = 64;
 
@@ -836,64 +851,77 @@ __global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs 
     __shared__ uint64_t s_big_off[kBigQueue];
     __shared__ uint32_t s_big_len[kBigQueue];
     __shared__ uint32_t s_nbig;
-    __shared__ KeyId s_best;  // this block's best of the previous round
-    __shared__ int s_reuse;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint64_t one_f = 1ull << a.f;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int nw = kGreedyThreads / 32;
     for (int i = threadIdx.x; i < kHotSlots; i += blockDim.x) {
         s_hkey[i] = kHotEmpty;
         s_hcnt[i] = 0;
     }
-    if (threadIdx.x == 0) {
-        s_nbig = 0;
-        s_best = KeyId{0, 0xFFFFFFFFu, 0};
-    }
+    if (threadIdx.x == 0) s_nbig = 0;
     uint64_t cov = 0, sum_c = 0;  // running totals, kept by block 0
     __syncthreads();
     for (int32_t round = 0; round < a.k; ++round) {
-        // keys only decrease, so if the block's previous best is still
-        // outside S with an unchanged Delta it is still the block's best
-        // (every other key is at most what it was; ties keep the lowest id)
-        if (threadIdx.x == 0) {
-            int reuse = 0;
-            if (s_best.valid) reuse = !a.inS[s_best.id] && __ldcg(a.delta + s_best.id) == s_best.d;
-            s_reuse = reuse;
-        }
-        __syncthreads();
-        const bool reuse = s_reuse != 0;
-        KeyId best{0, 0xFFFFFFFFu, 0};
-        if (!reuse) {
-        // four of the thread's vertices per pass, their loads issued together
-        // (a vertex's S flag is written only by the thread that scans it)
-        for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v0 < a.n; v0 += 4 * stride) {
-            uint8_t in4[4];
-            uint32_t d4[4];
-            uint64_t w4[4];
+        // the best outside S: each lane holds one segment's best at a time.
+        // Keys only decrease, so a segment whose best is still outside S
+        // with an unchanged Delta keeps it (every other key is at most what
+        // it was; ties keep the lowest id), and a segment with no vertex
+        // outside S stays so; the others are rescanned, one warp each.
+        // warp gw of W takes segments gw + W i, 32 of them at a time (lane l:
+        // gw + W (32 i + l)); the block index varies fastest over gw, so a
+        // few segments already spread over every SM
+        KeyId wbest{0, 0xFFFFFFFFu, 0};
+        const int64_t W = (int64_t)gridDim.x * nw, gw = (int64_t)wib * gridDim.x + blockIdx.x;
+        for (int64_t g0 = gw; g0 < a.nseg; g0 += 32 * W) {
+            const int64_t sg = g0 + lane * W;
+            KeyId b{0, 0xFFFFFFFFu, 0};
+            bool ok = sg >= a.nseg;
+            if (!ok && round > 0) {
+                b = ldcg_keyid(a.seg_best + sg);
+                ok = !b.valid || (!__ldcg(a.inS + b.id) && __ldcg(a.delta + b.id) == b.d);
+            }
+            unsigned redo = __ballot_sync(kFull, !ok);
+            while (redo) {
+                const int src = __ffs(redo) - 1;
+                redo &= redo - 1;
+                const int64_t v_lo = (g0 + src * W) << kGreedySegLog, v_hi = min(a.n, v_lo + kGreedySeg);
+                KeyId r{0, 0xFFFFFFFFu, 0};
+                // four of the lane's vertices per pass, their loads issued together
+                for (int64_t v0 = v_lo + lane; v0 < v_hi; v0 += 128) {
+                    uint8_t in4[4];
+                    uint32_t d4[4];
+                    uint64_t w4[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t v = v0 + q * stride;
-                in4[q] = 1;
-                if (v < a.n) {
-                    in4[q] = a.inS[v];
-                    d4[q] = __ldcg(a.delta + v);
-                    w4[q] = a.w[v];
+                    for (int q = 0; q < 4; ++q) {
+                        const int64_t v = v0 + 32 * q;
+                        in4[q] = 1;
+                        if (v < v_hi) {
+                            in4[q] = __ldcg(a.inS + v);
+                            d4[q] = __ldcg(a.delta + v);
+                            w4[q] = a.w[v];
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (in4[q]) continue;
+                        const u128 dv = (u128)d4[q];
+                        const KeyId c{a.ris ? dv : dv * a.W + (u128)a.T * (one_f - w4[q]), (uint32_t)(v0 + 32 * q),
+                                      1u, d4[q], 0u};
+                        if (better(c, r)) r = c;
+                    }
                 }
-            }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (in4[q]) continue;
-                const u128 dv = (u128)d4[q];
-                const KeyId c{a.ris ? dv : dv * a.W + (u128)a.T * (one_f - w4[q]), (uint32_t)(v0 + q * stride), 1u,
-                              d4[q], 0u};
-                if (better(c, best)) best = c;
+                for (int d = 16; d > 0; d >>= 1) {
+                    const KeyId o = shfl_down_keyid(r, d);
+                    if (better(o, r)) r = o;
+                }
+                r = shfl_keyid(r, 0);
+                if (lane == src) b = r;
+                if (lane == 0) a.seg_best[g0 + src * W] = r;
             }
+            if (better(b, wbest)) wbest = b;
         }
-        best = block_best(best, s_part);
-        if (threadIdx.x == 0) s_best = best;
-        } else {
-            best = s_best;
-        }
+        const KeyId best = block_best(wbest, s_part);
         if (threadIdx.x == 0) a.partial[blockIdx.x] = best;
         grid.sync();
         if (wib == 0) {
@@ -912,9 +940,8 @@ __global__ void __launch_bounds__(kGreedyThreads, 1) k_greedy_rounds(GreedyArgs 
         __syncthreads();
         const uint32_t v = s_win.id;
         if (threadIdx.x == 0) {
-            const int64_t owner = (int64_t)(v % (uint64_t)stride) / blockDim.x;
-            if (owner == blockIdx.x) a.inS[v] = 1;
             if (blockIdx.x == 0) {
+                a.inS[v] = 1;  // read (through L2) after the round's last grid barrier
                 cov += s_win.d;  // Delta_v as scanned, before any walk of this round
                 sum_c += one_f - a.w[v];
                 a.seeds[round] = (int32_t)v;
@@ -1038,6 +1065,7 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
     uint32_t *delta = nullptr, *covered = nullptr;
     uint8_t* inS = nullptr;
     KeyId* partial = nullptr;
+    KeyId* seg_best = nullptr;
     int32_t* d_seeds = nullptr;
     int64_t* d_cov = nullptr;
     double* d_est = nullptr;
@@ -1053,6 +1081,8 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
         CV_CUDA(dev_alloc_t(&inS, (size_t)n, st));
         CV_CUDA(dev_alloc_t(&covered, (size_t)((T + 31) / 32), st));
         CV_CUDA(dev_alloc_t(&partial, (size_t)gblocks, st));
+        const int64_t nseg = (n + kGreedySeg - 1) / kGreedySeg;
+        CV_CUDA(dev_alloc_t(&seg_best, (size_t)nseg, st));
         CV_CUDA(dev_alloc_t(&d_seeds, (size_t)k, st));
         CV_CUDA(dev_alloc_t(&d_cov, (size_t)k, st));
         CV_CUDA(dev_alloc_t(&d_est, (size_t)k, st));
@@ -1078,6 +1108,8 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
         ga.arena = s->arena;
         ga.covered = covered;
         ga.partial = partial;
+        ga.seg_best = seg_best;
+        ga.nseg = nseg;
         ga.seeds = d_seeds;
         ga.cov_out = d_cov;
         ga.est_out = d_est;
@@ -1096,6 +1128,7 @@ int sketch_greedy(skis_sketch* s, int32_t k, int32_t* h_seeds, int64_t* h_cov, d
     dev_free(covered, st);
     dev_free(inS, st);
     dev_free(partial, st);
+    dev_free(seg_best, st);
     dev_free(d_seeds, st);
     dev_free(d_cov, st);
     dev_free(d_est, st);

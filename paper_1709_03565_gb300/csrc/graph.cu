@@ -43,16 +43,6 @@ __global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __res
     }
 }
 
-// Sort key (dst, src) packed as dst << src_bits | src; the value is the input
-// index, so the stable sort breaks ties by input order.
-__global__ void k_make_keys(const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int64_t m,
-                            int src_bits, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
-        keys[e] = ((uint64_t)(uint32_t)dst[e] << src_bits) | (uint64_t)(uint32_t)src[e];
-        vals[e] = (uint32_t)e;
-    }
-}
-
 // Row offsets of the canonical CSR from the sorted keys: off[v] is the first
 // position whose destination is >= v. Position e writes off[v] for the
 // destinations v in (dst(e - 1), dst(e)], and the last position the ones
@@ -108,9 +98,6 @@ __global__ void k_rows(const uint64_t* __restrict__ off, int64_t n, int wc, RowI
     }
 }
 
-// Eq. gamma_v in fixed point: Q = 2^62; Q <- floor(Q (2^32 - tau) / 2^32) for
-// each in-edge in CSR order (0 on a sentinel); w_v = (2^62 - Q) >> s. With
-// chain != nullptr the running Q after every in-edge is kept as well.
 // One step of the fixed-point chain, Q <- floor(Q (2^32 - t) / 2^32) for
 // Q < 2^62 (0 for the sentinel). With Q = qh 2^32 + ql and c = 2^32 - t,
 // the floor is exactly qh c + floor(ql c / 2^32): two independent 32-bit
@@ -123,62 +110,156 @@ __device__ __forceinline__ uint64_t chain_step(uint64_t Q, uint32_t t) {
     return (uint64_t)(uint32_t)(Q >> 32) * c + __umulhi((uint32_t)Q, c);
 }
 
+// Eq. gamma_v in fixed point for one row: Q = 2^62; Q <- floor(Q (2^32 -
+// tau) / 2^32) for each in-edge in CSR order (0 on a sentinel); the caller
+// takes w_v = (2^62 - Q) >> s from the returned last value. With chain !=
+// nullptr the running Q after every in-edge is kept as well.
+__device__ __forceinline__ uint64_t gamma_row(const RowInfo& r, const uint32_t* __restrict__ csr_tau,
+                                              uint64_t* __restrict__ chain) {
+    uint64_t Q = 1ull << 62;
+    uint32_t k = 0;
+    if (!csr_tau) {  // one threshold for the row (weighted cascade)
+        const uint32_t t = r.tau;
+        if (t == kSentinel || t == 0) {  // every step gives 0, or keeps Q
+            const uint64_t q = (t == kSentinel && r.deg) ? 0 : Q;
+            if (chain)
+                for (; k < r.deg; ++k) chain[r.off + k] = q;
+            return q;
+        }
+        // a pure dependent chain of Q <- qh c + hi32(ql c), four steps an
+        // iteration, their values stored two to a 16-byte store when the
+        // position is even (the chain array is 16-byte aligned)
+        const uint32_t c = (uint32_t)(0x100000000ull - t);
+        auto step = [c](uint64_t q) { return (uint64_t)(uint32_t)(q >> 32) * c + __umulhi((uint32_t)q, c); };
+        if (chain && ((r.off + k) & 1) && k < r.deg) {
+            Q = step(Q);
+            chain[r.off + k] = Q;
+            ++k;
+        }
+        for (; k + 4 <= r.deg && (Q != 0 || chain); k += 4) {
+            const uint64_t q1 = step(Q), q2 = step(q1), q3 = step(q2), q4 = step(q3);
+            if (chain) {
+                ulonglong2* p = reinterpret_cast<ulonglong2*>(chain + r.off + k);
+                p[0] = make_ulonglong2(q1, q2);
+                p[1] = make_ulonglong2(q3, q4);
+            }
+            Q = q4;
+        }
+        for (; k < r.deg && (Q != 0 || chain); ++k) {
+            Q = step(Q);
+            if (chain) chain[r.off + k] = Q;
+        }
+        return Q;
+    }
+    for (; k + 8 <= r.deg && (Q != 0 || chain); k += 8) {
+        uint32_t t[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = csr_tau[r.off + k + i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            Q = chain_step(Q, t[i]);
+            if (chain) chain[r.off + k + i] = Q;
+        }
+    }
+    for (; k < r.deg && (Q != 0 || chain); ++k) {
+        Q = chain_step(Q, csr_tau[r.off + k]);
+        if (chain) chain[r.off + k] = Q;
+    }
+    return Q;
+}
+
+// Rows by the bit length of their degree (class b: 2^(b-1) <= d_in < 2^b;
+// class 0: no in-edge). A graph with no row of 2^15 in-edges or more walks
+// every chain in row order, one a thread, with coalesced row reads and chain
+// stores. Otherwise the rows below class kGammaMidClass (under 2^10
+// in-edges) still go in row order; the longer ones are ordered by class, so
+// that the threads of a warp walk chains of similar length (the order within
+// a class is arbitrary: rows are independent), and classes from
+// kGammaLongClass up run one row a thread in one-warp blocks: such a chain is
+// one dependent sequence of up to ~10^6 steps, and a thread walking it among
+// warps busy with short rows would wait for issue slots at every step.
+constexpr int kGammaClasses = 33;
+constexpr int kGammaMidClass = 11;
+constexpr int kGammaLongClass = 16;
+constexpr int kGammaOrderItems = 8;
+
+__device__ __forceinline__ int row_class(uint32_t deg) { return deg ? 32 - __clz(deg) : 0; }
+
+__global__ void k_row_class_count(const RowInfo* __restrict__ rows, int64_t n,
+                                  unsigned long long* __restrict__ cls) {
+    __shared__ unsigned int s_c[kGammaClasses];
+    if (threadIdx.x < kGammaClasses) s_c[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int c = row_class(rows[v].deg);
+        if (c >= kGammaMidClass) atomicAdd(&s_c[c], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kGammaClasses && s_c[threadIdx.x]) atomicAdd(&cls[threadIdx.x], (unsigned long long)s_c[threadIdx.x]);
+}
+
+// class counts -> class starts (exclusive, in place); cls[kGammaClasses] =
+// the number of ordered rows
+__global__ void k_row_class_starts(unsigned long long* __restrict__ cls) {
+    unsigned long long run = 0;
+    for (int c = 0; c < kGammaClasses; ++c) {
+        const unsigned long long x = cls[c];
+        cls[c] = run;
+        run += x;
+    }
+    cls[kGammaClasses] = run;
+}
+
+// order[cursor[class]++] = v for the rows of classes kGammaMidClass and up,
+// the cursors advanced once per class and chunk of 256 x kGammaOrderItems rows
+__global__ void __launch_bounds__(256) k_row_class_order(const RowInfo* __restrict__ rows, int64_t n,
+                                                         unsigned long long* __restrict__ cursor,
+                                                         uint32_t* __restrict__ order) {
+    __shared__ unsigned int s_c[kGammaClasses];
+    __shared__ unsigned long long s_base[kGammaClasses];
+    constexpr int64_t chunk = 256 * kGammaOrderItems;
+    for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < n; c0 += (int64_t)gridDim.x * chunk) {
+        if (threadIdx.x < kGammaClasses) s_c[threadIdx.x] = 0;
+        __syncthreads();
+        int cl[kGammaOrderItems];
+        unsigned int at[kGammaOrderItems];
+#pragma unroll
+        for (int i = 0; i < kGammaOrderItems; ++i) {
+            const int64_t v = c0 + i * 256 + threadIdx.x;
+            cl[i] = v < n ? row_class(rows[v].deg) : -1;
+            if (cl[i] < kGammaMidClass) cl[i] = -1;
+            at[i] = cl[i] >= 0 ? atomicAdd(&s_c[cl[i]], 1u) : 0;
+        }
+        __syncthreads();
+        if (threadIdx.x < kGammaClasses)
+            s_base[threadIdx.x] = s_c[threadIdx.x] ? atomicAdd(&cursor[threadIdx.x], (unsigned long long)s_c[threadIdx.x]) : 0;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kGammaOrderItems; ++i)
+            if (cl[i] >= 0) order[s_base[cl[i]] + at[i]] = (uint32_t)(c0 + i * 256 + threadIdx.x);
+        __syncthreads();
+    }
+}
+
+// w_v = (2^62 - Q_d) >> s for the rows below class c_end, in row order
 __global__ void k_gamma(const RowInfo* __restrict__ rows, const uint32_t* __restrict__ csr_tau, int64_t n, int s,
-                        uint64_t* __restrict__ w, uint64_t* __restrict__ chain) {
-    const uint64_t one62 = 1ull << 62;
+                        uint64_t* __restrict__ w, uint64_t* __restrict__ chain, int c_end) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const RowInfo r = rows[v];
-        uint64_t Q = one62;
-        uint32_t k = 0;
-        if (!csr_tau) {  // one threshold for the row (weighted cascade)
-            const uint32_t t = r.tau;
-            if (t == kSentinel || t == 0) {  // every step gives 0, or keeps Q
-                const uint64_t q = (t == kSentinel && r.deg) ? 0 : Q;
-                if (chain)
-                    for (; k < r.deg; ++k) chain[r.off + k] = q;
-                Q = q;
-            } else {
-                // a pure dependent chain of Q <- qh c + hi32(ql c), four steps an
-                // iteration, their values stored two to a 16-byte store when the
-                // position is even (the chain array is 16-byte aligned)
-                const uint32_t c = (uint32_t)(0x100000000ull - t);
-                auto step = [c](uint64_t q) { return (uint64_t)(uint32_t)(q >> 32) * c + __umulhi((uint32_t)q, c); };
-                if (chain && ((r.off + k) & 1) && k < r.deg) {
-                    Q = step(Q);
-                    chain[r.off + k] = Q;
-                    ++k;
-                }
-                for (; k + 4 <= r.deg && (Q != 0 || chain); k += 4) {
-                    const uint64_t q1 = step(Q), q2 = step(q1), q3 = step(q2), q4 = step(q3);
-                    if (chain) {
-                        ulonglong2* p = reinterpret_cast<ulonglong2*>(chain + r.off + k);
-                        p[0] = make_ulonglong2(q1, q2);
-                        p[1] = make_ulonglong2(q3, q4);
-                    }
-                    Q = q4;
-                }
-                for (; k < r.deg && (Q != 0 || chain); ++k) {
-                    Q = step(Q);
-                    if (chain) chain[r.off + k] = Q;
-                }
-            }
-        } else {
-            for (; k + 8 <= r.deg && (Q != 0 || chain); k += 8) {
-                uint32_t t[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) t[i] = csr_tau[r.off + k + i];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    Q = chain_step(Q, t[i]);
-                    if (chain) chain[r.off + k + i] = Q;
-                }
-            }
-            for (; k < r.deg && (Q != 0 || chain); ++k) {
-                Q = chain_step(Q, csr_tau[r.off + k]);
-                if (chain) chain[r.off + k] = Q;
-            }
-        }
-        w[v] = (one62 - Q) >> s;
+        if (row_class(r.deg) < c_end) w[v] = ((1ull << 62) - gamma_row(r, csr_tau, chain)) >> s;
+    }
+}
+
+// the same for the ordered rows order[starts[c_lo] .. starts[c_hi]); one-warp
+// blocks for the long classes
+__global__ void k_gamma_ordered(const RowInfo* __restrict__ rows, const uint32_t* __restrict__ csr_tau, int s,
+                                uint64_t* __restrict__ w, uint64_t* __restrict__ chain,
+                                const uint32_t* __restrict__ order, const unsigned long long* __restrict__ starts,
+                                int c_lo, int c_hi) {
+    const int64_t lo = (int64_t)starts[c_lo], hi = (int64_t)starts[c_hi];
+    for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = order[i];
+        w[v] = ((1ull << 62) - gamma_row(rows[v], csr_tau, chain)) >> s;
     }
 }
 
@@ -341,12 +422,11 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     const int64_t n = g->n, m = g->m;
     const int grid = sm_count() * 8, block = 256;
     const int src_bits = bits_for(n);
-    const int key_bits = 2 * src_bits;
     // temporaries
     DevStatus* d_status = nullptr;
     unsigned long long* d_W = nullptr;
-    uint64_t *keys = nullptr, *keys_s = nullptr, *keys_alt = nullptr;
-    uint32_t *vals = nullptr, *vals_s = nullptr, *vals_alt = nullptr;
+    uint64_t *keys_s = nullptr, *keys_alt = nullptr;
+    uint32_t *vals_s = nullptr, *vals_alt = nullptr;
     uint32_t *is_light = nullptr, *light_ids = nullptr, *heavy_ids = nullptr;
     uint64_t* light_idx = nullptr;
     u128 *deficit = nullptr, *excess = nullptr, *D = nullptr, *Ex = nullptr;
@@ -358,6 +438,8 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     g->f = g->lt ? 32 : 62 - g->s;
     g->row_uniform = (model == SKIS_W_WC);
     uint64_t* lt_w = nullptr;
+    uint32_t* row_order = nullptr;
+    unsigned long long* class_starts = nullptr;
     g->m_pad = ((m + 3) / 4) * 4 + 4;
 
     GB_CUDA(dev_alloc_t(&d_status, 1, st));
@@ -389,15 +471,11 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     GB_CUDA(dev_alloc_t(&g->w, (size_t)n, st));
     GB_CUDA(dev_alloc_t(&g->alias, (size_t)n, st));
     if (m > 0) {
-        GB_CUDA(dev_alloc_t(&keys, (size_t)m, st));
         GB_CUDA(dev_alloc_t(&keys_s, (size_t)m, st));
         GB_CUDA(dev_alloc_t(&keys_alt, (size_t)m, st));
-        GB_CUDA(dev_alloc_t(&vals, (size_t)m, st));
         GB_CUDA(dev_alloc_t(&vals_s, (size_t)m, st));
         GB_CUDA(dev_alloc_t(&vals_alt, (size_t)m, st));
-        k_make_keys<<<grid, block, 0, st>>>(d_src, d_dst, m, src_bits, keys, vals); note_launch();
-        GB_CUDA(cudaGetLastError());
-        GB_CUDA(radix_sort_pairs(keys, vals, keys_s, vals_s, keys_alt, vals_alt, m, key_bits, st));
+        GB_CUDA(sort_edges(d_src, d_dst, m, src_bits, keys_s, vals_s, keys_alt, vals_alt, &d_status->gave_up, st));
     }
     k_offsets_from_keys<<<grid, block, 0, st>>>(keys_s, m, n, src_bits, g->off); note_launch();
     GB_CUDA(cudaGetLastError());
@@ -429,7 +507,30 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     } else {
         // the chain is kept for the bucket form of the first step (8 bytes an edge)
         if (m > 0) GB_CUDA(dev_alloc_t(&g->chain, (size_t)m, st));
-        k_gamma<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->s, g->w, g->chain); note_launch();
+        // the rows' degree classes; with no long row, every chain in row
+        // order; else the short chains in row order, then the ordered
+        // middle classes, then the long rows
+        unsigned long long h_starts[kGammaClasses + 1];
+        GB_CUDA(dev_alloc_t(&class_starts, (size_t)2 * (kGammaClasses + 1), st));
+        unsigned long long* class_cursor = class_starts + kGammaClasses + 1;
+        GB_CUDA(cudaMemsetAsync(class_starts, 0, (kGammaClasses + 1) * sizeof(unsigned long long), st));
+        k_row_class_count<<<grid, block, 0, st>>>(g->rows, n, class_starts); note_launch();
+        k_row_class_starts<<<1, 1, 0, st>>>(class_starts); note_launch();
+        GB_CUDA(cudaMemcpyAsync(h_starts, class_starts, sizeof(h_starts), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        if (h_starts[kGammaLongClass] == h_starts[kGammaClasses]) {
+            k_gamma<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->s, g->w, g->chain, kGammaClasses); note_launch();
+        } else {
+            GB_CUDA(dev_alloc_t(&row_order, (size_t)h_starts[kGammaClasses], st));
+            GB_CUDA(cudaMemcpyAsync(class_cursor, class_starts, (kGammaClasses + 1) * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToDevice, st));
+            k_row_class_order<<<grid, 256, 0, st>>>(g->rows, n, class_cursor, row_order); note_launch();
+            k_gamma<<<grid, block, 0, st>>>(g->rows, g->tau, n, g->s, g->w, g->chain, kGammaMidClass); note_launch();
+            k_gamma_ordered<<<grid, block, 0, st>>>(g->rows, g->tau, g->s, g->w, g->chain, row_order, class_starts,
+                                                    kGammaMidClass, kGammaLongClass); note_launch();
+            k_gamma_ordered<<<sm_count() * 4, 32, 0, st>>>(g->rows, g->tau, g->s, g->w, g->chain, row_order,
+                                                           class_starts, kGammaLongClass, kGammaClasses); note_launch();
+        }
         GB_CUDA(cudaGetLastError());
     }
     GB_CUDA(sum_u64(g->w, n, d_W, st));
@@ -442,7 +543,13 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     GB_CUDA(scan_u32_to_u64(is_light, light_idx, n, st));
     GB_CUDA(cudaMemcpyAsync(&nl, light_idx + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaMemcpyAsync(&g->W, d_W, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(&h_status, d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaStreamSynchronize(st));
+    if (h_status.gave_up) {
+        *err = "skis_load_graph: the edge sort failed an internal check (look-back wait or output bounds)";
+        rc = SKIS_ERR_INTERNAL;
+        goto cleanup;
+    }
     nh = (uint64_t)n - nl;
     if (g->W == 0) {
         k_alias_empty<<<grid, block, 0, st>>>(n, g->alias); note_launch();
@@ -470,12 +577,12 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
 
 cleanup:
     dev_free(lt_w, st);
+    dev_free(row_order, st);
+    dev_free(class_starts, st);
     dev_free(d_status, st);
     dev_free(d_W, st);
-    dev_free(keys, st);
     dev_free(keys_s, st);
     dev_free(keys_alt, st);
-    dev_free(vals, st);
     dev_free(vals_s, st);
     dev_free(vals_alt, st);
     dev_free(is_light, st);

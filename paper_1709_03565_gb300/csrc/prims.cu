@@ -1,6 +1,7 @@
 // Device primitives used while building the graph and the greedy index:
 // stream-ordered allocation, exclusive prefix sums (u32->u64, u64, u128),
-// a stable LSD radix sort of (u64 key, u32 value) pairs, and a u64 sum.
+// a stable LSD radix sort of the edges by (destination, source), and a u64
+// sum.
 #include <algorithm>
 #include <atomic>
 #include <mutex>
@@ -170,46 +171,145 @@ cudaError_t scan_u128(const u128* in, u128* out, int64_t n, cudaStream_t st) {
     return scan_impl<u128, u128>(in, out, n, st);
 }
 
-// ------------------------------------------------------------- radix sort
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;  // 2048 pairs per tile
-constexpr int kSortTile = kSortThreads * kSortItems;
+// ------------------------------------------------------------- edge sort
+// Stable LSD radix sort of the edges by key dst << src_bits | src, the input
+// index as value (so equal keys keep input order), in 8-bit digits. One
+// kernel reads the edges once and counts every digit of every pass; then one
+// kernel a pass ("onesweep"): each CTA claims the next tile from a ticket,
+// ranks its items per warp (match_any, warp-striped loads: positions in warp
+// order, so the ranking is stable), publishes the tile's per-digit counts and
+// looks back over the previous tiles' published counts for its global
+// offsets (decoupled look-back), then writes the tile out through shared
+// memory in digit order, so that each digit's items leave as a contiguous
+// run. The first pass builds the keys from the edge arrays in registers.
+constexpr int kOsThreads = 256;
+constexpr int kOsItems = 16;
+constexpr int kOsTile = kOsThreads * kOsItems;  // 4096 items
+constexpr int kOsWarps = kOsThreads / 32;
+constexpr int kOsMaxPasses = 8;
+// status word of (tile, digit): state in bits 62-63 (1: the tile's own
+// count, 2: inclusive prefix over tiles 0 .. tile), the pass tag (pass + 1)
+// in bits 56-61, the count in bits 0-55. Words of another pass read as not
+// yet published, so one zeroing serves every pass.
+constexpr unsigned long long kOsAgg = 1ull << 62, kOsIncl = 2ull << 62;
+constexpr unsigned long long kOsCount = (1ull << 56) - 1;
+constexpr uint32_t kOsSpinLimit = 1u << 22;  // polls of one word before giving up (~0.3 s)
+constexpr int kOsWindow = 8;                 // predecessor tiles read at once in the look-back
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys, int64_t n,
-                                                             int shift, uint32_t* __restrict__ hist,
-                                                             int nblocks) {
-    __shared__ uint32_t s_h[256];
-    s_h[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    for (int c = 0; c < kSortItems; ++c) {
-        const int64_t i = base + (int64_t)c * kSortThreads + threadIdx.x;
-        if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_h[threadIdx.x];
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Stable scatter of one tile. The tile's items are ranked in order (chunks
-// of 256; within a chunk warp w precedes warp w+1 and lanes rank by lane id
-// among equal digits) and placed in shared memory in digit order; then the
-// tile is written out from shared memory, so that the items of one digit
-// leave as one contiguous run (coalesced) at the digit's global base.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+__device__ __forceinline__ uint64_t edge_key(const int32_t* src, const int32_t* dst, int64_t e, int src_bits) {
+    return ((uint64_t)(uint32_t)dst[e] << src_bits) | (uint64_t)(uint32_t)src[e];
+}
+
+// Digit counts of every pass: hist[p * 256 + d] = #{edges whose key has
+// digit d in pass p}.
+__global__ void __launch_bounds__(256) k_os_hist(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                                                 int64_t m, int src_bits, int passes,
+                                                 unsigned long long* __restrict__ hist) {
+    __shared__ uint32_t s_h[kOsMaxPasses * 256];
+    for (int i = threadIdx.x; i < passes * 256; i += 256) s_h[i] = 0;
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = edge_key(src, dst, e, src_bits);
+        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (uint32_t)((key >> (8 * p)) & 255u)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += 256)
+        if (s_h[i]) atomicAdd(&hist[i], (unsigned long long)s_h[i]);
+}
+
+// Exclusive prefix of each pass's digit counts, in place: base[p * 256 + d].
+__global__ void k_os_bases(unsigned long long* __restrict__ hist, int passes) {
+    __shared__ unsigned long long s_c[256];
+    for (int p = 0; p < passes; ++p) {
+        s_c[threadIdx.x] = hist[p * 256 + threadIdx.x];
+        __syncthreads();
+        unsigned long long b = 0;
+        for (int d = 0; d < (int)threadIdx.x; ++d) b += s_c[d];
+        hist[p * 256 + threadIdx.x] = b;
+        __syncthreads();
+    }
+}
+
+// One pass on digit `shift / 8`. kFirst: the items are the edges (key built
+// from src / dst, value = input index). Dynamic shared memory: kOsTile keys
+// and values.
+template <bool kFirst>
+__global__ void __launch_bounds__(kOsThreads, 3) k_os_pass(
+    const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int src_bits,
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out, int64_t n, int shift, const uint32_t* __restrict__ hist,
-    const uint64_t* __restrict__ offs, int nblocks) {
-    __shared__ uint64_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
-    __shared__ uint32_t s_wcnt[kSortThreads / 32][256];
-    __shared__ uint32_t s_start[256];  // digit start within the tile
-    __shared__ uint32_t s_run[256];    // items of the digit placed so far
-    __shared__ uint32_t s_wsum[kSortThreads / 32];
-    __shared__ uint64_t s_base[256];
+    uint32_t* __restrict__ vals_out, int64_t n, int shift, unsigned long long tag,
+    const unsigned long long* __restrict__ base, unsigned long long* __restrict__ status,
+    unsigned int* __restrict__ ticket, unsigned int* __restrict__ gave_up) {
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    uint64_t* s_keys = reinterpret_cast<uint64_t*>(os_smem);
+    uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kOsTile);
+    __shared__ uint32_t s_wcnt[kOsWarps][256];  // per warp: digit counts, then the warp's start in the digit
+    __shared__ uint32_t s_tstart[256];          // digit start within the tile
+    __shared__ unsigned long long s_gbase[256]; // output position of the digit's first item of the tile
+    __shared__ uint32_t s_wsum[kOsWarps];
+    __shared__ uint32_t s_tile, s_bad;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    s_base[tid] = offs[(int64_t)tid * nblocks + blockIdx.x];
-    // exclusive scan of this tile's digit counts
-    const uint32_t cnt = hist[(int64_t)tid * nblocks + blockIdx.x];
+    if (tid == 0) {
+        s_tile = atomicAdd(ticket, 1u);
+        s_bad = 0;
+    }
+    const unsigned long long digit_base = base[tid];  // in flight while the tile loads
+#pragma unroll
+    for (int w = 0; w < kOsWarps; ++w) s_wcnt[w][tid] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t t0 = (int64_t)tile * kOsTile;
+    const int64_t wb = t0 + (int64_t)wid * (32 * kOsItems);
+    uint64_t key[kOsItems];
+    uint32_t val[kOsItems], rnk[kOsItems];
+#pragma unroll
+    for (int c = 0; c < kOsItems; ++c) {
+        const int64_t i = wb + c * 32 + lane;
+        if (kFirst) {
+            key[c] = i < n ? edge_key(src, dst, i, src_bits) : 0;
+            val[c] = (uint32_t)i;
+        } else {
+            key[c] = i < n ? keys_in[i] : 0;
+            val[c] = i < n ? vals_in[i] : 0;
+        }
+    }
+    // rank within the warp: earlier chunks, then lower lanes
+#pragma unroll
+    for (int c = 0; c < kOsItems; ++c) {
+        const bool valid = wb + c * 32 + lane < n;
+        const uint32_t d = valid ? (uint32_t)((key[c] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t before = 0;
+        if (lane == leader && valid) {
+            before = s_wcnt[wid][d];
+            s_wcnt[wid][d] = before + (uint32_t)__popc(peers);
+        }
+        __syncwarp();  // this chunk's counts are in before the next chunk's leaders read them
+        before = __shfl_sync(kFull, before, leader);
+        rnk[c] = before + (uint32_t)__popc(peers & lanemask_lt());
+    }
+    __syncthreads();
+    // thread tid owns digit tid: the tile's count and each warp's start
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kOsWarps; ++w) {
+        const uint32_t c2 = s_wcnt[w][tid];
+        s_wcnt[w][tid] = cnt;
+        cnt += c2;
+    }
+    unsigned long long* my = status + (size_t)tile * 256 + tid;
+    st_relaxed_u64(my, (tile == 0 ? kOsIncl : kOsAgg) | tag | cnt);
+    // tile-local digit starts (exclusive scan of cnt over the block)
     uint32_t x = cnt;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -217,87 +317,128 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         if (lane >= d) x += y;
     }
     if (lane == 31) s_wsum[wid] = x;
+    // look back over the earlier tiles for this digit's items before the
+    // tile, kOsWindow tiles a read: sum their own counts back to the first
+    // inclusive prefix, waiting on the first tile not yet published
+    unsigned long long excl = 0;
+    if (tile > 0) {
+        int64_t t = (int64_t)tile - 1;  // the next tile to account for
+        uint32_t spins = 0;
+        bool done = false;
+        while (!done) {
+            unsigned long long v[kOsWindow];
 #pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][tid] = 0;
-    s_run[tid] = 0;
+            for (int k = 0; k < kOsWindow; ++k)
+                v[k] = t - k >= 0 ? ld_relaxed_u64(status + (size_t)(t - k) * 256 + tid) : 0;
+            int k = 0;
+#pragma unroll
+            for (int q = 0; q < kOsWindow; ++q) {
+                const bool ready = (v[q] & (63ull << 56)) == tag && (v[q] >> 62) != 0;
+                if (!ready) break;
+                excl += v[q] & kOsCount;
+                ++k;
+                if ((v[q] >> 62) == 2) {
+                    done = true;
+                    break;
+                }
+            }
+            if (done) break;
+            t -= k;  // tile 0 is always inclusive, so t stays >= 0
+            if (k < kOsWindow) {  // tile t is not published yet
+                if (++spins > kOsSpinLimit) {  // cannot happen while every claimed tile runs; never hang
+                    atomicOr(gave_up, 1u);
+                    s_bad = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        st_relaxed_u64(my, kOsIncl | tag | ((excl + cnt) & kOsCount));
+    }
+    s_gbase[tid] = digit_base + excl;
     __syncthreads();
     uint32_t before = 0;
     for (int w = 0; w < wid; ++w) before += s_wsum[w];
-    s_start[tid] = before + x - cnt;
+    s_tstart[tid] = before + x - cnt;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile;
-    const int tile_n = (int)min((int64_t)kSortTile, n - base);
-    for (int c = 0; c < kSortItems; ++c) {
-        const int64_t i = base + (int64_t)c * kSortThreads + tid;
-        const bool valid = i < n;
-        const uint64_t key = valid ? keys_in[i] : 0;
-        const uint32_t val = valid ? vals_in[i] : 0;
-        const uint32_t d = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
-        const unsigned peers = __match_any_sync(kFull, d);
-        const int rank = __popc(peers & lanemask_lt());
-        if (valid && lane == __ffs(peers) - 1) s_wcnt[wid][d] = (uint32_t)__popc(peers);
-        __syncthreads();
-        uint32_t run = 0;  // thread tid: digit tid's per-warp offsets within the chunk
+    // the tile in shared memory in digit order
 #pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) {
-            const uint32_t c2 = s_wcnt[w][tid];
-            s_wcnt[w][tid] = run;
-            run += c2;
+    for (int c = 0; c < kOsItems; ++c) {
+        if (wb + c * 32 + lane < n) {
+            const uint32_t d = (uint32_t)((key[c] >> shift) & 255u);
+            const uint32_t pos = s_tstart[d] + s_wcnt[wid][d] + rnk[c];
+            s_keys[pos] = key[c];
+            s_vals[pos] = val[c];
         }
-        __syncthreads();
-        if (valid) {
-            const uint32_t pos = s_start[d] + s_run[d] + s_wcnt[wid][d] + (uint32_t)rank;
-            s_keys[pos] = key;
-            s_vals[pos] = val;
-        }
-        __syncthreads();
-        s_run[tid] += run;
-#pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) s_wcnt[w][tid] = 0;
-        __syncthreads();
     }
-    for (int i = tid; i < tile_n; i += kSortThreads) {
-        const uint64_t key = s_keys[i];
-        const uint32_t d = (uint32_t)((key >> shift) & 255u);
-        const uint64_t pos = s_base[d] + (uint64_t)(i - (int)s_start[d]);
-        keys_out[pos] = key;
-        vals_out[pos] = s_vals[i];
+    __syncthreads();
+    if (s_bad) return;  // offsets unknown: write nothing (the host reports the failure)
+    const int tile_n = (int)min((int64_t)kOsTile, n - t0);
+    for (int i = tid; i < tile_n; i += kOsThreads) {
+        const uint64_t k = s_keys[i];
+        const uint32_t d = (uint32_t)((k >> shift) & 255u);
+        const unsigned long long g = s_gbase[d] + (unsigned long long)(i - (int)s_tstart[d]);
+        if (g >= (unsigned long long)n) {  // inconsistent counts (cannot happen): never write out of bounds
+            atomicOr(gave_up, 2u);
+            continue;
+        }
+        keys_out[g] = k;
+        vals_out[g] = s_vals[i];
     }
 }
 
-cudaError_t radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
-                             uint32_t* vals_out, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                             int bits, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    const int passes = (bits + 7) / 8;
-    if (passes == 0) {
-        cudaError_t e = cudaMemcpyAsync(keys_out, keys_in, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return e;
-        return cudaMemcpyAsync(vals_out, vals_in, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int src_bits, uint64_t* keys_out,
+                       uint32_t* vals_out, uint64_t* keys_alt, uint32_t* vals_alt, unsigned int* gave_up,
+                       cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    const int passes = std::max(1, (2 * src_bits + 7) / 8);
+    if (passes > kOsMaxPasses) return cudaErrorInvalidValue;
+    const int64_t ntiles = (m + kOsTile - 1) / kOsTile;
+    const size_t smem = (size_t)kOsTile * (sizeof(uint64_t) + sizeof(uint32_t));
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [smem] {
+        attr_err = cudaFuncSetAttribute(k_os_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(k_os_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    unsigned long long *hist = nullptr, *status = nullptr;
+    unsigned int* tickets = nullptr;
+    cudaError_t e = dev_alloc_t(&hist, (size_t)passes * 256, st);
+    if (e == cudaSuccess) e = dev_alloc_t(&status, (size_t)ntiles * 256, st);
+    if (e == cudaSuccess) e = dev_alloc_t(&tickets, (size_t)passes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (size_t)passes * 256 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, (size_t)ntiles * 256 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, (size_t)passes * sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+        const int grid = (int)std::min<int64_t>((int64_t)sm_count() * 8, std::max<int64_t>(1, (m + 255) / 256));
+        k_os_hist<<<grid, 256, 0, st>>>(src, dst, m, src_bits, passes, hist); note_launch();
+        k_os_bases<<<1, 256, 0, st>>>(hist, passes); note_launch();
+        e = cudaGetLastError();
     }
-    const int nb = div_up(n, kSortTile);
-    uint32_t* hist = nullptr;
-    uint64_t* offs = nullptr;
-    cudaError_t e = dev_alloc_t(&hist, (size_t)nb * 256, st);
-    if (e != cudaSuccess) return e;
-    e = dev_alloc_t(&offs, (size_t)nb * 256 + 1, st);
-    if (e != cudaSuccess) { dev_free(hist, st); return e; }
-    const uint64_t* ksrc = keys_in;
-    const uint32_t* vsrc = vals_in;
+    const uint64_t* ksrc = nullptr;
+    const uint32_t* vsrc = nullptr;
     for (int p = 0; p < passes && e == cudaSuccess; ++p) {
         const bool to_out = ((passes - 1 - p) % 2) == 0;
         uint64_t* kdst = to_out ? keys_out : keys_alt;
         uint32_t* vdst = to_out ? vals_out : vals_alt;
-        k_radix_hist<<<nb, kSortThreads, 0, st>>>(ksrc, n, 8 * p, hist, nb); note_launch();
-        e = scan_u32_to_u64(hist, offs, (int64_t)nb * 256, st);
-        if (e != cudaSuccess) break;
-        k_radix_scatter<<<nb, kSortThreads, 0, st>>>(ksrc, vsrc, kdst, vdst, n, 8 * p, hist, offs, nb); note_launch();
+        const unsigned long long tag = (unsigned long long)(p + 1) << 56;
+        if (p == 0)
+            k_os_pass<true><<<(unsigned)ntiles, kOsThreads, smem, st>>>(src, dst, src_bits, nullptr, nullptr, kdst, vdst,
+                                                                      m, 0, tag, hist, status, tickets, gave_up);
+        else
+            k_os_pass<false><<<(unsigned)ntiles, kOsThreads, smem, st>>>(nullptr, nullptr, src_bits, ksrc, vsrc, kdst,
+                                                                       vdst, m, 8 * p, tag, hist + p * 256, status,
+                                                                       tickets + p, gave_up);
+        note_launch();
         e = cudaGetLastError();
         ksrc = kdst;
         vsrc = vdst;
     }
     dev_free(hist, st);
-    dev_free(offs, st);
+    dev_free(status, st);
+    dev_free(tickets, st);
     return e;
 }
 

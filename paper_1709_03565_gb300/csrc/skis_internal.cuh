@@ -39,7 +39,7 @@ struct __align__(16) AliasEntry {
 // Device status word shared by kernels that can fail on the data.
 struct DevStatus {
     unsigned int flags;
-    unsigned int pad;
+    unsigned int gave_up;          // a bounded device wait ran out (an invariant failed)
     unsigned long long first_bad;  // smallest failing index / sample id
 };
 enum : unsigned int {
@@ -225,12 +225,15 @@ cudaError_t scan_u32_to_u64(const uint32_t* in, uint64_t* out, int64_t n, cudaSt
 cudaError_t scan_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t st);
 cudaError_t scan_u128(const u128* in, u128* out, int64_t n, cudaStream_t st);
 
-// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
-// Results land in keys_out / vals_out; the *_alt buffers are scratch of the
-// same sizes.
-cudaError_t radix_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
-                             uint32_t* vals_out, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
-                             int bits, cudaStream_t st);
+// Stable sort of the m edges by key dst << src_bits | src (keys of
+// 2 src_bits bits), the input index as value: keys_out / vals_out receive the
+// sorted pairs; the *_alt buffers (m entries each) are scratch. *gave_up
+// (device word) is set nonzero if a look-back wait ran out (which only a
+// tile that never ran could cause) or an output position fell outside
+// [0, m); the result is then invalid and nothing was written out of bounds.
+cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int src_bits, uint64_t* keys_out,
+                       uint32_t* vals_out, uint64_t* keys_alt, uint32_t* vals_alt, unsigned int* gave_up,
+                       cudaStream_t st);
 
 // Sum of a uint64 array (integers: order-independent), result in *out (device).
 cudaError_t sum_u64(const uint64_t* in, int64_t n, unsigned long long* out, cudaStream_t st);
