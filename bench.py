@@ -230,18 +230,18 @@ def alu_peak_blocks_per_s(sms: int, mhz: float) -> float:
 def measured_alu_ceiling(skis, stream, sms: int, gpu_id: str) -> dict:
     """The coin generator's measured throughput on this GPU: the probe launch
     draws only Philox blocks (2048 threads per SM, 4096 blocks each, four
-    independent blocks a step) and counts the words below a threshold, with
-    no memory traffic. Per form (0: every block in full; 1: the hub loop's
+    independent blocks a step) and folds their words into one XOR, with no
+    memory traffic. Per form (0: every block in full; 1: the hub loop's
     per-sample hoisting) three warm-up launches, then 40 timed ones: best and
     median, with the SM clocks sampled over the timed launches."""
     threads, per = sms * 2048, 4096
     out = {"threads": threads, "blocks_per_launch": threads * per, "kernel": "k_philox_rate"}
     for form, name in ((0, "full_blocks"), (1, "hoisted_blocks")):
         for r in range(3):
-            skis.skis_philox_rate(1 + r, threads, per, 4295, form, stream=stream)
+            skis.skis_philox_rate(1 + r, threads, per, form, stream=stream)
         clocks = ClockSampler(gpu_id)
         clocks.start()
-        ms = sorted(skis.skis_philox_rate(1 + r, threads, per, 4295, form, stream=stream)[0] for r in range(40))
+        ms = sorted(skis.skis_philox_rate(1 + r, threads, per, form, stream=stream)[0] for r in range(40))
         out[name] = {"blocks_per_s": threads * per / (ms[0] / 1e3), "ms": ms[0],
                      "median_blocks_per_s": threads * per / (ms[len(ms) // 2] / 1e3), "clocks": clocks.stop()}
     return out

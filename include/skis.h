@@ -430,15 +430,15 @@ void skis_server_free(skis_server *srv);
  * probe, no counterpart in the paper): `threads` threads each draw the
  * Philox4x32-10 blocks of edge quads [t b, (t + 1) b) of sample id t (BFS
  * domain, key seed; b = blocks_per_thread), four independent blocks a step,
- * and count the coin words below tau, in one launch with no memory traffic
- * but one count per thread: form 0 computes every block as a sampler tier
- * does (20 products), form 1 as the CTA tier's hub loop does (two products
- * hoisted per sample, 18). ms_out receives the launch's device time,
- * live_out the count (it depends on the coins only). threads and
- * blocks_per_thread in [1, 2^31] with fewer than 2^32 blocks in all, form 0
- * or 1, else SKIS_EINVAL; synchronises the stream. */
-int skis_philox_rate(uint64_t seed, uint64_t threads, uint64_t blocks_per_thread, uint32_t tau, int form,
-                     double *ms_out, uint64_t *live_out, void *cuda_stream);
+ * and fold every word of every block into one XOR, in one launch with no
+ * memory traffic but one atomic per thread: form 0 computes every block as a
+ * sampler tier does (20 products), form 1 as the CTA tier's hub loop does
+ * (two products hoisted per sample, 18). ms_out receives the launch's device
+ * time, fold_out the XOR of all words (it depends on the coins only).
+ * threads and blocks_per_thread in [1, 2^31] with fewer than 2^32 blocks in
+ * all, form 0 or 1, else SKIS_EINVAL; synchronises the stream. */
+int skis_philox_rate(uint64_t seed, uint64_t threads, uint64_t blocks_per_thread, int form, double *ms_out,
+                     uint32_t *fold_out, void *cuda_stream);
 
 /* Number of CUDA kernel launches the library has made in this process
  * (diagnostic; counts every launch of every entry point). */

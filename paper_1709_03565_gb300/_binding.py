@@ -90,7 +90,7 @@ _SIGNATURES = [
     ("skis_server_free", None, [_P]),
     ("skis_estimate_sharded", _INT, [_P, _I32, _P, _P, _P, _P, _INT, _P, _P, _P, _P]),
     ("skis_greedy_maxcover_sharded", _INT, [_P, _I32, _P, _P, _P, _P, _P, _P, _P]),
-    ("skis_philox_rate", _INT, [_U64, _U64, _U64, ctypes.c_uint32, _INT, _P, _P, _P]),
+    ("skis_philox_rate", _INT, [_U64, _U64, _U64, _INT, _P, _P, _P]),
     ("skis_kernel_launches", ctypes.c_uint64, []),
     ("skis_device_allocations", ctypes.c_uint64, []),
     ("skis_last_error", ctypes.c_char_p, []),
@@ -514,12 +514,12 @@ def skis_greedy_maxcover_sharded(s: Sketch, k: int, exchange, allreduce, stream=
     return seeds, cov, est
 
 
-def skis_philox_rate(seed: int, threads: int, blocks_per_thread: int, tau: int, form: int, stream=None):
-    """(device ms, coin words below tau) of the coin-generator probe."""
-    ms, live = ctypes.c_double(), ctypes.c_uint64()
-    _check(lib().skis_philox_rate(int(seed), int(threads), int(blocks_per_thread), int(tau), int(form),
-                                  ctypes.byref(ms), ctypes.byref(live), _stream(stream)))
-    return ms.value, live.value
+def skis_philox_rate(seed: int, threads: int, blocks_per_thread: int, form: int, stream=None):
+    """(device ms, XOR of every coin word) of the coin-generator probe."""
+    ms, fold = ctypes.c_double(), ctypes.c_uint32()
+    _check(lib().skis_philox_rate(int(seed), int(threads), int(blocks_per_thread), int(form), ctypes.byref(ms),
+                                  ctypes.byref(fold), _stream(stream)))
+    return ms.value, fold.value
 
 
 def skis_kernel_launches() -> int:

@@ -592,20 +592,18 @@ extern "C" void skis_sketch_free(skis_sketch* s) {
 
 extern "C" const char* skis_last_error(void) { return g_err.c_str(); }
 
-extern "C" int skis_philox_rate(uint64_t seed, uint64_t threads, uint64_t blocks_per_thread, uint32_t tau, int form,
-                                double* ms_out, uint64_t* live_out, void* cuda_stream) {
+extern "C" int skis_philox_rate(uint64_t seed, uint64_t threads, uint64_t blocks_per_thread, int form,
+                                double* ms_out, uint32_t* fold_out, void* cuda_stream) {
     API_TRY
-    if (!ms_out || !live_out) return fail(SKIS_EINVAL, "skis_philox_rate: NULL output");
+    if (!ms_out || !fold_out) return fail(SKIS_EINVAL, "skis_philox_rate: NULL output");
     if (threads < 1 || threads > (1ull << 31) || blocks_per_thread < 1 || blocks_per_thread > (1ull << 31) ||
         form < 0 || form > 1 || threads * blocks_per_thread >= (1ull << 32))
         return fail(SKIS_EINVAL, "skis_philox_rate: threads and blocks per thread in [1, 2^31], fewer than 2^32 "
                                  "blocks, form 0 or 1");
     std::string err;
-    unsigned long long live = 0;
-    const int rc = philox_rate(seed, threads, blocks_per_thread, tau, form, ms_out, &live,
-                               (cudaStream_t)cuda_stream, &err);
+    const int rc = philox_rate(seed, threads, blocks_per_thread, form, ms_out, fold_out, (cudaStream_t)cuda_stream,
+                               &err);
     if (rc != SKIS_OK) return fail(rc, err);
-    *live_out = live;
     return SKIS_OK;
     API_CATCH
 }

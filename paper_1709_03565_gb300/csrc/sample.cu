@@ -453,6 +453,11 @@ constexpr int kLaneQ = 32;
 constexpr int kLaneStride = kLaneQ + 1;  // odd: conflict-free by lane and by member
 constexpr int kLaneRefill = 8;
 
+// One of 64 bits for vertex u (the top six bits of a multiplicative hash): a
+// lane's sample keeps the OR over its members, so a candidate whose bit is
+// clear is new without searching the member list.
+__device__ __forceinline__ uint64_t member_bit(uint32_t u) { return 1ull << ((u * 0x9E3779B9u) >> 26); }
+
 __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
     __shared__ int32_t s_q[kLaneBlock / 32][32 * kLaneStride];
     const int lane = threadIdx.x & 31;
@@ -472,6 +477,7 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
     uint32_t pool_n = 0, pool_used = 0;
     uint4 rec = make_uint4(0, 0, 0, 0);
     uint2 prec = make_uint2(0, 0);
+    uint64_t sig = 0;  // the sample's members, one hashed bit each (member_bit)
     uint64_t chunk_pos = 0, chunk_end = 0;
 
     for (;;) {
@@ -576,6 +582,7 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                         pf_ok = false;
                         r = 0;
                         mine[0] = (int32_t)v;
+                        sig = member_bit(v);
                         len = 1;
                         head = 1;
                         src_deg = rv_deg;
@@ -585,6 +592,7 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                         q_last = hi > lo ? (hi - 1) >> 2 : lo >> 2;
                         if (a.srcpick) {  // bucket form: the picked in-edge, round-0 coins after it
                             mine[1] = (int32_t)pk_u;
+                            sig |= member_bit(pk_u);
                             len = 2;
                             lo = pk_e + 1;
                             any = true;
@@ -644,11 +652,15 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                         if (!((lh >> k) & 1u) || handed) continue;
                         const int32_t u = cand[k];
                         bool seen = false;
-                        for (uint32_t i = 0; i < len; ++i)
-                            if (mine[i] == u) { seen = true; break; }
+                        if (sig & member_bit(u))  // else u is certainly new
+                            for (uint32_t i = 0; i < len; ++i)
+                                if (mine[i] == u) { seen = true; break; }
                         if (seen) continue;
                         if (len == (uint32_t)kLaneQ) handed = true;  // the warp tier takes it
-                        else mine[len++] = u;
+                        else {
+                            mine[len++] = u;
+                            sig |= member_bit(u);
+                        }
                     }
                 }
             }

@@ -394,8 +394,8 @@ void sketch_release(skis_sketch* s);
 int sketch_autotune(skis_sketch* s, uint64_t pilot, cudaStream_t st, double* cand_ms, int cand_cap, int* ncand,
                     std::string* err);
 // The coin generator's throughput on this GPU (the ALU ceiling probe).
-int philox_rate(uint64_t seed, uint64_t threads, uint64_t per, uint32_t tau, int form, double* ms_out,
-                unsigned long long* live_out, cudaStream_t st, std::string* err);
+int philox_rate(uint64_t seed, uint64_t threads, uint64_t per, int form, double* ms_out, uint32_t* fold_out,
+                cudaStream_t st, std::string* err);
 
 // Records msg as the calling thread's last error (skis_last_error); returns code.
 int set_last_error(int code, const std::string& msg);
