@@ -522,7 +522,26 @@ __global__ void __launch_bounds__(kLaneBlock, 4) k_iis_lane(SampleArgs a) {
                     }
                 }
                 __syncwarp();
-                if (fits) {
+                if (fits && total < 16u * (uint32_t)__popc(dn)) {
+                    // short samples: their members end to end over the warp's
+                    // lanes, each lane finding the sample that holds its entry
+                    // (the first lane whose inclusive end exceeds it)
+                    const uint32_t excl = incl - mylen;
+                    for (uint32_t b0 = 0; b0 < total; b0 += 32) {
+                        const uint32_t idx = b0 + (uint32_t)lane;
+                        int owner = 0;
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1)
+                            if (__shfl_sync(kFull, incl, owner + step - 1) <= idx) owner += step;
+                        const uint32_t start = __shfl_sync(kFull, excl, owner);
+                        if (idx < total) {
+                            const int32_t u = mq[owner * kLaneStride + (idx - start)];
+                            a.arena[chunk_pos + idx] = u;
+                            count_member(a, u);
+                        }
+                    }
+                    chunk_pos += total;
+                } else if (fits) {
                     unsigned m = dn;
                     while (m) {
                         const int sl = __ffs(m) - 1;
