@@ -51,12 +51,35 @@ def _pair(n, src, dst, model, weights=None, weight_seed=0):
     return g, o
 
 
+def _long_rows(model):
+    """2000 vertices with in-rows of every gamma-chain path: three rows of
+    2^15 in-edges and more (walked one a thread in one-warp blocks), four of
+    2^10 .. 2^13 (ordered by degree class) and an ER background (row order);
+    edges shuffled; WC, or per-edge p below 1e-4 so that the long rows stay
+    sparse."""
+    rng = np.random.default_rng(21)
+    n = 2000
+    ps, pd = [], []
+    for v, d in ((0, 33000), (1, 34000), (2, 40000), (3, 1500), (4, 2100), (5, 1100), (6, 5000)):
+        s = rng.integers(0, n - 1, d)
+        ps.append(np.where(s >= v, s + 1, s))  # no self-loop
+        pd.append(np.full(d, v))
+    es, ed = synth.er(n, 16000, 22)
+    src = np.concatenate(ps + [es]).astype(np.int32)
+    dst = np.concatenate(pd + [ed]).astype(np.int32)
+    order = rng.permutation(len(src))
+    src, dst = src[order], dst[order]
+    return n, src, dst, model, (None if model == "wc" else synth.uniform_p(len(src), 23, 0.0, 1e-4))
+
+
 GRAPHS = {
     "er-wc": lambda: (3000, *synth.er(3000, 24000, 11), "wc", None),
     "chunglu-p": lambda: (20000, *synth.chunglu(20000, 150000, 2.1, 12), "p", synth.tri(150000, 12)),
     "chunglu-tri": lambda: (5000, *synth.chunglu(5000, 40000, 2.1, 13), "tri", None),
     "rmat-tau": lambda: (4096, *synth.rmat(12, 30000, 0.57, 0.19, 0.19, 14), "tau",
                          (synth.uniform_p(30000, 14, 0.0, 0.3) * 2**32).astype(np.uint32)),
+    "long-rows-wc": lambda: _long_rows("wc"),
+    "long-rows-p": lambda: _long_rows("p"),
     "tiny-ragged": lambda: (7, np.array([1, 2, 3, 4, 5, 6, 0, 2, 2], np.int32),
                             np.array([0, 0, 0, 1, 1, 2, 3, 3, 3], np.int32), "p",
                             np.array([0.5, 1.0, 0.2, 0.7, 0.0, 0.9, 0.3, 0.3, 1e-9])),
