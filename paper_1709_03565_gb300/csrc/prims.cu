@@ -209,62 +209,81 @@ __device__ __forceinline__ uint64_t edge_key(const int32_t* src, const int32_t* 
     return ((uint64_t)(uint32_t)dst[e] << src_bits) | (uint64_t)(uint32_t)src[e];
 }
 
-// Digit counts of every pass: hist[p * 256 + d] = #{edges whose key has
-// digit d in pass p}.
+// Pass p sorts on the digit (key >> shift[p]) & (2^bits[p] - 1), bits[p] in
+// {8, 9}: a 9-bit pass has 512 digits, two a thread in the per-digit steps,
+// so that 50- and 52-bit keys take six passes instead of seven.
+constexpr int kOsMaxDigits = 512;
+struct OsPasses {
+    int n;
+    int shift[kOsMaxPasses];
+    int bits[kOsMaxPasses];
+};
+
+// Digit counts of every pass: hist[p * kOsMaxDigits + d] = #{edges whose key
+// has digit d in pass p}.
 __global__ void __launch_bounds__(256) k_os_hist(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
-                                                 int64_t m, int src_bits, int passes,
+                                                 int64_t m, int src_bits, OsPasses ps,
                                                  unsigned long long* __restrict__ hist) {
-    __shared__ uint32_t s_h[kOsMaxPasses * 256];
-    for (int i = threadIdx.x; i < passes * 256; i += 256) s_h[i] = 0;
+    __shared__ uint32_t s_h[kOsMaxPasses * kOsMaxDigits];
+    for (int i = threadIdx.x; i < ps.n * kOsMaxDigits; i += 256) s_h[i] = 0;
     __syncthreads();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t key = edge_key(src, dst, e, src_bits);
-        for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + (uint32_t)((key >> (8 * p)) & 255u)], 1u);
+#pragma unroll
+        for (int p = 0; p < kOsMaxPasses; ++p)  // static indices: the pass table stays in the parameters
+            if (p < ps.n)
+                atomicAdd(&s_h[p * kOsMaxDigits + (uint32_t)((key >> ps.shift[p]) & ((1u << ps.bits[p]) - 1u))], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += 256)
+    for (int i = threadIdx.x; i < ps.n * kOsMaxDigits; i += 256)
         if (s_h[i]) atomicAdd(&hist[i], (unsigned long long)s_h[i]);
 }
 
-// Exclusive prefix of each pass's digit counts, in place: base[p * 256 + d].
-__global__ void k_os_bases(unsigned long long* __restrict__ hist, int passes) {
-    __shared__ unsigned long long s_c[256];
+// Exclusive prefix of each pass's digit counts, in place: base[p * kOsMaxDigits + d].
+__global__ void __launch_bounds__(kOsMaxDigits) k_os_bases(unsigned long long* __restrict__ hist, int passes) {
+    __shared__ unsigned long long s_c[kOsMaxDigits];
     for (int p = 0; p < passes; ++p) {
-        s_c[threadIdx.x] = hist[p * 256 + threadIdx.x];
+        s_c[threadIdx.x] = hist[p * kOsMaxDigits + threadIdx.x];
         __syncthreads();
         unsigned long long b = 0;
         for (int d = 0; d < (int)threadIdx.x; ++d) b += s_c[d];
-        hist[p * 256 + threadIdx.x] = b;
+        hist[p * kOsMaxDigits + threadIdx.x] = b;
         __syncthreads();
     }
 }
 
-// One pass on digit `shift / 8`. kFirst: the items are the edges (key built
-// from src / dst, value = input index). Dynamic shared memory: kOsTile keys
-// and values.
-template <bool kFirst>
+// One pass on the kBits-bit digit at `shift`. kFirst: the items are the
+// edges (key built from src / dst, value = input index). Dynamic shared
+// memory: kOsTile keys and values.
+template <bool kFirst, int kBits>
 __global__ void __launch_bounds__(kOsThreads, 3) k_os_pass(
     const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int src_bits,
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, int64_t n, int shift, unsigned long long tag,
     const unsigned long long* __restrict__ base, unsigned long long* __restrict__ status,
     unsigned int* __restrict__ ticket, unsigned int* __restrict__ gave_up) {
+    constexpr int kDigits = 1 << kBits, kPer = kDigits / kOsThreads;  // digits a thread owns
+    constexpr uint32_t kMask = kDigits - 1;
     extern __shared__ __align__(16) unsigned char os_smem[];
     uint64_t* s_keys = reinterpret_cast<uint64_t*>(os_smem);
     uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + kOsTile);
-    __shared__ uint32_t s_wcnt[kOsWarps][256];  // per warp: digit counts, then the warp's start in the digit
-    __shared__ uint32_t s_tstart[256];          // digit start within the tile
-    __shared__ unsigned long long s_gbase[256]; // output position of the digit's first item of the tile
-    __shared__ uint32_t s_wsum[kOsWarps];
+    __shared__ uint32_t s_wcnt[kOsWarps][kDigits];   // per warp: digit counts, then the warp's start in the digit
+    __shared__ uint32_t s_tstart[kDigits];           // digit start within the tile
+    __shared__ unsigned long long s_gbase[kDigits];  // output position of the digit's first item of the tile
+    __shared__ uint32_t s_wsum[kPer][kOsWarps];
     __shared__ uint32_t s_tile, s_bad;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
         s_tile = atomicAdd(ticket, 1u);
         s_bad = 0;
     }
-    const unsigned long long digit_base = base[tid];  // in flight while the tile loads
+    unsigned long long digit_base[kPer];  // in flight while the tile loads
 #pragma unroll
-    for (int w = 0; w < kOsWarps; ++w) s_wcnt[w][tid] = 0;
+    for (int r = 0; r < kPer; ++r) digit_base[r] = base[tid + r * kOsThreads];
+#pragma unroll
+    for (int w = 0; w < kOsWarps; ++w)
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) s_wcnt[w][tid + r * kOsThreads] = 0;
     __syncthreads();
     const uint32_t tile = s_tile;
     const int64_t t0 = (int64_t)tile * kOsTile;
@@ -286,7 +305,7 @@ __global__ void __launch_bounds__(kOsThreads, 3) k_os_pass(
 #pragma unroll
     for (int c = 0; c < kOsItems; ++c) {
         const bool valid = wb + c * 32 + lane < n;
-        const uint32_t d = valid ? (uint32_t)((key[c] >> shift) & 255u) : 256u;
+        const uint32_t d = valid ? (uint32_t)((key[c] >> shift) & kMask) : (uint32_t)kDigits;
         const unsigned peers = __match_any_sync(kFull, d);
         const int leader = __ffs(peers) - 1;
         uint32_t before = 0;
@@ -299,73 +318,89 @@ __global__ void __launch_bounds__(kOsThreads, 3) k_os_pass(
         rnk[c] = before + (uint32_t)__popc(peers & lanemask_lt());
     }
     __syncthreads();
-    // thread tid owns digit tid: the tile's count and each warp's start
-    uint32_t cnt = 0;
+    // thread tid owns digits tid + r kOsThreads: the tile's count and each warp's start
+    uint32_t cnt[kPer], x[kPer];
 #pragma unroll
-    for (int w = 0; w < kOsWarps; ++w) {
-        const uint32_t c2 = s_wcnt[w][tid];
-        s_wcnt[w][tid] = cnt;
-        cnt += c2;
-    }
-    unsigned long long* my = status + (size_t)tile * 256 + tid;
-    st_relaxed_u64(my, (tile == 0 ? kOsIncl : kOsAgg) | tag | cnt);
-    // tile-local digit starts (exclusive scan of cnt over the block)
-    uint32_t x = cnt;
+    for (int r = 0; r < kPer; ++r) {
+        const int dd = tid + r * kOsThreads;
+        uint32_t run = 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) s_wsum[wid] = x;
-    // look back over the earlier tiles for this digit's items before the
-    // tile, kOsWindow tiles a read: sum their own counts back to the first
-    // inclusive prefix, waiting on the first tile not yet published
-    unsigned long long excl = 0;
-    if (tile > 0) {
-        int64_t t = (int64_t)tile - 1;  // the next tile to account for
-        uint32_t spins = 0;
-        bool done = false;
-        while (!done) {
-            unsigned long long v[kOsWindow];
-#pragma unroll
-            for (int k = 0; k < kOsWindow; ++k)
-                v[k] = t - k >= 0 ? ld_relaxed_u64(status + (size_t)(t - k) * 256 + tid) : 0;
-            int k = 0;
-#pragma unroll
-            for (int q = 0; q < kOsWindow; ++q) {
-                const bool ready = (v[q] & (63ull << 56)) == tag && (v[q] >> 62) != 0;
-                if (!ready) break;
-                excl += v[q] & kOsCount;
-                ++k;
-                if ((v[q] >> 62) == 2) {
-                    done = true;
-                    break;
-                }
-            }
-            if (done) break;
-            t -= k;  // tile 0 is always inclusive, so t stays >= 0
-            if (k < kOsWindow) {  // tile t is not published yet
-                if (++spins > kOsSpinLimit) {  // cannot happen while every claimed tile runs; never hang
-                    atomicOr(gave_up, 1u);
-                    s_bad = 1;
-                    break;
-                }
-                __nanosleep(64);
-            }
+        for (int w = 0; w < kOsWarps; ++w) {
+            const uint32_t c2 = s_wcnt[w][dd];
+            s_wcnt[w][dd] = run;
+            run += c2;
         }
-        st_relaxed_u64(my, kOsIncl | tag | ((excl + cnt) & kOsCount));
+        cnt[r] = run;
+        st_relaxed_u64(status + (size_t)tile * kDigits + dd, (tile == 0 ? kOsIncl : kOsAgg) | tag | run);
+        // tile-local digit starts: exclusive scan of the counts in digit order
+        uint32_t y = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t z = __shfl_up_sync(kFull, y, o);
+            if (lane >= o) y += z;
+        }
+        x[r] = y;
+        if (lane == 31) s_wsum[r][wid] = y;
     }
-    s_gbase[tid] = digit_base + excl;
+    // look back over the earlier tiles for each owned digit's items before
+    // the tile, kOsWindow tiles a read: sum their own counts back to the first
+    // inclusive prefix, waiting on the first tile not yet published
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int dd = tid + r * kOsThreads;
+        unsigned long long excl = 0;
+        if (tile > 0) {
+            int64_t t = (int64_t)tile - 1;  // the next tile to account for
+            uint32_t spins = 0;
+            bool done = false;
+            while (!done) {
+                unsigned long long v[kOsWindow];
+#pragma unroll
+                for (int k = 0; k < kOsWindow; ++k)
+                    v[k] = t - k >= 0 ? ld_relaxed_u64(status + (size_t)(t - k) * kDigits + dd) : 0;
+                int k = 0;
+#pragma unroll
+                for (int q = 0; q < kOsWindow; ++q) {
+                    const bool ready = (v[q] & (63ull << 56)) == tag && (v[q] >> 62) != 0;
+                    if (!ready) break;
+                    excl += v[q] & kOsCount;
+                    ++k;
+                    if ((v[q] >> 62) == 2) {
+                        done = true;
+                        break;
+                    }
+                }
+                if (done) break;
+                t -= k;  // tile 0 is always inclusive, so t stays >= 0
+                if (k < kOsWindow) {  // tile t is not published yet
+                    if (++spins > kOsSpinLimit) {  // cannot happen while every claimed tile runs; never hang
+                        atomicOr(gave_up, 1u);
+                        s_bad = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            st_relaxed_u64(status + (size_t)tile * kDigits + dd, kOsIncl | tag | ((excl + cnt[r]) & kOsCount));
+        }
+        s_gbase[dd] = digit_base[r] + excl;
+    }
     __syncthreads();
-    uint32_t before = 0;
-    for (int w = 0; w < wid; ++w) before += s_wsum[w];
-    s_tstart[tid] = before + x - cnt;
+    uint32_t lower = 0;  // items of the tile in the digits owned before this pass of r
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        uint32_t before = lower;
+        for (int w = 0; w < wid; ++w) before += s_wsum[r][w];
+        s_tstart[tid + r * kOsThreads] = before + x[r] - cnt[r];
+#pragma unroll
+        for (int w = 0; w < kOsWarps; ++w) lower += s_wsum[r][w];
+    }
     __syncthreads();
     // the tile in shared memory in digit order
 #pragma unroll
     for (int c = 0; c < kOsItems; ++c) {
         if (wb + c * 32 + lane < n) {
-            const uint32_t d = (uint32_t)((key[c] >> shift) & 255u);
+            const uint32_t d = (uint32_t)((key[c] >> shift) & kMask);
             const uint32_t pos = s_tstart[d] + s_wcnt[wid][d] + rnk[c];
             s_keys[pos] = key[c];
             s_vals[pos] = val[c];
@@ -376,7 +411,7 @@ __global__ void __launch_bounds__(kOsThreads, 3) k_os_pass(
     const int tile_n = (int)min((int64_t)kOsTile, n - t0);
     for (int i = tid; i < tile_n; i += kOsThreads) {
         const uint64_t k = s_keys[i];
-        const uint32_t d = (uint32_t)((k >> shift) & 255u);
+        const uint32_t d = (uint32_t)((k >> shift) & kMask);
         const unsigned long long g = s_gbase[d] + (unsigned long long)(i - (int)s_tstart[d]);
         if (g >= (unsigned long long)n) {  // inconsistent counts (cannot happen): never write out of bounds
             atomicOr(gave_up, 2u);
@@ -387,34 +422,76 @@ __global__ void __launch_bounds__(kOsThreads, 3) k_os_pass(
     }
 }
 
+// The passes for keys of `bits` bits: P = ceil(bits / 9) passes (at least
+// one), the last max(0, bits - 8 P) of them 9 bits wide, the others 8 (50
+// bits: 8, 8, 8, 8, 9, 9; 40 bits: five of 8).
+static OsPasses os_passes(int bits) {
+    OsPasses ps{};
+    const int P = std::max(1, (bits + 8) / 9);
+    const int nine = std::max(0, bits - 8 * P);  // <= P, as 9 P >= bits
+    ps.n = P;
+    int sh = 0;
+    for (int p = 0; p < P; ++p) {
+        ps.bits[p] = p >= P - nine ? 9 : 8;
+        ps.shift[p] = sh;
+        sh += ps.bits[p];
+    }
+    return ps;
+}
+
+template <int kBits>
+static cudaError_t os_pass_attr(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_os_pass<true, kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_os_pass<false, kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
+}
+
+template <int kBits>
+static void os_launch(bool first, int64_t ntiles, size_t smem, cudaStream_t st, const int32_t* src, const int32_t* dst,
+                      int src_bits, const uint64_t* ksrc, const uint32_t* vsrc, uint64_t* kdst, uint32_t* vdst,
+                      int64_t m, int shift, unsigned long long tag, const unsigned long long* base,
+                      unsigned long long* status, unsigned int* ticket, unsigned int* gave_up) {
+    if (first)
+        k_os_pass<true, kBits><<<(unsigned)ntiles, kOsThreads, smem, st>>>(src, dst, src_bits, nullptr, nullptr, kdst,
+                                                                          vdst, m, shift, tag, base, status, ticket,
+                                                                          gave_up);
+    else
+        k_os_pass<false, kBits><<<(unsigned)ntiles, kOsThreads, smem, st>>>(nullptr, nullptr, src_bits, ksrc, vsrc,
+                                                                           kdst, vdst, m, shift, tag, base, status,
+                                                                           ticket, gave_up);
+}
+
 cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int src_bits, uint64_t* keys_out,
                        uint32_t* vals_out, uint64_t* keys_alt, uint32_t* vals_alt, unsigned int* gave_up,
                        cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
-    const int passes = std::max(1, (2 * src_bits + 7) / 8);
-    if (passes > kOsMaxPasses) return cudaErrorInvalidValue;
+    const OsPasses ps = os_passes(2 * src_bits);
+    if (ps.n > kOsMaxPasses) return cudaErrorInvalidValue;
+    const int passes = ps.n;
     const int64_t ntiles = (m + kOsTile - 1) / kOsTile;
     const size_t smem = (size_t)kOsTile * (sizeof(uint64_t) + sizeof(uint32_t));
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [smem] {
-        attr_err = cudaFuncSetAttribute(k_os_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(k_os_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_err = os_pass_attr<8>(smem);
+        if (attr_err == cudaSuccess) attr_err = os_pass_attr<9>(smem);
     });
     if (attr_err != cudaSuccess) return attr_err;
     unsigned long long *hist = nullptr, *status = nullptr;
     unsigned int* tickets = nullptr;
-    cudaError_t e = dev_alloc_t(&hist, (size_t)passes * 256, st);
-    if (e == cudaSuccess) e = dev_alloc_t(&status, (size_t)ntiles * 256, st);
+    cudaError_t e = dev_alloc_t(&hist, (size_t)passes * kOsMaxDigits, st);
+    if (e == cudaSuccess) e = dev_alloc_t(&status, (size_t)ntiles * kOsMaxDigits, st);
     if (e == cudaSuccess) e = dev_alloc_t(&tickets, (size_t)passes, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, (size_t)passes * 256 * sizeof(unsigned long long), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, (size_t)ntiles * 256 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(hist, 0, (size_t)passes * kOsMaxDigits * sizeof(unsigned long long), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(status, 0, (size_t)ntiles * kOsMaxDigits * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, (size_t)passes * sizeof(unsigned int), st);
     if (e == cudaSuccess) {
         const int grid = (int)std::min<int64_t>((int64_t)sm_count() * 8, std::max<int64_t>(1, (m + 255) / 256));
-        k_os_hist<<<grid, 256, 0, st>>>(src, dst, m, src_bits, passes, hist); note_launch();
-        k_os_bases<<<1, 256, 0, st>>>(hist, passes); note_launch();
+        k_os_hist<<<grid, 256, 0, st>>>(src, dst, m, src_bits, ps, hist); note_launch();
+        k_os_bases<<<1, kOsMaxDigits, 0, st>>>(hist, passes); note_launch();
         e = cudaGetLastError();
     }
     const uint64_t* ksrc = nullptr;
@@ -424,13 +501,12 @@ cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int sr
         uint64_t* kdst = to_out ? keys_out : keys_alt;
         uint32_t* vdst = to_out ? vals_out : vals_alt;
         const unsigned long long tag = (unsigned long long)(p + 1) << 56;
-        if (p == 0)
-            k_os_pass<true><<<(unsigned)ntiles, kOsThreads, smem, st>>>(src, dst, src_bits, nullptr, nullptr, kdst, vdst,
-                                                                      m, 0, tag, hist, status, tickets, gave_up);
+        if (ps.bits[p] == 9)
+            os_launch<9>(p == 0, ntiles, smem, st, src, dst, src_bits, ksrc, vsrc, kdst, vdst, m, ps.shift[p], tag,
+                         hist + p * kOsMaxDigits, status, tickets + p, gave_up);
         else
-            k_os_pass<false><<<(unsigned)ntiles, kOsThreads, smem, st>>>(nullptr, nullptr, src_bits, ksrc, vsrc, kdst,
-                                                                       vdst, m, 8 * p, tag, hist + p * 256, status,
-                                                                       tickets + p, gave_up);
+            os_launch<8>(p == 0, ntiles, smem, st, src, dst, src_bits, ksrc, vsrc, kdst, vdst, m, ps.shift[p], tag,
+                         hist + p * kOsMaxDigits, status, tickets + p, gave_up);
         note_launch();
         e = cudaGetLastError();
         ksrc = kdst;
