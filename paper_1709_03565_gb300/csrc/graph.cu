@@ -43,41 +43,34 @@ __global__ void k_validate(const int32_t* __restrict__ src, const int32_t* __res
     }
 }
 
-// Row offsets of the canonical CSR from the sorted keys: off[v] is the first
-// position whose destination is >= v. Position e writes off[v] for the
-// destinations v in (dst(e - 1), dst(e)], and the last position the ones
-// after its destination, so every entry of off[0 .. n] is written once.
-__global__ void k_offsets_from_keys(const uint64_t* __restrict__ keys, int64_t m, int64_t n, int src_bits,
-                                    uint64_t* __restrict__ off) {
+// Row offsets of the canonical CSR from the sorted destinations: off[v] is
+// the first position whose destination is >= v. Position e writes off[v]
+// for the destinations v in (dst(e - 1), dst(e)], and the last position the
+// ones after its destination, so every entry of off[0 .. n] is written once.
+__global__ void k_offsets_from_dst(const uint32_t* __restrict__ csr_dst, int64_t m, int64_t n,
+                                   uint64_t* __restrict__ off) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e <= m; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t prev = e > 0 ? (int64_t)(keys[e - 1] >> src_bits) : -1;
-        const int64_t cur = e < m ? (int64_t)(keys[e] >> src_bits) : n;
+        const int64_t prev = e > 0 ? (int64_t)csr_dst[e - 1] : -1;
+        const int64_t cur = e < m ? (int64_t)csr_dst[e] : n;
         for (int64_t v = prev + 1; v <= cur; ++v) off[v] = (uint64_t)e;
     }
 }
 
-// CSR arrays from the sorted pairs; per-edge thresholds by model. Padding
-// positions (m .. m_pad) get source 0 and threshold 0 (never live).
-__global__ void k_gather_edges(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t m,
-                               int64_t m_pad, int src_bits, int model, const void* __restrict__ weights,
-                               uint64_t weight_seed, int32_t* __restrict__ csr_src, uint32_t* __restrict__ csr_tau,
-                               uint32_t* __restrict__ perm) {
-    const uint64_t mask = (1ull << src_bits) - 1;
+// Per-edge thresholds of the CSR positions by model (explicit p or tau read
+// through the input index; TRI from the WEIGHT coin of the position).
+// Padding positions (m .. m_pad) get threshold 0 (never live).
+__global__ void k_edge_tau(const uint32_t* __restrict__ perm, int64_t m, int64_t m_pad, int model,
+                           const void* __restrict__ weights, uint64_t weight_seed, uint32_t* __restrict__ csr_tau) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m_pad; e += (int64_t)gridDim.x * blockDim.x) {
         if (e >= m) {
-            csr_src[e] = 0;
-            if (csr_tau) csr_tau[e] = 0;
+            csr_tau[e] = 0;
             continue;
         }
-        const uint32_t idx = vals[e];
-        csr_src[e] = (int32_t)(keys[e] & mask);
-        perm[e] = idx;
-        if (!csr_tau) continue;
         uint32_t t;
         if (model == SKIS_W_EXPLICIT_P) {
-            t = tau_from_p(((const double*)weights)[idx]);
+            t = tau_from_p(((const double*)weights)[perm[e]]);
         } else if (model == SKIS_W_EXPLICIT_TAU) {
-            t = ((const uint32_t*)weights)[idx];
+            t = ((const uint32_t*)weights)[perm[e]];
         } else {  // SKIS_W_TRI: level floor(3 x / 2^32) of the WEIGHT coin of position e
             const uint4 x = coin_block(weight_seed, (uint64_t)e >> 2, 0, kDomWeight, 0);
             const uint32_t level = (uint32_t)(((uint64_t)word_of(x, (int)(e & 3)) * 3u) >> 32);
@@ -425,8 +418,8 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     // temporaries
     DevStatus* d_status = nullptr;
     unsigned long long* d_W = nullptr;
-    uint64_t *keys_s = nullptr, *keys_alt = nullptr;
-    uint32_t *vals_s = nullptr, *vals_alt = nullptr;
+    uint64_t *keys_a = nullptr, *keys_b = nullptr;
+    uint32_t *vals_a = nullptr, *vals_b = nullptr, *csr_dst = nullptr;
     uint32_t *is_light = nullptr, *light_ids = nullptr, *heavy_ids = nullptr;
     uint64_t* light_idx = nullptr;
     u128 *deficit = nullptr, *excess = nullptr, *D = nullptr, *Ex = nullptr;
@@ -471,17 +464,22 @@ int graph_build(skis_graph* g, const int32_t* d_src, const int32_t* d_dst, const
     GB_CUDA(dev_alloc_t(&g->w, (size_t)n, st));
     GB_CUDA(dev_alloc_t(&g->alias, (size_t)n, st));
     if (m > 0) {
-        GB_CUDA(dev_alloc_t(&keys_s, (size_t)m, st));
-        GB_CUDA(dev_alloc_t(&keys_alt, (size_t)m, st));
-        GB_CUDA(dev_alloc_t(&vals_s, (size_t)m, st));
-        GB_CUDA(dev_alloc_t(&vals_alt, (size_t)m, st));
-        GB_CUDA(sort_edges(d_src, d_dst, m, src_bits, keys_s, vals_s, keys_alt, vals_alt, &d_status->gave_up, st));
+        GB_CUDA(dev_alloc_t(&keys_a, (size_t)m, st));
+        GB_CUDA(dev_alloc_t(&keys_b, (size_t)m, st));
+        GB_CUDA(dev_alloc_t(&vals_a, (size_t)m, st));
+        GB_CUDA(dev_alloc_t(&vals_b, (size_t)m, st));
+        GB_CUDA(dev_alloc_t(&csr_dst, (size_t)m, st));
+        GB_CUDA(sort_edges(d_src, d_dst, m, src_bits, g->src, csr_dst, g->perm, keys_a, vals_a, keys_b, vals_b,
+                           &d_status->gave_up, st));
     }
-    k_offsets_from_keys<<<grid, block, 0, st>>>(keys_s, m, n, src_bits, g->off); note_launch();
+    k_offsets_from_dst<<<grid, block, 0, st>>>(csr_dst, m, n, g->off); note_launch();
     GB_CUDA(cudaGetLastError());
-    k_gather_edges<<<grid, block, 0, st>>>(keys_s, vals_s, m, g->m_pad, src_bits, model, d_weights, weight_seed,
-                                           g->src, g->tau, g->perm); note_launch();
-    GB_CUDA(cudaGetLastError());
+    // padding positions (m .. m_pad) get source 0 and, with per-edge models, threshold 0 (never live)
+    GB_CUDA(cudaMemsetAsync(g->src + m, 0, (size_t)(g->m_pad - m) * sizeof(int32_t), st));
+    if (g->tau) {
+        k_edge_tau<<<grid, block, 0, st>>>(g->perm, m, g->m_pad, model, d_weights, weight_seed, g->tau); note_launch();
+        GB_CUDA(cudaGetLastError());
+    }
     k_rows<<<grid, block, 0, st>>>(g->off, n, g->row_uniform, g->rows); note_launch();
     GB_CUDA(cudaGetLastError());
 
@@ -581,10 +579,11 @@ cleanup:
     dev_free(class_starts, st);
     dev_free(d_status, st);
     dev_free(d_W, st);
-    dev_free(keys_s, st);
-    dev_free(keys_alt, st);
-    dev_free(vals_s, st);
-    dev_free(vals_alt, st);
+    dev_free(keys_a, st);
+    dev_free(keys_b, st);
+    dev_free(vals_a, st);
+    dev_free(vals_b, st);
+    dev_free(csr_dst, st);
     dev_free(is_light, st);
     dev_free(light_idx, st);
     dev_free(light_ids, st);

@@ -253,13 +253,23 @@ __global__ void __launch_bounds__(kOsMaxDigits) k_os_bases(unsigned long long* _
 }
 
 // One pass on the kBits-bit digit at `shift`. kFirst: the items are the
-// edges (key built from src / dst, value = input index). Dynamic shared
-// memory: kOsTile keys and values.
-template <bool kFirst, int kBits>
+// edges (key built from src / dst, value = input index). kLast: the sorted
+// items leave as the CSR arrays (source = the key's low src_bits bits,
+// destination = the rest, input index) instead of keys and values. Dynamic
+// shared memory: kOsTile keys and values.
+struct OsOut {
+    uint64_t* keys;
+    uint32_t* vals;
+    int32_t* csr_src;
+    uint32_t* csr_dst;
+    uint32_t* perm;
+};
+
+template <bool kFirst, bool kLast, int kBits>
 __global__ void __launch_bounds__(kOsThreads, 3) k_os_pass(
     const int32_t* __restrict__ src, const int32_t* __restrict__ dst, int src_bits,
-    const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint64_t* __restrict__ keys_out,
-    uint32_t* __restrict__ vals_out, int64_t n, int shift, unsigned long long tag,
+    const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, OsOut out, int64_t n, int shift,
+    unsigned long long tag,
     const unsigned long long* __restrict__ base, unsigned long long* __restrict__ status,
     unsigned int* __restrict__ ticket, unsigned int* __restrict__ gave_up) {
     constexpr int kDigits = 1 << kBits, kPer = kDigits / kOsThreads;  // digits a thread owns
@@ -417,8 +427,14 @@ __global__ void __launch_bounds__(kOsThreads, 3) k_os_pass(
             atomicOr(gave_up, 2u);
             continue;
         }
-        keys_out[g] = k;
-        vals_out[g] = s_vals[i];
+        if (kLast) {
+            out.csr_src[g] = (int32_t)(k & ((1ull << src_bits) - 1));
+            out.csr_dst[g] = (uint32_t)(k >> src_bits);
+            out.perm[g] = s_vals[i];
+        } else {
+            out.keys[g] = k;
+            out.vals[g] = s_vals[i];
+        }
     }
 }
 
@@ -441,30 +457,31 @@ static OsPasses os_passes(int bits) {
 
 template <int kBits>
 static cudaError_t os_pass_attr(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_os_pass<true, kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_os_pass<false, kBits>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return e;
+    const void* fns[4] = {(const void*)k_os_pass<true, false, kBits>, (const void*)k_os_pass<false, false, kBits>,
+                          (const void*)k_os_pass<true, true, kBits>, (const void*)k_os_pass<false, true, kBits>};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-template <int kBits>
+template <int kBits, bool kLast>
 static void os_launch(bool first, int64_t ntiles, size_t smem, cudaStream_t st, const int32_t* src, const int32_t* dst,
-                      int src_bits, const uint64_t* ksrc, const uint32_t* vsrc, uint64_t* kdst, uint32_t* vdst,
-                      int64_t m, int shift, unsigned long long tag, const unsigned long long* base,
-                      unsigned long long* status, unsigned int* ticket, unsigned int* gave_up) {
+                      int src_bits, const uint64_t* ksrc, const uint32_t* vsrc, const OsOut& out, int64_t m, int shift,
+                      unsigned long long tag, const unsigned long long* base, unsigned long long* status,
+                      unsigned int* ticket, unsigned int* gave_up) {
     if (first)
-        k_os_pass<true, kBits><<<(unsigned)ntiles, kOsThreads, smem, st>>>(src, dst, src_bits, nullptr, nullptr, kdst,
-                                                                          vdst, m, shift, tag, base, status, ticket,
-                                                                          gave_up);
+        k_os_pass<true, kLast, kBits><<<(unsigned)ntiles, kOsThreads, smem, st>>>(
+            src, dst, src_bits, nullptr, nullptr, out, m, shift, tag, base, status, ticket, gave_up);
     else
-        k_os_pass<false, kBits><<<(unsigned)ntiles, kOsThreads, smem, st>>>(nullptr, nullptr, src_bits, ksrc, vsrc,
-                                                                           kdst, vdst, m, shift, tag, base, status,
-                                                                           ticket, gave_up);
+        k_os_pass<false, kLast, kBits><<<(unsigned)ntiles, kOsThreads, smem, st>>>(
+            nullptr, nullptr, src_bits, ksrc, vsrc, out, m, shift, tag, base, status, ticket, gave_up);
 }
 
-cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int src_bits, uint64_t* keys_out,
-                       uint32_t* vals_out, uint64_t* keys_alt, uint32_t* vals_alt, unsigned int* gave_up,
-                       cudaStream_t st) {
+cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int src_bits, int32_t* csr_src,
+                       uint32_t* csr_dst, uint32_t* perm, uint64_t* keys_a, uint32_t* vals_a, uint64_t* keys_b,
+                       uint32_t* vals_b, unsigned int* gave_up, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     const OsPasses ps = os_passes(2 * src_bits);
     if (ps.n > kOsMaxPasses) return cudaErrorInvalidValue;
@@ -497,20 +514,30 @@ cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int sr
     const uint64_t* ksrc = nullptr;
     const uint32_t* vsrc = nullptr;
     for (int p = 0; p < passes && e == cudaSuccess; ++p) {
-        const bool to_out = ((passes - 1 - p) % 2) == 0;
-        uint64_t* kdst = to_out ? keys_out : keys_alt;
-        uint32_t* vdst = to_out ? vals_out : vals_alt;
+        // passes alternate between the a and b buffers; the last one writes the CSR arrays
+        const bool last = p == passes - 1;
+        const OsOut out{p % 2 == 0 ? keys_a : keys_b, p % 2 == 0 ? vals_a : vals_b, csr_src, csr_dst, perm};
         const unsigned long long tag = (unsigned long long)(p + 1) << 56;
-        if (ps.bits[p] == 9)
-            os_launch<9>(p == 0, ntiles, smem, st, src, dst, src_bits, ksrc, vsrc, kdst, vdst, m, ps.shift[p], tag,
-                         hist + p * kOsMaxDigits, status, tickets + p, gave_up);
-        else
-            os_launch<8>(p == 0, ntiles, smem, st, src, dst, src_bits, ksrc, vsrc, kdst, vdst, m, ps.shift[p], tag,
-                         hist + p * kOsMaxDigits, status, tickets + p, gave_up);
+        const unsigned long long* base = hist + p * kOsMaxDigits;
+        if (ps.bits[p] == 9) {
+            if (last)
+                os_launch<9, true>(p == 0, ntiles, smem, st, src, dst, src_bits, ksrc, vsrc, out, m, ps.shift[p], tag,
+                                   base, status, tickets + p, gave_up);
+            else
+                os_launch<9, false>(p == 0, ntiles, smem, st, src, dst, src_bits, ksrc, vsrc, out, m, ps.shift[p], tag,
+                                    base, status, tickets + p, gave_up);
+        } else {
+            if (last)
+                os_launch<8, true>(p == 0, ntiles, smem, st, src, dst, src_bits, ksrc, vsrc, out, m, ps.shift[p], tag,
+                                   base, status, tickets + p, gave_up);
+            else
+                os_launch<8, false>(p == 0, ntiles, smem, st, src, dst, src_bits, ksrc, vsrc, out, m, ps.shift[p], tag,
+                                    base, status, tickets + p, gave_up);
+        }
         note_launch();
         e = cudaGetLastError();
-        ksrc = kdst;
-        vsrc = vdst;
+        ksrc = out.keys;
+        vsrc = out.vals;
     }
     dev_free(hist, st);
     dev_free(status, st);

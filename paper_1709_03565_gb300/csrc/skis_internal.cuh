@@ -226,14 +226,16 @@ cudaError_t scan_u64(const uint64_t* in, uint64_t* out, int64_t n, cudaStream_t 
 cudaError_t scan_u128(const u128* in, u128* out, int64_t n, cudaStream_t st);
 
 // Stable sort of the m edges by key dst << src_bits | src (keys of
-// 2 src_bits bits), the input index as value: keys_out / vals_out receive the
-// sorted pairs; the *_alt buffers (m entries each) are scratch. *gave_up
-// (device word) is set nonzero if a look-back wait ran out (which only a
-// tile that never ran could cause) or an output position fell outside
-// [0, m); the result is then invalid and nothing was written out of bounds.
-cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int src_bits, uint64_t* keys_out,
-                       uint32_t* vals_out, uint64_t* keys_alt, uint32_t* vals_alt, unsigned int* gave_up,
-                       cudaStream_t st);
+// 2 src_bits bits), the input index as value, written out as the CSR arrays:
+// csr_src[e], csr_dst[e] and perm[e] (the input index) for every sorted
+// position e < m. keys_a / vals_a and keys_b / vals_b (m entries each) are
+// scratch. *gave_up (device word) is set nonzero if a look-back wait ran out
+// (which only a tile that never ran could cause) or an output position fell
+// outside [0, m); the result is then invalid and nothing was written out of
+// bounds.
+cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int src_bits, int32_t* csr_src,
+                       uint32_t* csr_dst, uint32_t* perm, uint64_t* keys_a, uint32_t* vals_a, uint64_t* keys_b,
+                       uint32_t* vals_b, unsigned int* gave_up, cudaStream_t st);
 
 // Sum of a uint64 array (integers: order-independent), result in *out (device).
 cudaError_t sum_u64(const uint64_t* in, int64_t n, unsigned long long* out, cudaStream_t st);
