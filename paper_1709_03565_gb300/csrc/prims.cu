@@ -488,12 +488,9 @@ cudaError_t sort_edges(const int32_t* src, const int32_t* dst, int64_t m, int sr
     const int passes = ps.n;
     const int64_t ntiles = (m + kOsTile - 1) / kOsTile;
     const size_t smem = (size_t)kOsTile * (sizeof(uint64_t) + sizeof(uint32_t));
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [smem] {
-        attr_err = os_pass_attr<8>(smem);
-        if (attr_err == cudaSuccess) attr_err = os_pass_attr<9>(smem);
-    });
+    // set on every call: the attribute belongs to the current device
+    cudaError_t attr_err = os_pass_attr<8>(smem);
+    if (attr_err == cudaSuccess) attr_err = os_pass_attr<9>(smem);
     if (attr_err != cudaSuccess) return attr_err;
     unsigned long long *hist = nullptr, *status = nullptr;
     unsigned int* tickets = nullptr;
