@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 import paper_1709_03565_gb300 as skis
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -53,6 +55,11 @@ def test_bad_arguments_are_rejected_before_any_device_work():
                              ctypes.c_void_p(dst.ctypes.data), None, 9, 0, skis.SKIS_MEM_HOST, None)
     assert rc == skis.SKIS_EINVAL
     assert lib.skis_sketch_set_option(None, 0, 1) == skis.SKIS_EINVAL
+    # the coin-generator probe checks its sizes and form on the host: no thread or block, a third
+    # form, 2^32 blocks in all, more than 2^31 blocks a thread
+    for args in ((1, 0, 1, 0), (1, 1, 0, 0), (1, 1, 1, 2), (1, 1 << 20, 1 << 12, 0), (1, 1, (1 << 31) + 1, 0)):
+        with pytest.raises(skis.SkisError):
+            skis.skis_philox_rate(*args)
 
 
 _CTYPES = {"int32_t": ctypes.c_int32, "uint32_t": ctypes.c_uint32, "int64_t": ctypes.c_int64,

@@ -34,9 +34,3 @@ def test_probe_folds_the_oracles_coins(seed, per):
     for form in (0, 1):
         ms, fold = skis.skis_philox_rate(seed, threads, per, form)
         assert fold == want and ms > 0
-
-
-def test_probe_rejects_bad_sizes():
-    for args in ((1, 0, 1, 0), (1, 1, 0, 0), (1, 1, 1, 2), (1, 1 << 20, 1 << 12, 0)):
-        with pytest.raises(skis.SkisError):
-            skis.skis_philox_rate(*args)
